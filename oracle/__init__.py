@@ -1,0 +1,259 @@
+"""FP64 CPU oracle for TA-SC-IVR power spectra (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The library in ``paper_1312_4698_gb300`` never
+imports it, and the two share no code: this wrapper loads ``scivr_oracle.c``
+(plain C, libm, compiled with gcc) through ctypes.
+
+Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
+  pes_eval          finite differences, Euler homogeneity, Morse closed forms
+  log_overlap       numerical quadrature of the coherent-state wavefunctions
+  det_real/complex  numpy.linalg.det (LAPACK) on random matrices
+  propagate         harmonic closed form (Glauber coherent-state algebra),
+                    symplecticity M^T J M = J, energy O(dt^4), time reversal,
+                    finite-difference monodromy, order-4 convergence,
+                    generating-function identity of the action
+  spectrum          Dirichlet-kernel closed form, harmonic eigen-expansion,
+                    Parseval, 1D Morse closed-form levels
+  sample_initial    Philox4x32-10 known-answer vectors, moments, the
+                    resolution-of-identity expectation of the weights
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "scivr_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle_scivr.so")
+_CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-tree-vectorize", "-fopenmp",
+           "-shared", "-fPIC"]
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (in-tree shared object)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *_CFLAGS, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Pes(C.Structure):
+    _fields_ = [("F", C.c_int32), ("diag_kind", C.c_int32),
+                ("omega", C.c_void_p), ("D", C.c_void_p), ("a", C.c_void_p),
+                ("n3", C.c_int32), ("idx3", C.c_void_p), ("c3", C.c_void_p),
+                ("n4", C.c_int32), ("idx4", C.c_void_p), ("c4", C.c_void_p)]
+
+
+class _Prop(C.Structure):
+    _fields_ = [("F", C.c_int32), ("n_steps", C.c_int32), ("dt", C.c_double),
+                ("stab_tol", C.c_double), ("gamma", C.c_void_p), ("p_eq", C.c_void_p),
+                ("q_eq", C.c_void_p), ("n_chi", C.c_int32)]
+
+
+class _Cplx(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class _Final(C.Structure):
+    _fields_ = [("p", C.c_void_p), ("q", C.c_void_p), ("S", C.c_void_p), ("theta", C.c_void_p),
+                ("detM", C.c_void_p), ("detA", C.c_void_p), ("M", C.c_void_p)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+            lib.or_pes_eval.restype = d
+            lib.or_pes_eval.argtypes = [vp, vp, vp, vp]
+            lib.or_det_real.restype = d
+            lib.or_det_real.argtypes = [C.c_int, vp]
+            lib.or_det_complex.restype = _Cplx
+            lib.or_det_complex.argtypes = [C.c_int, vp]
+            lib.or_log_overlap.restype = _Cplx
+            lib.or_log_overlap.argtypes = [C.c_int, vp, vp, vp, vp, vp]
+            lib.or_propagate_one.restype = C.c_int
+            lib.or_propagate_one.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
+            lib.or_propagate.restype = C.c_int
+            lib.or_propagate.argtypes = [vp, vp, i64, vp, vp, vp, i64, vp,
+                                         vp, vp, vp, vp, vp, vp, vp, C.c_int]
+            lib.or_spectrum.restype = C.c_int
+            lib.or_spectrum.argtypes = [vp, i64, vp, vp, i64, i32, d, d, d, i32, vp, vp, C.c_int]
+            lib.or_philox4x32_10.restype = None
+            lib.or_philox4x32_10.argtypes = [vp, vp, vp]
+            lib.or_sample_initial.restype = C.c_int
+            lib.or_sample_initial.argtypes = [i32, vp, vp, vp, i64, C.c_uint64, vp, vp, vp]
+            lib.or_max_threads.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Pes:
+    """Owns contiguous copies of a descriptor's arrays and the C struct pointing at them."""
+
+    def __init__(self, desc):
+        self.F = int(desc.F)
+        self._keep = [_f64(desc.omega), _f64(desc.D), _f64(desc.a),
+                      np.ascontiguousarray(desc.idx3, dtype=np.int32), _f64(desc.c3),
+                      np.ascontiguousarray(desc.idx4, dtype=np.int32), _f64(desc.c4)]
+        om, D, a, i3, c3, i4, c4 = self._keep
+        self.s = _Pes(self.F, int(desc.diag_kind), _p(om), _p(D), _p(a),
+                      c3.size, _p(i3), _p(c3), c4.size, _p(i4), _p(c4))
+
+
+def max_threads() -> int:
+    return int(_load().or_max_threads())
+
+
+def pes_eval(desc, q):
+    """V, grad V [F], Hessian [F, F] at one point q [F]."""
+    lib = _load()
+    P = Pes(desc)
+    q = _f64(q)
+    g = np.zeros(P.F)
+    H = np.zeros((P.F, P.F))
+    V = lib.or_pes_eval(C.byref(P.s), _p(q), _p(g), _p(H))
+    return float(V), g, H
+
+
+def det_real(A):
+    A = _f64(A).copy()
+    return float(_load().or_det_real(A.shape[0], _p(A)))
+
+
+def det_complex(A):
+    A = np.ascontiguousarray(A, dtype=np.complex128).copy()
+    r = _load().or_det_complex(A.shape[0], _p(A))
+    return complex(r.re, r.im)
+
+
+def log_overlap(gamma, p1, q1, p2, q2):
+    """log <p1 q1 | p2 q2> for product coherent states of widths gamma."""
+    gamma, p1, q1, p2, q2 = map(_f64, (gamma, p1, q1, p2, q2))
+    r = _load().or_log_overlap(gamma.size, _p(gamma), _p(p1), _p(q1), _p(p2), _p(q2))
+    return complex(r.re, r.im)
+
+
+def _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol):
+    gamma = _f64(gamma)
+    p_eq = _f64(np.atleast_2d(p_eq))
+    q_eq = _f64(np.atleast_2d(q_eq))
+    s = _Prop(F, int(n_steps), float(dt), float(stab_tol), _p(gamma), _p(p_eq), _p(q_eq),
+              p_eq.shape[0])
+    return s, (gamma, p_eq, q_eq)
+
+
+def propagate_one(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6):
+    """One trajectory with full diagnostics.
+
+    Returns a dict with amp [n_chi, K], good, the series S, theta, detA, detM
+    [K] and the final p, q, M."""
+    lib = _load()
+    P = Pes(desc)
+    F = P.F
+    s, keep = _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol)
+    K = n_steps + 1
+    n_chi = keep[1].shape[0]
+    amp = np.zeros((n_chi, K), dtype=np.complex128)
+    S = np.zeros(K); th = np.zeros(K); dA = np.zeros(K, dtype=np.complex128); dM = np.zeros(K)
+    fp = np.zeros(F); fq = np.zeros(F); fS = np.zeros(1); fth = np.zeros(1); fdM = np.zeros(1)
+    fdA = np.zeros(1, dtype=np.complex128); fM = np.zeros((2 * F, 2 * F))
+    fin = _Final(_p(fp), _p(fq), _p(fS), _p(fth), _p(fdM), _p(fdA), _p(fM))
+    p0 = _f64(p0); q0 = _f64(q0)
+    ok = lib.or_propagate_one(C.byref(P.s), C.byref(s), _p(p0), _p(q0), _p(amp), K,
+                              C.byref(fin), _p(S), _p(th), _p(dA), _p(dM))
+    return dict(amp=amp, good=bool(ok), S=S, theta=th, detA=dA, detM=dM, p=fp, q=fq, M=fM)
+
+
+def propagate(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6, n_threads=0,
+              final=False):
+    """Batch propagation; p0, q0 are [F, n_traj] (variable-major).
+
+    Returns amp [n_chi, n_traj, n_steps+1] complex128 and good [n_traj] uint8,
+    plus a dict of final-state arrays when final=True."""
+    lib = _load()
+    P = Pes(desc)
+    F = P.F
+    p0 = _f64(p0); q0 = _f64(q0)
+    n = p0.shape[1]
+    s, keep = _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol)
+    n_chi = keep[1].shape[0]
+    K = n_steps + 1
+    amp = np.zeros((n_chi, n, K), dtype=np.complex128)
+    good = np.zeros(n, dtype=np.uint8)
+    fin = None
+    if final:
+        fin = dict(p=np.zeros((n, F)), q=np.zeros((n, F)), S=np.zeros(n), theta=np.zeros(n),
+                   detM=np.zeros(n), detA=np.zeros(n, dtype=np.complex128),
+                   M=np.zeros((n, 2 * F, 2 * F)))
+    g = (lambda k: _p(fin[k])) if final else (lambda k: None)
+    lib.or_propagate(C.byref(P.s), C.byref(s), n, _p(p0), _p(q0), _p(amp), K, _p(good),
+                     g("p"), g("q"), g("S"), g("theta"), g("detM"), g("detA"), g("M"),
+                     int(n_threads))
+    return (amp, good, fin) if final else (amp, good)
+
+
+def spectrum(amp, w, good, n_steps, dt, E_min, E_max, n_E, n_threads=0):
+    """Eq. I(E)_discreto on amp [n_traj, K]; returns (I [n_E], n_good)."""
+    lib = _load()
+    amp = np.ascontiguousarray(amp, dtype=np.complex128)
+    w = _f64(w)
+    good = np.ascontiguousarray(good, dtype=np.uint8)
+    I = np.zeros(int(n_E))
+    ng = np.zeros(1, dtype=np.int64)
+    lib.or_spectrum(_p(amp), amp.shape[1], _p(w), _p(good), amp.shape[0], int(n_steps),
+                    float(dt), float(E_min), float(E_max), int(n_E), _p(I), _p(ng),
+                    int(n_threads))
+    return I, int(ng[0])
+
+
+def philox4x32_10(ctr, key):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32)
+    key = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().or_philox4x32_10(_p(ctr), _p(key), _p(out))
+    return out
+
+
+def sample_initial(gamma, p_eq, q_eq, n_traj, seed):
+    """Husimi samples: returns p0, q0 [F, n_traj] and w [n_traj]."""
+    gamma = _f64(gamma)
+    p_eq = _f64(np.atleast_2d(p_eq)[0])
+    q_eq = _f64(np.atleast_2d(q_eq)[0])
+    F = gamma.size
+    p0 = np.zeros((F, n_traj)); q0 = np.zeros((F, n_traj)); w = np.zeros(n_traj)
+    _load().or_sample_initial(F, _p(gamma), _p(p_eq), _p(q_eq), int(n_traj),
+                              C.c_uint64(int(seed)), _p(p0), _p(q0), _p(w))
+    return p0, q0, w
+
+
+def run_workload(wl, p0=None, q0=None, w=None, n_threads=0):
+    """Sample (unless given), propagate and take the spectrum for every chi."""
+    if p0 is None:
+        p0, q0, w = sample_initial(wl.gamma, wl.p_eq, wl.q_eq, wl.n_traj, wl.seed)
+    amp, good = propagate(wl.pes, wl.gamma, wl.p_eq, wl.q_eq, wl.dt, wl.n_steps, p0, q0,
+                          wl.stab_tol, n_threads)
+    spectra = []
+    ng = 0
+    for x in range(amp.shape[0]):
+        I, ng = spectrum(amp[x], w, good, wl.n_steps, wl.dt, wl.E_min, wl.E_max, wl.n_E,
+                         n_threads)
+        spectra.append(I)
+    return dict(p0=p0, q0=q0, w=w, amp=amp, good=good, I=np.stack(spectra), n_good=ng)

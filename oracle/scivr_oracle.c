@@ -1,0 +1,509 @@
+/*
+ * scivr_oracle.c -- plain, slow FP64 CPU oracle for TA-SC-IVR power spectra.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library or its CUDA kernels may
+ * call, link or include this file; only the tests, the package's smoke check
+ * and the benchmark's CPU-baseline leg use it.  It shares no code, header,
+ * table or constant generator with the GPU path.
+ *
+ * What it computes, step by step, in the paper's order and notation
+ * (Tamascelli, Dambrosio, Conte, Ceotto, "GPU accelerated SC-IVR molecular
+ * dynamics", arXiv:1312.4698):
+ *
+ *   1. Potential V(q), gradient and Hessian of a Morse (or harmonic) diagonal
+ *      plus cubic and quartic coupling monomials (Sec. IV; analytic forms).
+ *   2. Husimi sampling of (p0, q0) around chi = |p_eq, q_eq> and the weights
+ *      w_j (Sec. III.A, after Eq. I(E)_discreto).
+ *   3. Fourth-order symplectic propagation of (p, q), the action S and the
+ *      2F x 2F monodromy matrix M = d(p_t, q_t)/d(p_0, q_0) (Sec. II, Eq.
+ *      prefactor; Sec. III.A).  Integrator: Yoshida's triple-jump composition
+ *      of exact drift and kick sub-flows (the paper only says "fourth order
+ *      symplectic"; this is the reading used throughout).
+ *   4. Stability monitor: bad once |det(M^T M) - 1| > tol (Sec. II and III.A).
+ *   5. Herman-Kluk prefactor matrix A (Eq. prefactor), its complex
+ *      determinant and the continuous phase phi_t = arg(det A)/2 (Eq.
+ *      sep_approx and the phase definition just before it).
+ *   6. Coherent-state overlap <chi|p_t, q_t> (Eq. coherent_state) and the
+ *      amplitude a(c) = <chi|p_c q_c> exp(i (S_c + phi_c)) (Eq. I(E)_discreto).
+ *   7. The discrete time-averaged spectrum, Eq. I(E)_discreto, as a direct
+ *      O(K * N_E) Fourier sum per good trajectory.
+ *
+ * Every number is IEEE double; transcendental functions come from libm.
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_TWO_PI 6.283185307179586476925286766559
+
+/* ------------------------------------------------------------------------ */
+/* Potential: V(q) = sum_i diag_i(q_i) + sum_m c3_m q_i q_j q_k + sum_m c4_m q_i q_j q_k q_l */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t F;
+    int32_t diag_kind;        /* 0: harmonic omega^2 q^2 / 2, 1: Morse D (1 - e^{-a q})^2 */
+    const double *omega;      /* [F] */
+    const double *D;          /* [F] */
+    const double *a;          /* [F] */
+    int32_t n3;
+    const int32_t *idx3;      /* [n3 * 3] */
+    const double *c3;         /* [n3] */
+    int32_t n4;
+    const int32_t *idx4;      /* [n4 * 4] */
+    const double *c4;         /* [n4] */
+} or_pes;
+
+/* One monomial c * prod_s q[idx[s]] and its derivatives by the product rule
+ * over index positions (repeated indices are handled automatically). */
+static void or_monomial(int deg, const int32_t *idx, double c, const double *q, int F,
+                        double *V, double *g, double *H)
+{
+    double v = c;
+    for (int s = 0; s < deg; ++s) v *= q[idx[s]];
+    *V += v;
+    if (g) {
+        for (int s = 0; s < deg; ++s) {
+            double prod = c;
+            for (int t = 0; t < deg; ++t)
+                if (t != s) prod *= q[idx[t]];
+            g[idx[s]] += prod;
+        }
+    }
+    if (H) {
+        for (int s = 0; s < deg; ++s)
+            for (int t = 0; t < deg; ++t) {
+                if (t == s) continue;
+                double prod = c;
+                for (int u = 0; u < deg; ++u)
+                    if (u != s && u != t) prod *= q[idx[u]];
+                H[idx[s] * F + idx[t]] += prod;
+            }
+    }
+}
+
+/* V(q); if g != NULL also the gradient [F]; if H != NULL also the Hessian [F*F] row-major. */
+double or_pes_eval(const or_pes *pes, const double *q, double *g, double *H)
+{
+    const int F = pes->F;
+    double V = 0.0;
+    if (g) memset(g, 0, sizeof(double) * F);
+    if (H) memset(H, 0, sizeof(double) * F * F);
+    for (int i = 0; i < F; ++i) {
+        if (pes->diag_kind == 0) {
+            double w2 = pes->omega[i] * pes->omega[i];
+            V += 0.5 * w2 * q[i] * q[i];
+            if (g) g[i] += w2 * q[i];
+            if (H) H[i * F + i] += w2;
+        } else {
+            double Dm = pes->D[i], am = pes->a[i];
+            double u = exp(-am * q[i]);
+            V += Dm * (1.0 - u) * (1.0 - u);
+            if (g) g[i] += 2.0 * Dm * am * u * (1.0 - u);
+            if (H) H[i * F + i] += 2.0 * Dm * am * am * u * (2.0 * u - 1.0);
+        }
+    }
+    for (int m = 0; m < pes->n3; ++m) or_monomial(3, pes->idx3 + 3 * m, pes->c3[m], q, F, &V, g, H);
+    for (int m = 0; m < pes->n4; ++m) or_monomial(4, pes->idx4 + 4 * m, pes->c4[m], q, F, &V, g, H);
+    return V;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Determinants by LU with partial pivoting (textbook Doolittle elimination) */
+/* ------------------------------------------------------------------------ */
+
+/* det of an n x n real matrix (row-major); A is destroyed. */
+double or_det_real(int n, double *A)
+{
+    double det = 1.0;
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        double best = fabs(A[k * n + k]);
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(A[i * n + k]) > best) { best = fabs(A[i * n + k]); piv = i; }
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[k * n + j]; A[k * n + j] = A[piv * n + j]; A[piv * n + j] = t;
+            }
+            det = -det;
+        }
+        double akk = A[k * n + k];
+        det *= akk;
+        if (akk == 0.0) return 0.0;
+        for (int i = k + 1; i < n; ++i) {
+            double l = A[i * n + k] / akk;
+            for (int j = k + 1; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+        }
+    }
+    return det;
+}
+
+/* det of an n x n complex matrix (row-major); A is destroyed. */
+double complex or_det_complex(int n, double complex *A)
+{
+    double complex det = 1.0;
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        double best = cabs(A[k * n + k]);
+        for (int i = k + 1; i < n; ++i)
+            if (cabs(A[i * n + k]) > best) { best = cabs(A[i * n + k]); piv = i; }
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) {
+                double complex t = A[k * n + j]; A[k * n + j] = A[piv * n + j]; A[piv * n + j] = t;
+            }
+            det = -det;
+        }
+        double complex akk = A[k * n + k];
+        det *= akk;
+        if (akk == 0.0) return 0.0;
+        for (int i = k + 1; i < n; ++i) {
+            double complex l = A[i * n + k] / akk;
+            for (int j = k + 1; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+        }
+    }
+    return det;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coherent states (Eq. coherent_state, normalisation (gamma_i/pi)^{1/4} per mode) */
+/* ------------------------------------------------------------------------ */
+
+/* log <p1 q1 | p2 q2> for product coherent states of widths gamma:
+ * sum_i [ -gamma_i/4 (q1-q2)^2 - (p1-p2)^2/(4 gamma_i) + (i/2)(p1+p2)(q1-q2) ]. */
+double complex or_log_overlap(int F, const double *gamma, const double *p1, const double *q1,
+                              const double *p2, const double *q2)
+{
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < F; ++i) {
+        double dq = q1[i] - q2[i], dp = p1[i] - p2[i];
+        re += -0.25 * gamma[i] * dq * dq - dp * dp / (4.0 * gamma[i]);
+        im += 0.5 * (p1[i] + p2[i]) * dq;
+    }
+    return re + I * im;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Propagation of one trajectory                                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t F;
+    int32_t n_steps;
+    double dt;
+    double stab_tol;
+    const double *gamma;   /* [F] */
+    const double *p_eq;    /* [n_chi * F] */
+    const double *q_eq;    /* [n_chi * F] */
+    int32_t n_chi;
+} or_prop;
+
+typedef struct {
+    double *p, *q;          /* [F] at T */
+    double *S, *theta;      /* action and unwrapped arg det A at T */
+    double *detM;           /* det M at T */
+    double complex *detA;   /* det A at T */
+    double *M;              /* [2F * 2F] at T, rows (p, q), columns (p0, q0) */
+} or_final;
+
+/* Yoshida (1990) fourth-order triple jump, written as position-Verlet
+ * compositions: drifts c1..c4 and kicks d1..d3 (fractions of dt). */
+static void or_yoshida(double c[4], double d[3])
+{
+    double cbrt2 = cbrt(2.0);
+    double w1 = 1.0 / (2.0 - cbrt2);
+    double w0 = -cbrt2 / (2.0 - cbrt2);
+    c[0] = 0.5 * w1; c[1] = 0.5 * (w0 + w1); c[2] = c[1]; c[3] = c[0];
+    d[0] = w1; d[1] = w0; d[2] = w1;
+}
+
+/* Drift by tau under T = p^2/2: q += tau p, S += tau p.p/2, dq-rows of M += tau dp-rows. */
+static void or_drift(int F, double tau, double *q, const double *p, double *S, double *M)
+{
+    const int n = 2 * F;
+    double kin = 0.0;
+    for (int a = 0; a < F; ++a) kin += 0.5 * p[a] * p[a];
+    *S += tau * kin;
+    for (int a = 0; a < F; ++a) q[a] += tau * p[a];
+    for (int a = 0; a < F; ++a)
+        for (int col = 0; col < n; ++col) M[(F + a) * n + col] += tau * M[a * n + col];
+}
+
+/* Kick by tau under V(q): p -= tau grad V, S -= tau V, dp-rows of M -= tau H dq-rows. */
+static void or_kick(const or_pes *pes, double tau, const double *q, double *p, double *S,
+                    double *M, double *g, double *H)
+{
+    const int F = pes->F, n = 2 * F;
+    double V = or_pes_eval(pes, q, g, H);
+    *S -= tau * V;
+    for (int a = 0; a < F; ++a) p[a] -= tau * g[a];
+    for (int a = 0; a < F; ++a)
+        for (int col = 0; col < n; ++col) {
+            double hm = 0.0;
+            for (int b = 0; b < F; ++b) hm += H[a * F + b] * M[(F + b) * n + col];
+            M[a * n + col] -= tau * hm;
+        }
+}
+
+/* Herman-Kluk prefactor matrix (Eq. prefactor), in the width-symmetric form
+ * A = 1/2 [ G^{1/2} Mqq G^{-1/2} + G^{-1/2} Mpp G^{1/2}
+ *           - i G^{1/2} Mqp G^{1/2} + i G^{-1/2} Mpq G^{-1/2} ],  G = diag(gamma),
+ * with Mqq = dq_t/dq_0, Mpp = dp_t/dp_0, Mqp = dq_t/dp_0, Mpq = dp_t/dq_0. */
+static void or_prefactor_matrix(int F, const double *gamma, const double *M, double complex *A)
+{
+    const int n = 2 * F;
+    for (int a = 0; a < F; ++a)
+        for (int b = 0; b < F; ++b) {
+            double ga = sqrt(gamma[a]), gb = sqrt(gamma[b]);
+            double Mpp = M[a * n + b];
+            double Mpq = M[a * n + F + b];
+            double Mqp = M[(F + a) * n + b];
+            double Mqq = M[(F + a) * n + F + b];
+            double re = ga / gb * Mqq + gb / ga * Mpp;
+            double im = -ga * gb * Mqp + Mpq / (ga * gb);
+            A[a * F + b] = 0.5 * (re + I * im);
+        }
+}
+
+/* Continuous phase of det A.  The argument is unwrapped relative to the
+ * reference rotation exp(-i sum_i gamma_i t): per step, the change of
+ * arg(det A) + sum_i gamma_i t is taken as its principal value. */
+static double or_unwrap(double theta, double arg_old, double arg_new, double ref_step)
+{
+    double d = arg_new - arg_old + ref_step;
+    d -= OR_TWO_PI * nearbyint(d / OR_TWO_PI);
+    return theta + d - ref_step;
+}
+
+/* Propagate one trajectory from (p0, q0) and write the amplitude series
+ * amp[chi * amp_chi_stride + c], c = 0..n_steps, for every reference state chi.
+ * The optional series (length n_steps+1, may be NULL) record S_c, theta_c,
+ * det A_c and det M_c.  Returns 1 if the trajectory stayed good, else 0. */
+int or_propagate_one(const or_pes *pes, const or_prop *prm, const double *p0, const double *q0,
+                     double complex *amp, int64_t amp_chi_stride, or_final *fin,
+                     double *S_series, double *theta_series, double complex *detA_series,
+                     double *detM_series)
+{
+    const int F = pes->F, n = 2 * F;
+    double c[4], d[3];
+    or_yoshida(c, d);
+
+    double *p = malloc(sizeof(double) * F), *q = malloc(sizeof(double) * F);
+    double *M = malloc(sizeof(double) * n * n), *Mw = malloc(sizeof(double) * n * n);
+    double *g = malloc(sizeof(double) * F), *H = malloc(sizeof(double) * F * F);
+    double complex *A = malloc(sizeof(double complex) * F * F);
+
+    memcpy(p, p0, sizeof(double) * F);
+    memcpy(q, q0, sizeof(double) * F);
+    for (int i = 0; i < n * n; ++i) M[i] = 0.0;
+    for (int i = 0; i < n; ++i) M[i * n + i] = 1.0;
+    double S = 0.0, theta = 0.0, arg_old = 0.0, detM = 1.0;
+    double complex detA = 1.0;
+    double ref_step = 0.0;
+    for (int i = 0; i < F; ++i) ref_step += prm->gamma[i] * prm->dt;
+    int good = 1;
+
+    for (int step = 0; step <= prm->n_steps; ++step) {
+        if (step > 0) {
+            const double dt = prm->dt;
+            or_drift(F, c[0] * dt, q, p, &S, M);
+            or_kick(pes, d[0] * dt, q, p, &S, M, g, H);
+            or_drift(F, c[1] * dt, q, p, &S, M);
+            or_kick(pes, d[1] * dt, q, p, &S, M, g, H);
+            or_drift(F, c[2] * dt, q, p, &S, M);
+            or_kick(pes, d[2] * dt, q, p, &S, M, g, H);
+            or_drift(F, c[3] * dt, q, p, &S, M);
+
+            /* stability monitor: |det(M^T M) - 1| = |det(M)^2 - 1| */
+            memcpy(Mw, M, sizeof(double) * n * n);
+            detM = or_det_real(n, Mw);
+            if (!isfinite(detM) || fabs(detM * detM - 1.0) > prm->stab_tol) good = 0;
+
+            /* prefactor determinant and its continuous phase */
+            or_prefactor_matrix(F, prm->gamma, M, A);
+            detA = or_det_complex(F, A);
+            double arg_new = carg(detA);
+            theta = or_unwrap(theta, arg_old, arg_new, ref_step);
+            arg_old = arg_new;
+            if (!isfinite(S) || !isfinite(theta)) good = 0;
+            for (int i = 0; i < F; ++i)
+                if (!isfinite(p[i]) || !isfinite(q[i])) good = 0;
+        }
+        if (S_series) S_series[step] = S;
+        if (theta_series) theta_series[step] = theta;
+        if (detA_series) detA_series[step] = detA;
+        if (detM_series) detM_series[step] = detM;
+        if (amp) {
+            for (int x = 0; x < prm->n_chi; ++x) {
+                double complex lo = or_log_overlap(F, prm->gamma, prm->p_eq + x * F,
+                                                   prm->q_eq + x * F, p, q);
+                double phase = cimag(lo) + S + 0.5 * theta;
+                amp[x * amp_chi_stride + step] = exp(creal(lo)) * (cos(phase) + I * sin(phase));
+            }
+        }
+    }
+    if (fin) {
+        if (fin->p) memcpy(fin->p, p, sizeof(double) * F);
+        if (fin->q) memcpy(fin->q, q, sizeof(double) * F);
+        if (fin->S) *fin->S = S;
+        if (fin->theta) *fin->theta = theta;
+        if (fin->detM) *fin->detM = detM;
+        if (fin->detA) *fin->detA = detA;
+        if (fin->M) memcpy(fin->M, M, sizeof(double) * n * n);
+    }
+    free(p); free(q); free(M); free(Mw); free(g); free(H); free(A);
+    return good;
+}
+
+/* Batch propagation.  p0, q0: [F][n_traj] (variable-major).  amp: complex
+ * [n_chi][n_traj][amp_ld], amp_ld >= n_steps + 1.  good: [n_traj].  Optional
+ * final-state arrays (may be NULL): fin_p, fin_q [n_traj][F]; fin_S, fin_theta,
+ * fin_detM [n_traj]; fin_detA [n_traj]; fin_M [n_traj][2F][2F]. */
+int or_propagate(const or_pes *pes, const or_prop *prm, int64_t n_traj, const double *p0,
+                 const double *q0, double complex *amp, int64_t amp_ld, uint8_t *good,
+                 double *fin_p, double *fin_q, double *fin_S, double *fin_theta, double *fin_detM,
+                 double complex *fin_detA, double *fin_M, int n_threads)
+{
+    const int F = pes->F, n = 2 * F;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int64_t j = 0; j < n_traj; ++j) {
+        double p_init[64], q_init[64];
+        for (int i = 0; i < F; ++i) { p_init[i] = p0[i * n_traj + j]; q_init[i] = q0[i * n_traj + j]; }
+        or_final fin = {
+            fin_p ? fin_p + j * F : NULL, fin_q ? fin_q + j * F : NULL,
+            fin_S ? fin_S + j : NULL, fin_theta ? fin_theta + j : NULL,
+            fin_detM ? fin_detM + j : NULL, fin_detA ? fin_detA + j : NULL,
+            fin_M ? fin_M + j * n * n : NULL };
+        int ok = or_propagate_one(pes, prm, p_init, q_init, amp ? amp + j * amp_ld : NULL,
+                                  n_traj * amp_ld, &fin, NULL, NULL, NULL, NULL);
+        if (good) good[j] = (uint8_t)ok;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time-averaged spectrum, Eq. I(E)_discreto                                 */
+/* ------------------------------------------------------------------------ */
+
+/* I(E_k) = dt^2 / (2 pi T n_good) sum_{j good} w_j | sum_{c=0}^{n_steps} a_j(c) e^{i E_k c dt} |^2
+ * with T = n_steps dt and E_k = E_min + k (E_max - E_min)/(n_E - 1).  The
+ * paper's (2 pi)^{-F} is carried by the weights (w_j = 1/|<p0 q0|chi>|^2 for
+ * Husimi samples).  amp: [n_traj][amp_ld]. */
+int or_spectrum(const double complex *amp, int64_t amp_ld, const double *w, const uint8_t *good,
+                int64_t n_traj, int32_t n_steps, double dt, double E_min, double E_max,
+                int32_t n_E, double *I_out, int64_t *n_good_out, int n_threads)
+{
+    int64_t n_good = 0;
+    for (int64_t j = 0; j < n_traj; ++j) n_good += good[j] ? 1 : 0;
+    if (n_good_out) *n_good_out = n_good;
+    const double T = n_steps * dt;
+    const double norm = n_good > 0 ? dt * dt / (OR_TWO_PI * T * (double)n_good) : 0.0;
+    const int K = n_steps + 1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel
+#endif
+    {
+        double complex *tw = malloc(sizeof(double complex) * K);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int k = 0; k < n_E; ++k) {
+            double E = n_E > 1 ? E_min + k * ((E_max - E_min) / (n_E - 1)) : E_min;
+            for (int c = 0; c < K; ++c) {
+                double ang = E * (c * dt);
+                tw[c] = cos(ang) + I * sin(ang);
+            }
+            double acc = 0.0;
+            for (int64_t j = 0; j < n_traj; ++j) {
+                if (!good[j]) continue;
+                double complex X = 0.0;
+                const double complex *a = amp + j * amp_ld;
+                for (int c = 0; c < K; ++c) X += a[c] * tw[c];
+                acc += w[j] * (creal(X) * creal(X) + cimag(X) * cimag(X));
+            }
+            I_out[k] = norm * acc;
+        }
+        free(tw);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Husimi sampling with a counter-based generator                            */
+/* ------------------------------------------------------------------------ */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+ * 4-word Philox S-box with multipliers 0xD2511F53, 0xCD9E8D57 and key
+ * schedule increments 0x9E3779B9, 0xBB67AE85. */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * x0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * x2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Standard normal number d (0 <= d < 2F) of trajectory j: Philox block d/4
+ * with counter (j_lo, j_hi, d/4, 0) and key (seed_lo, seed_hi); words (0,1)
+ * and (2,3) feed two Box-Muller pairs; uniforms are (u + 1/2) 2^-32. */
+static double or_normal(uint64_t seed, int64_t j, int d)
+{
+    uint32_t ctr[4] = { (uint32_t)j, (uint32_t)((uint64_t)j >> 32), (uint32_t)(d / 4), 0u };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t u[4];
+    or_philox4x32_10(ctr, key, u);
+    int pair = (d % 4) / 2, second = d % 2;
+    double u1 = ((double)u[2 * pair] + 0.5) * 0x1p-32;
+    double u2 = ((double)u[2 * pair + 1] + 0.5) * 0x1p-32;
+    double r = sqrt(-2.0 * log(u1));
+    return second ? r * sin(OR_TWO_PI * u2) : r * cos(OR_TWO_PI * u2);
+}
+
+/* Husimi samples around chi = |p_eq, q_eq>: q0_i = q_eq_i + z_i / sqrt(gamma_i),
+ * p0_i = p_eq_i + z_{F+i} sqrt(gamma_i), i.e. density |<p0 q0|chi>|^2 / (2 pi)^F,
+ * and weights w = 1 / |<p0 q0|chi>|^2.  p0, q0: [F][n_traj]; w: [n_traj]. */
+int or_sample_initial(int32_t F, const double *gamma, const double *p_eq, const double *q_eq,
+                      int64_t n_traj, uint64_t seed, double *p0, double *q0, double *w)
+{
+    for (int64_t j = 0; j < n_traj; ++j) {
+        double pj[64], qj[64];
+        for (int i = 0; i < F; ++i) {
+            qj[i] = q_eq[i] + or_normal(seed, j, i) / sqrt(gamma[i]);
+            pj[i] = p_eq[i] + or_normal(seed, j, F + i) * sqrt(gamma[i]);
+            q0[i * n_traj + j] = qj[i];
+            p0[i * n_traj + j] = pj[i];
+        }
+        double complex lo = or_log_overlap(F, gamma, pj, qj, p_eq, q_eq);
+        w[j] = exp(-2.0 * creal(lo));
+    }
+    return 0;
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,217 @@
+"""Pins of the oracle's propagation: integrator, monodromy, action, prefactor phase, amplitude.
+
+* Harmonic modes: the triple-jump step is a rotation by theta in coordinates
+  scaled by gamma_tilde, so Herman-Kluk with widths gamma_tilde is exact and
+  <chi|U^c|p0 q0> has a closed form in Glauber coherent-state algebra.  The
+  oracle's amplitude series (overlap, action, prefactor phase and its
+  unwrapping) must equal it to rounding.
+* Anharmonic surfaces: symplecticity M^T J M = J, energy conservation of
+  order dt^4, time reversal, finite-difference monodromy, order-4 convergence
+  and the generating-function identity dS = p_t dq_t - p_0 dq_0.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1312_4698_gb300 import workloads as wl
+from tests import closed_forms as cf
+
+
+def _J(F):
+    Z, I = np.zeros((F, F)), np.eye(F)
+    # ordering (p, q): dp/dt = -dH/dq, dq/dt = dH/dp
+    return np.block([[Z, -I], [I, Z]])
+
+
+@pytest.mark.parametrize("omegas", [[wl.cm1(1600.0)], wl.cm1([1600.0, 3650.0, 3750.0])])
+def test_harmonic_amplitude_closed_form(omegas):
+    omegas = np.atleast_1d(np.asarray(omegas, dtype=float))
+    F = omegas.size
+    dt, n_steps = 10.0, 1500
+    thetas, gts = zip(*[cf.harmonic_rotation(w, dt) for w in omegas])
+    gts = np.array(gts)
+    pes = wl.harmonic_pes(omegas)
+    p_eq, q_eq = np.sqrt(gts), np.zeros(F)
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        q0 = rng.normal(0, 1, F) / np.sqrt(gts)
+        p0 = p_eq + rng.normal(0, 1, F) * np.sqrt(gts)
+        r = oracle.propagate_one(pes, gts, p_eq, q_eq, dt, n_steps, p0, q0)
+        ref, th, _ = cf.harmonic_amplitude(omegas, dt, n_steps, p0, q0, p_eq, q_eq)
+        assert r["good"]
+        err = np.max(np.abs(r["amp"][0] - ref))
+        assert err < 1e-10, err
+        c = np.arange(n_steps + 1)
+        # continuous phase: theta_c = arg det A = -c sum_i theta_i, |det A| = 1
+        assert np.max(np.abs(r["theta"] - (-c * np.sum(th)))) < 1e-9
+        assert np.max(np.abs(np.abs(r["detA"]) - 1.0)) < 1e-12
+        assert np.max(np.abs(r["detM"] - 1.0)) < 1e-12
+        # action of a quadratic flow: S = (p q - p0 q0) / 2
+        assert abs(r["S"][-1] - 0.5 * np.sum(r["p"] * r["q"] - p0 * q0)) < 1e-10
+
+
+def test_harmonic_prefactor_limits_with_frequency_widths():
+    """With gamma = omega: |C_t| -> 1 and phi_t -> -sum omega t / 2 as dt -> 0 (O((omega dt)^4))."""
+    omegas = wl.cm1([1600.0, 3650.0])
+    pes = wl.harmonic_pes(omegas)
+    T = 4000.0
+    errs = []
+    for dt in (10.0, 5.0):
+        n = int(T / dt)
+        r = oracle.propagate_one(pes, omegas, np.sqrt(omegas), np.zeros(2), dt, n,
+                                 np.sqrt(omegas) + 0.01, np.array([1.0, -2.0]))
+        phi = 0.5 * r["theta"][-1]
+        errs.append((abs(abs(r["detA"][-1]) - 1.0), abs(phi + 0.5 * np.sum(omegas) * T)))
+    # fourth order: halving dt divides the modulus defect and the phase drift by ~16
+    assert errs[0][0] / errs[1][0] > 12
+    assert errs[0][1] / errs[1][1] > 12
+    assert errs[0][0] < 1e-3
+
+
+def _anharmonic(F=3, seed=1):
+    return wl.recipe_pes(F, np.random.default_rng(seed), sigma3=3e-8, sigma4=3e-9)
+
+
+def _start(pes, seed=2):
+    """A typical Husimi-like starting point (about one sigma from chi) for the surface's modes."""
+    rng = np.random.default_rng(seed)
+    om = pes.omega
+    z = rng.uniform(-1.0, 1.0, (2, pes.F))
+    return np.sqrt(om) * (1.0 + z[0]), z[1] / np.sqrt(om), om
+
+
+@pytest.mark.parametrize("F", [2, 3, 6])
+def test_monodromy_is_symplectic(F):
+    pes = _anharmonic(F)
+    p0, q0, om = _start(pes)
+    r = oracle.propagate_one(pes, om, np.sqrt(om), np.zeros(F), 10.0, 3000, p0, q0)
+    M = r["M"]
+    J = _J(F)
+    defect = np.max(np.abs(M.T @ J @ M - J)) / max(1.0, np.max(np.abs(M)) ** 2)
+    assert defect < 1e-10, defect
+    assert abs(r["detM"][-1] - 1.0) < 1e-9
+
+
+def _energy(pes, p, q):
+    return 0.5 * np.sum(p * p) + oracle.pes_eval(pes, q)[0]
+
+
+def test_energy_conservation_is_fourth_order():
+    F = 3
+    pes = _anharmonic(F)
+    p0, q0, om = _start(pes)
+    E0 = _energy(pes, p0, q0)
+    T = 20000.0
+    errs = []
+    for dt in (20.0, 10.0):
+        r = oracle.propagate_one(pes, om, np.sqrt(om), np.zeros(F), dt, int(T / dt), p0, q0)
+        errs.append(abs(_energy(pes, r["p"], r["q"]) - E0) / abs(E0))
+    assert errs[1] < 1e-5
+    assert errs[0] / errs[1] > 10.0, errs
+
+
+def test_time_reversal():
+    F = 3
+    pes = _anharmonic(F)
+    p0, q0, om = _start(pes)
+    chi = (np.sqrt(om), np.zeros(F))
+    fw = oracle.propagate_one(pes, om, *chi, 10.0, 2000, p0, q0)
+    bw = oracle.propagate_one(pes, om, *chi, 10.0, 2000, -fw["p"], fw["q"])
+    assert np.allclose(bw["q"], q0, rtol=0, atol=1e-9 * np.max(np.abs(q0)))
+    assert np.allclose(-bw["p"], p0, rtol=0, atol=1e-9 * np.max(np.abs(p0)))
+    assert abs(bw["S"][-1] - fw["S"][-1]) < 1e-9 * max(1.0, abs(fw["S"][-1]))
+
+
+def test_monodromy_matches_finite_differences():
+    F = 3
+    pes = _anharmonic(F)
+    p0, q0, om = _start(pes)
+    chi = (np.sqrt(om), np.zeros(F))
+    n = 800
+    r = oracle.propagate_one(pes, om, *chi, 10.0, n, p0, q0)
+    M_fd = np.zeros((2 * F, 2 * F))
+    for col in range(2 * F):
+        h = 1e-5 * (np.sqrt(om[col % F]) if col < F else 1.0 / np.sqrt(om[col % F]))
+        dp = np.zeros(F); dq = np.zeros(F)
+        (dp if col < F else dq)[col % F] = h
+        a = oracle.propagate_one(pes, om, *chi, 10.0, n, p0 + dp, q0 + dq)
+        b = oracle.propagate_one(pes, om, *chi, 10.0, n, p0 - dp, q0 - dq)
+        M_fd[:, col] = np.concatenate([a["p"] - b["p"], a["q"] - b["q"]]) / (2 * h)
+    rel = np.max(np.abs(M_fd - r["M"])) / np.max(np.abs(r["M"]))
+    assert rel < 1e-7, rel
+
+
+def test_fourth_order_convergence_of_the_flow():
+    F = 3
+    pes = _anharmonic(F)
+    p0, q0, om = _start(pes)
+    chi = (np.sqrt(om), np.zeros(F))
+    T = 3000.0
+    sols = []
+    for dt in (20.0, 10.0, 5.0):
+        r = oracle.propagate_one(pes, om, *chi, dt, int(round(T / dt)), p0, q0)
+        sols.append(np.concatenate([r["p"], r["q"]]))
+    e1 = np.max(np.abs(sols[0] - sols[1]))
+    e2 = np.max(np.abs(sols[1] - sols[2]))
+    assert 12.0 < e1 / e2 < 20.0, e1 / e2
+
+
+def test_action_is_a_generating_function():
+    """dS_T = p_T . dq_T - p_0 . dq_0 (holds exactly for compositions of exact sub-flows)."""
+    F = 3
+    pes = _anharmonic(F)
+    p0, q0, om = _start(pes)
+    chi = (np.sqrt(om), np.zeros(F))
+    n = 600
+    r = oracle.propagate_one(pes, om, *chi, 10.0, n, p0, q0)
+    M = r["M"]
+    Mqp, Mqq = M[F:, :F], M[F:, F:]
+    dS_dp0 = r["p"] @ Mqp
+    dS_dq0 = r["p"] @ Mqq - p0
+    for i in range(F):
+        for which, ref in (("p", dS_dp0[i]), ("q", dS_dq0[i])):
+            h = 1e-5 * (np.sqrt(om[i]) if which == "p" else 1 / np.sqrt(om[i]))
+            d = np.zeros(F); d[i] = h
+            if which == "p":
+                a = oracle.propagate_one(pes, om, *chi, 10.0, n, p0 + d, q0)
+                b = oracle.propagate_one(pes, om, *chi, 10.0, n, p0 - d, q0)
+            else:
+                a = oracle.propagate_one(pes, om, *chi, 10.0, n, p0, q0 + d)
+                b = oracle.propagate_one(pes, om, *chi, 10.0, n, p0, q0 - d)
+            fd = (a["S"][-1] - b["S"][-1]) / (2 * h)
+            assert abs(fd - ref) < 1e-6 * max(1.0, abs(ref)), (which, i, fd, ref)
+
+
+def test_stability_threshold_direction():
+    F = 3
+    pes = _anharmonic(F)
+    p0, q0, om = _start(pes)
+    chi = (np.sqrt(om), np.zeros(F))
+    assert oracle.propagate_one(pes, om, *chi, 10.0, 300, p0, q0, stab_tol=1.0)["good"]
+    # rounding alone moves det M off 1 by more than 1e-300
+    assert not oracle.propagate_one(pes, om, *chi, 10.0, 300, p0, q0, stab_tol=1e-300)["good"]
+
+
+def test_runaway_trajectory_is_flagged_bad():
+    # a strongly negative quartic coupling makes large-amplitude motion escape to infinity
+    F = 2
+    om = wl.cm1([1500.0, 2500.0])
+    pes = wl.morse_pes(om, 0.2, idx4=np.array([[0, 0, 1, 1]]), c4=np.array([-1e-3]))
+    r = oracle.propagate_one(pes, om, np.sqrt(om), np.zeros(F), 10.0, 400,
+                             np.array([2.0, 2.0]), np.array([5.0, 5.0]))
+    assert not r["good"]
+
+
+def test_batch_matches_single_and_chi_layout():
+    F = 3
+    pes = _anharmonic(F)
+    om = wl.cm1([1600.0, 3650.0, 3750.0])
+    p_eq = np.stack([np.sqrt(om), np.sqrt(3 * om)])
+    q_eq = np.zeros((2, F))
+    p0, q0, w = oracle.sample_initial(om, p_eq[0], q_eq[0], 7, 1)
+    amp, good = oracle.propagate(pes, om, p_eq, q_eq, 10.0, 50, p0, q0)
+    assert amp.shape == (2, 7, 51)
+    for j in range(7):
+        r = oracle.propagate_one(pes, om, p_eq, q_eq, 10.0, 50, p0[:, j], q0[:, j])
+        assert np.array_equal(r["amp"], amp[:, j, :], equal_nan=True)
+        assert r["good"] == bool(good[j])
