@@ -1,0 +1,379 @@
+"""Benchmark: TA-SC-IVR power spectrum, trajectory-steps/s and spectra/s.
+
+One step = one pass of the whole hot path over one batch: Husimi sampling
+of n_traj initial conditions, propagation of (p, q, S, M, prefactor phase,
+amplitudes) over n_steps, and the time -> energy transform with the weighted
+|.|^2 reduction into I(E).  Default workload: F = 6 (formaldehyde-sized)
+Morse + cubic + quartic surface, 16384 trajectories, 4000 steps of 10 au,
+4000 energies, FP64 propagation and FP64 Fourier step.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload f6|f3|f9]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+
+Multi-GPU (torchrun): weak scaling, every rank runs its own batch (seed
+base + rank); the per-rank spectra combine through one all-reduce of
+n_E + 1 numbers.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+from paper_1312_4698_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "trajectory-steps/s and spectra/s at ≤1 cm⁻¹ peak error vs FP64 oracle"
+L2_FLUSH_BYTES = 512 << 20
+FP64_PEAK_GFLOPS = 1250.0      # GB300 dense FP64 (nominal, CUDA cores and tensor cores alike)
+
+
+def workload(name: str, seed: int):
+    if name == "f3":
+        return wl.config_f3(seed=seed)
+    if name == "f6":
+        return wl.config_f6(seed=seed)
+    if name == "f9":
+        return wl.config_f9(seed=seed)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(w8, precision="fp64", ft="fp64"):
+    return (f"{w8.name}: F={w8.F}, {w8.n_traj} trajectories, {w8.n_steps} steps of {w8.dt} au, "
+            f"{w8.n_E} energies, propagation {precision}, Fourier step {ft}")
+
+
+def propagate_flops_per_traj_step(F: int, n3: int, n4: int) -> float:
+    """Algorithmic flops of one trajectory step (multiply-add = 2 flops).
+
+    3 kicks: potential (pair products P, cubic Hessian P*F and quartic
+    Hessian P*P multiply-adds, gradient and energy 2P each, Morse diagonal ~6F)
+    and the monodromy kick M_p -= tau H M_q (2F * F * F multiply-adds);
+    4 drifts: q and M_q (F + 2F*F multiply-adds) and the kinetic action (F);
+    det M by LU of 2F x 2F ((2/3)(2F)^3 flops), det A by complex LU of F x F
+    (8/3 F^3 real flops) plus building A (6 F^2), phase (~30) and the
+    amplitude per reference state (~10 F + 30)."""
+    P = F * (F + 1) // 2
+    pes = 2 * (P + (P * F if n3 else 0) + (P * P if n4 else 0) + 4 * P) + 6 * F
+    kick = pes + 2 * (2 * F * F * F) + 2 * F
+    drift = 2 * (F + 2 * F * F) + 2 * F
+    lu_m = (2.0 / 3.0) * (2 * F) ** 3
+    lu_a = (8.0 / 3.0) * F ** 3 + 6 * F * F
+    return 3 * kick + 4 * drift + lu_m + lu_a + 30 + 10 * F + 30
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_selector(local: int) -> str:
+    """nvidia-smi -i argument for torch device `local` (UUID when available)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[local].strip()
+    return str(local)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def run_cpu_oracle(w8, n_sample: int, threads: int):
+    """Time the oracle (as it stands) on the first n_sample trajectories of the workload."""
+    import oracle
+    oracle.build()
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, n_sample, w8.seed)
+    t0 = time.perf_counter()
+    amp, good = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0,
+                                 w8.stab_tol, threads)
+    t1 = time.perf_counter()
+    oracle.spectrum(amp[0], w, good, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, threads)
+    t2 = time.perf_counter()
+    used = threads if threads > 0 else oracle.max_threads()
+    return dict(seconds=t2 - t0, prop_s=t1 - t0, spec_s=t2 - t1, cores=used,
+                value=n_sample * w8.n_steps / (t2 - t0))
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w8 = workload(args.workload, 0)
+    n_sample = args.cpu_sample
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = run_cpu_oracle(w8, n_sample, 0)
+        if i >= args.warmup:
+            times.append(r)
+    sec = sum(t["seconds"] for t in times) / len(times)
+    value = n_sample * w8.n_steps / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "trajectory-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(w8), "sample": f"{n_sample} of {w8.n_traj} trajectories",
+                   "l2": "n/a (host)"},
+        "spectra_per_s": value / (w8.n_traj * w8.n_steps),
+        "cpu_baseline": {"value": value, "unit": "trajectory-steps/s", "cores": times[0]["cores"],
+                         "kind": "oracle",
+                         "sample": f"first {n_sample} of {w8.n_traj} trajectories, all {w8.n_steps} "
+                                   f"steps and {w8.n_E} energies; rate is linear in trajectories"},
+        "e2e": {"value": value, "unit": "trajectory-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="f6", choices=["f3", "f6", "f9"])
+    ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1312_4698_gb300 import scivr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w8 = workload(args.workload, seed=rank)        # weak scaling: one batch per rank
+    pes = scivr.scivr_create_pes(w8.pes)
+    bufs = scivr.alloc_buffers(w8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    K = w8.n_steps + 1
+    n = w8.n_traj
+
+    ev = {k: [] for k in ("prop0", "prop1", "spec1")}
+
+    def one_step(record):
+        scivr.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], n, w8.seed, bufs.p0,
+                                   bufs.q0, bufs.w, stream)
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True); e0.record(stream); ev["prop0"].append(e0)
+        scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0, bufs.q0,
+                              bufs.amp, K, bufs.good, stab_tol=w8.stab_tol, stream=stream)
+        if record:
+            e1 = torch.cuda.Event(enable_timing=True); e1.record(stream); ev["prop1"].append(e1)
+        scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min,
+                             w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, stream=stream)
+        if record:
+            e2 = torch.cuda.Event(enable_timing=True); e2.record(stream); ev["spec1"].append(e2)
+        if world > 1:
+            # combine spectra across ranks: sum of n_good * I and of n_good
+            v = torch.cat([bufs.I[0] * bufs.n_good.to(torch.float64), bufs.n_good.to(torch.float64)])
+            dist.all_reduce(v)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    scivr.launch_count(reset=True)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_selector(local)) as clk:
+        t_start.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            one_step(True)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    launches = scivr.launch_count(reset=True)
+    if world > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    prop_ms = [a.elapsed_time(b) for a, b in zip(ev["prop0"], ev["prop1"])]
+    spec_ms = [a.elapsed_time(b) for a, b in zip(ev["prop1"], ev["spec1"])]
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    n_good = int(bufs.n_good.item())
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hp0 = bufs.p0.cpu().pin_memory()
+        hq0 = bufs.q0.cpu().pin_memory()
+        hw = bufs.w.cpu().pin_memory()
+        hI = torch.empty(w8.n_E, dtype=torch.float64).pin_memory()
+        hng = torch.empty(1, dtype=torch.int64).pin_memory()
+        h2d = hp0.numel() * 8 + hq0.numel() * 8 + hw.numel() * 8
+        d2h = hI.numel() * 8 + 8
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            bufs.p0.copy_(hp0, non_blocking=True)
+            bufs.q0.copy_(hq0, non_blocking=True)
+            bufs.w.copy_(hw, non_blocking=True)
+            scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0,
+                                  bufs.q0, bufs.amp, K, bufs.good, stab_tol=w8.stab_tol, stream=stream)
+            scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min,
+                                 w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, stream=stream)
+            hI.copy_(bufs.I[0], non_blocking=True)
+            hng.copy_(bufs.n_good, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_ms = float(te.item()) / args.steps
+        e2e = {"value": world * n * w8.n_steps / (e2e_ms * 1e-3), "unit": "trajectory-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e2e_ms}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    value = world * n * w8.n_steps / (ms_per_step * 1e-3)
+    prop_avg = float(np.mean(prop_ms))
+    spec_avg = float(np.mean(spec_ms))
+    ft_flops = 8.0 * n * K * w8.n_E
+    pr_flops = propagate_flops_per_traj_step(w8.F, w8.pes.c3.size, w8.pes.c4.size) * n * w8.n_steps
+    ft_tf = ft_flops / (spec_avg * 1e-3) / 1e12
+    pr_tf = pr_flops / (prop_avg * 1e-3) / 1e12
+    peak_tf = FP64_PEAK_GFLOPS / 1e3
+    if spec_avg >= prop_avg:
+        roof = {"kernel": "k_ft_fp64 (scivr_spectrum)", "bound": "alu", "achieved": ft_tf,
+                "peak": peak_tf, "unit": "TFLOP/s", "frac": ft_tf / peak_tf, "traffic": None,
+                "peak_source": "GB300 nominal dense FP64 (profiling recipe table); no measured FP64 peak"}
+    else:
+        roof = {"kernel": "k_propagate (scivr_propagate)", "bound": "alu", "achieved": pr_tf,
+                "peak": peak_tf, "unit": "TFLOP/s", "frac": pr_tf / peak_tf, "traffic": None,
+                "peak_source": "GB300 nominal dense FP64 (profiling recipe table); no measured FP64 peak"}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        r = run_cpu_oracle(w8, args.cpu_sample, 0)
+        cpu = {"value": r["value"], "unit": "trajectory-steps/s", "cores": r["cores"],
+               "kind": "oracle",
+               "sample": f"first {args.cpu_sample} of {n} trajectories, all {w8.n_steps} steps and "
+                         f"{w8.n_E} energies ({r['seconds']:.1f} s); rate is linear in trajectories"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": describe(w8), "global_batch": world * n, "seed": "base 0 + rank",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); amplitudes "
+                         f"({n * K * 16 / 1e9:.2f} GB) exceed L2",
+                   "parallelism": f"replicas x{world}"},
+        "spectra_per_s": world / (ms_per_step * 1e-3),
+        "propagate_ms": prop_avg, "spectrum_ms": spec_avg, "n_good": n_good,
+        "propagate_tflops": pr_tf, "spectrum_tflops": ft_tf,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

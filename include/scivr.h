@@ -1,0 +1,187 @@
+/*
+ * scivr.h -- C ABI of libscivr: GB300 (sm_103a) time-averaged semiclassical
+ * initial-value-representation (TA-SC-IVR) power spectra.
+ *
+ * Method: Tamascelli, Dambrosio, Conte, Ceotto, arXiv:1312.4698.  The
+ * library evaluates the Monte Carlo estimate of the separable-approximation
+ * spectral density (Eq. sep_approx) in the discrete form of Eq. I(E)_discreto:
+ *
+ *   I(E_k) = dt^2 / (2 pi T n_good) * sum_{j good} w_j
+ *            | sum_{c=0}^{n_steps} <chi|p_j(c dt), q_j(c dt)> e^{i (S_j(c dt) + E_k c dt + phi_j(c dt))} |^2
+ *
+ * with T = n_steps dt, Husimi-sampled initial conditions (Sec. III.A), a
+ * fourth-order symplectic integrator, the Herman-Kluk prefactor phase phi_t
+ * (Eq. prefactor) and the stability filter |det(M^T M) - 1| > tol (Sec. II).
+ *
+ * Conventions for every entry point:
+ *   - atomic units, hbar = 1, mass-weighted normal coordinates (masses 1);
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device, allocated and owned by the caller; "host" pointers are ordinary
+ *     memory, read during the call and not retained;
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream); all work is
+ *     enqueued asynchronously on it; no call synchronises the device unless
+ *     stated;
+ *   - every call returns a scivr_status; on failure nothing (or nothing
+ *     further) is enqueued and scivr_last_error() describes the cause.
+ *     Argument checks happen before any launch and return SCIVR_EINVAL.
+ *     Launch or runtime failures return SCIVR_ECUDA.
+ */
+#ifndef SCIVR_H
+#define SCIVR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SCIVR_OK = 0,
+    SCIVR_EINVAL = -1,        /* invalid argument (shape, range, null pointer) */
+    SCIVR_ENOMEM = -2,        /* device allocation failed */
+    SCIVR_ECUDA = -3,         /* CUDA launch or runtime error */
+    SCIVR_ETIMEOUT = -4,      /* a bounded device-side wait expired */
+    SCIVR_EUNSUPPORTED = -5   /* valid request this build does not implement */
+} scivr_status;
+
+/* Diagonal part of the potential. */
+enum { SCIVR_DIAG_HARMONIC = 0,   /* omega_i^2 q_i^2 / 2 */
+       SCIVR_DIAG_MORSE = 1 };    /* D_i (1 - exp(-a_i q_i))^2 */
+
+/* Potential kinds. */
+enum { SCIVR_PES_POLY = 0 };      /* diagonal + cubic + quartic coupling monomials */
+
+/* Arithmetic of the propagation. */
+enum { SCIVR_FP64 = 0,            /* everything in IEEE double */
+       SCIVR_MIXED = 1 };         /* monodromy + potential in FP32; p, q, S,
+                                     prefactor determinant and phase in FP64 */
+
+/* Arithmetic of the time -> energy Fourier step. */
+enum { SCIVR_FT_FP64 = 0 };       /* FP64 fused-multiply-add contraction */
+
+#define SCIVR_MAX_F 24            /* largest number of modes */
+#define SCIVR_MAX_CHI 8           /* largest number of reference states per call */
+
+typedef struct scivr_pes_s *scivr_pes;   /* opaque, library-owned */
+
+/* Potential energy surface, V(q) = sum_i diag_i(q_i)
+ *                                 + sum_m c3[m] q_i q_j q_k      (i <= j <= k = idx3[3m..3m+2])
+ *                                 + sum_m c4[m] q_i q_j q_k q_l  (i <= j <= k <= l = idx4[4m..4m+3]).
+ * The paper's molecules use analytic fitted surfaces (Sec. IV); the
+ * Morse-diagonal form is its H2 potential and uncoupled-oscillator study.
+ * All arrays are host memory, copied by scivr_create_pes. */
+typedef struct {
+    int32_t F;              /* number of modes, 1..SCIVR_MAX_F */
+    int32_t kind;           /* SCIVR_PES_POLY */
+    int32_t diag_kind;      /* SCIVR_DIAG_HARMONIC or SCIVR_DIAG_MORSE */
+    const double *omega;    /* [F] harmonic frequencies (> 0) */
+    const double *D;        /* [F] Morse depths (> 0; ignored for harmonic) */
+    const double *a;        /* [F] Morse range parameters (> 0; ignored for harmonic) */
+    int32_t n3;             /* number of cubic monomials (>= 0) */
+    const int32_t *idx3;    /* [n3 * 3], each triple sorted, entries in [0, F) */
+    const double *c3;       /* [n3] */
+    int32_t n4;             /* number of quartic monomials (>= 0) */
+    const int32_t *idx4;    /* [n4 * 4], each quadruple sorted, entries in [0, F) */
+    const double *c4;       /* [n4] */
+} scivr_pes_desc;
+
+/* Propagation parameters (host memory, read during the call). */
+typedef struct {
+    double dt;              /* time step (> 0) */
+    int32_t n_steps;        /* steps to T = n_steps dt (>= 1); K = n_steps + 1 samples */
+    int32_t precision;      /* SCIVR_FP64 or SCIVR_MIXED */
+    double stab_tol;        /* trajectory is bad once |det(M)^2 - 1| > stab_tol (paper: 1e-6) */
+    const double *gamma;    /* [F] coherent-state widths (> 0) */
+    const double *p_eq;     /* [n_chi * F] reference-state momenta */
+    const double *q_eq;     /* [n_chi * F] reference-state positions */
+    int32_t n_chi;          /* number of reference states, 1..SCIVR_MAX_CHI */
+} scivr_prop_params;
+
+/* Optional final-state outputs of scivr_propagate (device pointers, each may be NULL). */
+typedef struct {
+    double *p;              /* [F][n_traj] momenta at T */
+    double *q;              /* [F][n_traj] positions at T */
+    double *S;              /* [n_traj] classical action at T */
+    double *theta;          /* [n_traj] continuous arg det A at T (phi_T = theta / 2) */
+    double *detM;           /* [n_traj] det M at T */
+    double *detA;           /* [n_traj][2] det A at T (re, im) */
+    double *M;              /* [n_traj][2F][2F] monodromy at T, rows (p, q), columns (p0, q0) */
+} scivr_final_state;
+
+/* Create a potential from a descriptor (Sec. IV potentials; see scivr_pes_desc).
+ * Allocates device memory on the current device.  *out receives the handle.
+ * Errors: SCIVR_EINVAL (F out of range, non-positive omega/D/a, unsorted or
+ * out-of-range monomial indices, NULL arrays with nonzero counts),
+ * SCIVR_ENOMEM, SCIVR_ECUDA. */
+int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out);
+
+/* Release a potential created by scivr_create_pes (synchronises the device
+ * so that no launch still reads it).  NULL is accepted. */
+int scivr_destroy_pes(scivr_pes pes);
+
+/* Number of modes of a potential (0 for NULL). */
+int32_t scivr_pes_modes(scivr_pes pes);
+
+/* Husimi sampling of initial conditions (Sec. III.A, after Eq. I(E)_discreto):
+ * q0_i = q_eq_i + z_i / sqrt(gamma_i), p0_i = p_eq_i + z_{F+i} sqrt(gamma_i),
+ * with z standard normal, i.e. the density |<p0 q0|chi>|^2 / (2 pi)^F around
+ * chi = |p_eq, q_eq>, and weights w = 1 / |<p0 q0|chi>|^2 (this carries the
+ * paper's (2 pi)^-F).  Normal z_d of trajectory j comes from Philox4x32-10
+ * (counter (j mod 2^32, j / 2^32, d / 4, 0), key (seed mod 2^32, seed / 2^32))
+ * and Box-Muller on words (0,1) and (2,3) with uniforms (u + 1/2) 2^-32.
+ * gamma, p_eq, q_eq: host [F].  p0, q0: device [F][n_traj]; w: device [n_traj].
+ * Errors: SCIVR_EINVAL (NULL pointers, n_traj < 1, gamma <= 0). */
+int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
+                         const double *q_eq, int64_t n_traj, uint64_t seed,
+                         double *p0, double *q0, double *w, void *stream);
+
+/* Propagate n_traj trajectories from (p0, q0) to T = n_steps dt and record, for
+ * every reference state x and step c = 0..n_steps, the amplitude
+ *   amp[x][j][c] = <chi_x|p_j(c dt), q_j(c dt)> exp(i (S_j(c dt) + phi_j(c dt)))
+ * (the summand of Eq. I(E)_discreto without the energy factor).  Integrator:
+ * Yoshida's fourth-order triple jump of exact drift/kick sub-flows for (p, q),
+ * the action S and the monodromy M (Sec. III.A).  phi = theta/2 with theta the
+ * continuous arg det A of the Herman-Kluk matrix (Eq. prefactor), unwrapped
+ * per step relative to the reference rotation exp(-i sum_i gamma_i t).  A
+ * trajectory is marked bad (good[j] = 0) once |det(M)^2 - 1| > stab_tol or any
+ * state value is not finite (Sec. II, Sec. III.B); bad trajectories are still
+ * propagated to T and their amplitudes are unspecified.
+ * p0, q0: device [F][n_traj].  amp: device complex double (re, im interleaved)
+ * [n_chi][n_traj][amp_ld], amp_ld >= n_steps + 1, 16-byte aligned.  good:
+ * device [n_traj].  fin: host struct of optional device outputs (NULL = none).
+ * Errors: SCIVR_EINVAL (NULL pointers, n_traj < 1, n_steps < 1, dt <= 0,
+ * gamma <= 0, amp_ld too small, F mismatch, n_chi out of range),
+ * SCIVR_EUNSUPPORTED (precision not built for this F). */
+int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
+                    const double *p0, const double *q0, void *amp, int64_t amp_ld,
+                    uint8_t *good, const scivr_final_state *fin, void *stream);
+
+/* Time-averaged spectrum of one reference state, Eq. I(E)_discreto:
+ *   I(E_k) = dt^2 / (2 pi T n_good) sum_{j: good[j] != 0} w_j | sum_{c=0}^{n_steps} amp[j][c] e^{i E_k c dt} |^2
+ * with E_k = E_min + k (E_max - E_min) / (n_E - 1), k = 0..n_E-1 (endpoints
+ * included, Sec. III.A) and T = n_steps dt.  Bad trajectories contribute
+ * nothing, whatever their amplitudes hold.  If n_good = 0, I is all zeros.
+ * amp: device complex double [n_traj][amp_ld] (amp_prec = SCIVR_FP64).  w:
+ * device [n_traj].  good: device [n_traj].  I_out: device [n_E].  n_good_out:
+ * device int64 (may be NULL).  Allocates stream-ordered scratch
+ * (cudaMallocAsync) of about 16 (n_steps+1) n_E + 8 n_E ceil(n_traj/64) bytes.
+ * Errors: SCIVR_EINVAL (NULL pointers, n_traj < 1, n_steps < 1, n_E < 2,
+ * E_max <= E_min, dt <= 0, amp_ld < n_steps + 1), SCIVR_EUNSUPPORTED
+ * (amp_prec or ft_mode not built), SCIVR_ENOMEM. */
+int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const double *w,
+                   const uint8_t *good, int64_t n_traj, int32_t n_steps, double dt,
+                   double E_min, double E_max, int32_t n_E, int32_t ft_mode,
+                   double *I_out, int64_t *n_good_out, void *stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *scivr_last_error(void);
+
+/* Number of kernel launches this library has enqueued on the calling thread
+ * since the counter was last reset (for launch accounting in benchmarks). */
+int64_t scivr_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCIVR_H */

@@ -1,0 +1,79 @@
+// Internal declarations shared by the libscivr translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "scivr.h"
+
+namespace scivr {
+
+// Device-resident potential.  The coupling polynomial is stored in the
+// Hessian-generating form used by the kernels:
+//   H3[a][b] = sum_k T3[k][e(a,b)] q_k,          (cubic part of the Hessian)
+//   H4[a][b] = sum_{k<=l} T4[e(k,l)][e(a,b)] q_k q_l   (quartic part)
+// with e(a,b) the packed index of the upper triangle (a <= b).  By Euler's
+// theorem for homogeneous polynomials, grad V3 = H3 q / 2, V3 = q.H3 q / 6,
+// grad V4 = H4 q / 3 and V4 = q.H4 q / 12, so one pass over the packed
+// Hessian entries yields V, grad V and H.
+struct PesDev {
+    int F, P, diag_kind;
+    int has3, has4;
+    const double *omega, *D, *a;     // [F]
+    const double *T3;                // [F][P]
+    const double *T4;                // [P][P]
+    const float *T3f, *T4f;          // FP32 copies for the mixed-precision path
+};
+
+// Kernel-side propagation parameters, passed by value.
+struct PropArgs {
+    int F, n_steps, n_chi, precision;
+    double dt, stab_tol, ref_step;   // ref_step = sum_i gamma_i dt
+    double cdrift[4], dkick[3];      // triple-jump fractions of dt
+    double gamma[SCIVR_MAX_F];
+    double rg[SCIVR_MAX_F];          // sqrt(gamma)
+    double irg[SCIVR_MAX_F];         // 1 / sqrt(gamma)
+    double qw[SCIVR_MAX_F];          // gamma / 4
+    double pw[SCIVR_MAX_F];          // 1 / (4 gamma)
+    double p_eq[SCIVR_MAX_CHI * SCIVR_MAX_F];
+    double q_eq[SCIVR_MAX_CHI * SCIVR_MAX_F];
+};
+
+struct FinalDev {
+    double *p, *q, *S, *theta, *detM, *detA, *M;
+};
+
+struct PropLaunch {
+    PesDev pes;
+    PropArgs args;
+    int64_t n_traj;
+    const double *p0, *q0;
+    double2 *amp;
+    int64_t amp_ld, chi_stride;
+    uint8_t *good;
+    FinalDev fin;
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_propagate(const PropLaunch &L, cudaStream_t s, int *n_launch);
+cudaError_t launch_sample(int F, const double *gamma, const double *p_eq, const double *q_eq,
+                          int64_t n_traj, uint64_t seed, double *p0, double *q0, double *w,
+                          cudaStream_t s, int *n_launch);
+cudaError_t launch_spectrum_fp64(const double2 *amp, int64_t amp_ld, const double *w,
+                                 const uint8_t *good, int64_t n_traj, int n_steps, double dt,
+                                 double E_min, double E_max, int n_E, double *I_out,
+                                 int64_t *n_good_out, void *scratch, cudaStream_t s,
+                                 int *n_launch);
+size_t spectrum_fp64_scratch_bytes(int64_t n_traj, int n_steps, int n_E);
+
+bool propagate_supported(int F, int precision);
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kInvTwoPi = 0.15915494309189533576888376337251;
+
+}  // namespace scivr
+
+struct scivr_pes_s {
+    scivr::PesDev dev;
+    void *blob;          // single device allocation holding all arrays
+};

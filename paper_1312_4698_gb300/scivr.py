@@ -1,0 +1,248 @@
+"""ctypes binding of libscivr (include/scivr.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libscivr.so.  PyTorch supplies device memory and the current
+stream.  Importing this module loads the library and raises ImportError if
+it has not been built (``paper_1312_4698_gb300.build.build()``); there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+SCIVR_OK = 0
+SCIVR_EINVAL = -1
+SCIVR_ENOMEM = -2
+SCIVR_ECUDA = -3
+SCIVR_ETIMEOUT = -4
+SCIVR_EUNSUPPORTED = -5
+
+SCIVR_DIAG_HARMONIC = 0
+SCIVR_DIAG_MORSE = 1
+SCIVR_PES_POLY = 0
+SCIVR_FP64 = 0
+SCIVR_MIXED = 1
+SCIVR_FT_FP64 = 0
+SCIVR_MAX_F = 24
+SCIVR_MAX_CHI = 8
+
+if not os.path.exists(_build.LIB):
+    raise ImportError(f"libscivr.so is not built ({_build.LIB}); run "
+                      "paper_1312_4698_gb300.build.build() on a machine with nvcc")
+
+_lib = C.CDLL(_build.LIB)
+LIBRARY_PATH = _build.LIB
+
+
+class ScivrError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where} failed with status {code}: {last_error()}")
+
+
+class scivr_pes_desc(C.Structure):
+    _fields_ = [("F", C.c_int32), ("kind", C.c_int32), ("diag_kind", C.c_int32),
+                ("omega", C.c_void_p), ("D", C.c_void_p), ("a", C.c_void_p),
+                ("n3", C.c_int32), ("idx3", C.c_void_p), ("c3", C.c_void_p),
+                ("n4", C.c_int32), ("idx4", C.c_void_p), ("c4", C.c_void_p)]
+
+
+class scivr_prop_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("n_steps", C.c_int32), ("precision", C.c_int32),
+                ("stab_tol", C.c_double), ("gamma", C.c_void_p), ("p_eq", C.c_void_p),
+                ("q_eq", C.c_void_p), ("n_chi", C.c_int32)]
+
+
+class scivr_final_state(C.Structure):
+    _fields_ = [("p", C.c_void_p), ("q", C.c_void_p), ("S", C.c_void_p), ("theta", C.c_void_p),
+                ("detM", C.c_void_p), ("detA", C.c_void_p), ("M", C.c_void_p)]
+
+
+_vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_lib.scivr_create_pes.argtypes = [C.POINTER(scivr_pes_desc), C.POINTER(_vp)]
+_lib.scivr_create_pes.restype = C.c_int
+_lib.scivr_destroy_pes.argtypes = [_vp]
+_lib.scivr_destroy_pes.restype = C.c_int
+_lib.scivr_pes_modes.argtypes = [_vp]
+_lib.scivr_pes_modes.restype = _i32
+_lib.scivr_sample_initial.argtypes = [_vp, _vp, _vp, _vp, _i64, C.c_uint64, _vp, _vp, _vp, _vp]
+_lib.scivr_sample_initial.restype = C.c_int
+_lib.scivr_propagate.argtypes = [_vp, C.POINTER(scivr_prop_params), _i64, _vp, _vp, _vp, _i64,
+                                 _vp, C.POINTER(scivr_final_state), _vp]
+_lib.scivr_propagate.restype = C.c_int
+_lib.scivr_spectrum.argtypes = [_vp, _i64, _i32, _vp, _vp, _i64, _i32, _d, _d, _d, _i32, _i32,
+                                _vp, _vp, _vp]
+_lib.scivr_spectrum.restype = C.c_int
+_lib.scivr_last_error.argtypes = []
+_lib.scivr_last_error.restype = C.c_char_p
+_lib.scivr_launch_count.argtypes = [C.c_int]
+_lib.scivr_launch_count.restype = _i64
+
+EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_sample_initial",
+            "scivr_propagate", "scivr_spectrum", "scivr_last_error", "scivr_launch_count"]
+
+
+def last_error() -> str:
+    return _lib.scivr_last_error().decode()
+
+
+def launch_count(reset: bool = False) -> int:
+    return int(_lib.scivr_launch_count(1 if reset else 0))
+
+
+def _check(code, where):
+    if code != SCIVR_OK:
+        raise ScivrError(code, where)
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Pes:
+    """Owning handle of a scivr_pes (destroyed with the object)."""
+
+    def __init__(self, handle: int, F: int):
+        self.handle = handle
+        self.F = F
+
+    def close(self):
+        if self.handle:
+            _lib.scivr_destroy_pes(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scivr_create_pes(desc) -> Pes:
+    """desc: workloads.PesDesc-like object (F, diag_kind, omega, D, a, idx3, c3, idx4, c4)."""
+    keep = [_f64(desc.omega), _f64(desc.D), _f64(desc.a),
+            np.ascontiguousarray(desc.idx3, dtype=np.int32), _f64(desc.c3),
+            np.ascontiguousarray(desc.idx4, dtype=np.int32), _f64(desc.c4)]
+    om, D, a, i3, c3, i4, c4 = keep
+    d = scivr_pes_desc(int(desc.F), SCIVR_PES_POLY, int(desc.diag_kind), om.ctypes.data,
+                       D.ctypes.data, a.ctypes.data, c3.size, i3.ctypes.data if c3.size else None,
+                       c3.ctypes.data if c3.size else None, c4.size,
+                       i4.ctypes.data if c4.size else None, c4.ctypes.data if c4.size else None)
+    h = _vp()
+    _check(_lib.scivr_create_pes(C.byref(d), C.byref(h)), "scivr_create_pes")
+    return Pes(h.value, int(desc.F))
+
+
+create_pes = scivr_create_pes
+
+
+def scivr_sample_initial(pes: Pes, gamma, p_eq, q_eq, n_traj, seed, p0, q0, w, stream=None):
+    g, pe, qe = _f64(gamma), _f64(p_eq), _f64(q_eq)
+    _check(_lib.scivr_sample_initial(pes.handle, g.ctypes.data, pe.ctypes.data, qe.ctypes.data,
+                                     int(n_traj), C.c_uint64(int(seed)), _ptr(p0), _ptr(q0),
+                                     _ptr(w), _stream(stream)), "scivr_sample_initial")
+
+
+sample_initial = scivr_sample_initial
+
+
+def scivr_propagate(pes: Pes, dt, n_steps, gamma, p_eq, q_eq, n_traj, p0, q0, amp, amp_ld, good,
+                    precision=SCIVR_FP64, stab_tol=1e-6, fin: Optional[dict] = None, stream=None):
+    """p_eq, q_eq: [n_chi, F] host arrays.  fin: optional dict of device tensors."""
+    g = _f64(gamma)
+    pe = _f64(np.atleast_2d(p_eq))
+    qe = _f64(np.atleast_2d(q_eq))
+    prm = scivr_prop_params(float(dt), int(n_steps), int(precision), float(stab_tol),
+                            g.ctypes.data, pe.ctypes.data, qe.ctypes.data, pe.shape[0])
+    fs = None
+    if fin:
+        fs = scivr_final_state(*[_ptr(fin.get(k)) for k in ("p", "q", "S", "theta", "detM", "detA", "M")])
+    _check(_lib.scivr_propagate(pes.handle, C.byref(prm), int(n_traj), _ptr(p0), _ptr(q0), _ptr(amp),
+                                int(amp_ld), _ptr(good), C.byref(fs) if fs is not None else None,
+                                _stream(stream)), "scivr_propagate")
+
+
+propagate = scivr_propagate
+
+
+def scivr_spectrum(amp, amp_ld, w, good, n_traj, n_steps, dt, E_min, E_max, n_E, I_out,
+                   n_good_out=None, amp_prec=SCIVR_FP64, ft_mode=SCIVR_FT_FP64, stream=None):
+    _check(_lib.scivr_spectrum(_ptr(amp), int(amp_ld), int(amp_prec), _ptr(w), _ptr(good),
+                               int(n_traj), int(n_steps), float(dt), float(E_min), float(E_max),
+                               int(n_E), int(ft_mode), _ptr(I_out), _ptr(n_good_out),
+                               _stream(stream)), "scivr_spectrum")
+
+
+spectrum = scivr_spectrum
+
+
+# --------------------------------------------------------------------------
+# Convenience: allocate outputs with torch and run the whole path on a workload
+# --------------------------------------------------------------------------
+
+@dataclass
+class Buffers:
+    p0: "object"
+    q0: "object"
+    w: "object"
+    amp: "object"
+    good: "object"
+    I: "object"
+    n_good: "object"
+
+
+def alloc_buffers(wl, device="cuda", n_traj=None):
+    import torch
+    n = wl.n_traj if n_traj is None else n_traj
+    K = wl.n_steps + 1
+    return Buffers(
+        p0=torch.empty((wl.F, n), dtype=torch.float64, device=device),
+        q0=torch.empty((wl.F, n), dtype=torch.float64, device=device),
+        w=torch.empty(n, dtype=torch.float64, device=device),
+        amp=torch.empty((wl.n_chi, n, K, 2), dtype=torch.float64, device=device),
+        good=torch.empty(n, dtype=torch.uint8, device=device),
+        I=torch.empty((wl.n_chi, wl.n_E), dtype=torch.float64, device=device),
+        n_good=torch.zeros(1, dtype=torch.int64, device=device),
+    )
+
+
+def run_spectrum_path(pes: Pes, wl, bufs: Buffers, sample=True, precision=SCIVR_FP64,
+                      ft_mode=SCIVR_FT_FP64, stream=None):
+    """sample (optional) -> propagate -> spectrum for every reference state, all on the GPU."""
+    n = bufs.w.shape[0]
+    K = wl.n_steps + 1
+    if sample:
+        scivr_sample_initial(pes, wl.gamma, wl.p_eq[0], wl.q_eq[0], n, wl.seed, bufs.p0, bufs.q0,
+                             bufs.w, stream)
+    scivr_propagate(pes, wl.dt, wl.n_steps, wl.gamma, wl.p_eq, wl.q_eq, n, bufs.p0, bufs.q0,
+                    bufs.amp, K, bufs.good, precision=precision, stab_tol=wl.stab_tol, stream=stream)
+    for x in range(wl.n_chi):
+        scivr_spectrum(bufs.amp[x], K, bufs.w, bufs.good, n, wl.n_steps, wl.dt, wl.E_min, wl.E_max,
+                       wl.n_E, bufs.I[x], bufs.n_good, ft_mode=ft_mode, stream=stream)

@@ -1,0 +1,265 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Inputs come from the oracle's sampler or from numpy; nothing the oracle
+consumes or is compared with comes from the CUDA path.
+
+Tolerances (FP64 path): rounding differs between the two implementations
+(fused multiply-adds, summation order, libm vs CUDA transcendental
+functions, reciprocal-multiply instead of division in the LU), so values are
+compared with bounds derived from error growth along a trajectory:
+amplitudes to 1e-9 of the trajectory's largest amplitude, spectra to 1e-9
+relative in the max norm, peak positions to 0.1 cm^-1.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1312_4698_gb300 import workloads as wl
+from tests import closed_forms as cf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    from paper_1312_4698_gb300 import scivr
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return scivr
+
+
+def _t(x, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda", dtype=dtype)
+
+
+def gpu_propagate(G, w8, p0, q0, precision=0, fin=False):
+    import torch
+    F, n = p0.shape
+    K = w8.n_steps + 1
+    pes = G.scivr_create_pes(w8.pes)
+    amp = torch.empty((w8.n_chi, n, K, 2), dtype=torch.float64, device="cuda")
+    good = torch.empty(n, dtype=torch.uint8, device="cuda")
+    fd = None
+    if fin:
+        fd = dict(p=torch.empty((F, n), dtype=torch.float64, device="cuda"),
+                  q=torch.empty((F, n), dtype=torch.float64, device="cuda"),
+                  S=torch.empty(n, dtype=torch.float64, device="cuda"),
+                  theta=torch.empty(n, dtype=torch.float64, device="cuda"),
+                  detM=torch.empty(n, dtype=torch.float64, device="cuda"),
+                  detA=torch.empty((n, 2), dtype=torch.float64, device="cuda"),
+                  M=torch.empty((n, 2 * F, 2 * F), dtype=torch.float64, device="cuda"))
+    G.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, _t(p0), _t(q0), amp, K,
+                      good, precision=precision, stab_tol=w8.stab_tol, fin=fd)
+    torch.cuda.synchronize()
+    a = amp.cpu().numpy()
+    a = a[..., 0] + 1j * a[..., 1]
+    out = dict(amp=a, good=good.cpu().numpy())
+    if fin:
+        out.update({k: v.cpu().numpy() for k, v in fd.items()})
+    return out
+
+
+def gpu_spectrum(G, amp, w, good, n_steps, dt, E_min, E_max, n_E):
+    import torch
+    n, K = amp.shape
+    a = np.stack([amp.real, amp.imag], axis=-1)
+    I = torch.empty(n_E, dtype=torch.float64, device="cuda")
+    ng = torch.zeros(1, dtype=torch.int64, device="cuda")
+    G.scivr_spectrum(_t(a), K, _t(w), _t(good.astype(np.uint8)), n, n_steps, dt, E_min, E_max, n_E, I, ng)
+    torch.cuda.synchronize()
+    return I.cpu().numpy(), int(ng.cpu().item())
+
+
+def amp_err(a, b, good):
+    """Max over good trajectories of |a - b| / max_c |b|."""
+    sel = good.astype(bool)
+    if not sel.any():
+        return 0.0
+    scale = np.max(np.abs(b[..., sel, :]), axis=-1, keepdims=True)
+    return float(np.max(np.abs(a[..., sel, :] - b[..., sel, :]) / scale))
+
+
+def test_sampler_matches_oracle(G):
+    import torch
+    w8 = wl.config_f6(n_traj=1000)
+    n = 1000
+    pes = G.scivr_create_pes(w8.pes)
+    p0 = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    q0 = torch.empty_like(p0)
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    G.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], n, 12345, p0, q0, w)
+    torch.cuda.synchronize()
+    rp, rq, rw = oracle.sample_initial(w8.gamma, w8.p_eq[0], w8.q_eq[0], n, 12345)
+    assert np.allclose(p0.cpu().numpy(), rp, rtol=1e-13, atol=1e-15)
+    assert np.allclose(q0.cpu().numpy(), rq, rtol=1e-13, atol=1e-13)
+    assert np.allclose(w.cpu().numpy(), rw, rtol=1e-12)
+
+
+@pytest.mark.parametrize("F", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+def test_propagate_matches_oracle_small(G, F):
+    """Every supported F; 70 trajectories (ragged w.r.t. any block size)."""
+    if F == 3:
+        w8 = wl.config_f3(n_traj=70, n_steps=300)
+    else:
+        w8 = wl.config_generic(F, seed=F, n_traj=70, n_steps=300)
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, 11)
+    ra, rg, rf = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0,
+                                  final=True)
+    g = gpu_propagate(G, w8, p0, q0, fin=True)
+    assert np.array_equal(g["good"], rg)
+    assert amp_err(g["amp"], ra, rg) < 1e-9
+    sel = rg.astype(bool)
+    assert np.allclose(g["p"][:, sel], rf["p"].T[:, sel], rtol=1e-9, atol=1e-12)
+    assert np.allclose(g["q"][:, sel], rf["q"].T[:, sel], rtol=1e-9, atol=1e-9)
+    assert np.allclose(g["S"][sel], rf["S"][sel], rtol=1e-9, atol=1e-9)
+    assert np.allclose(g["theta"][sel], rf["theta"][sel], rtol=1e-9, atol=1e-9)
+    assert np.allclose(g["M"][sel], rf["M"][sel], rtol=1e-8, atol=1e-8 * np.max(np.abs(rf["M"][sel])))
+    dA = g["detA"][:, 0] + 1j * g["detA"][:, 1]
+    assert np.allclose(dA[sel], rf["detA"][sel], rtol=1e-9)
+
+
+def test_propagate_several_reference_states(G):
+    w8 = wl.config_f3(n_traj=33, n_steps=200)
+    om = w8.gamma
+    w8 = w8.with_(p_eq=np.stack([np.sqrt(om), np.sqrt(3 * om), -np.sqrt(om)]),
+                  q_eq=np.stack([np.zeros(3), np.zeros(3), np.array([1.0, -2.0, 0.5])]))
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq[0], w8.q_eq[0], w8.n_traj, 5)
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0)
+    g = gpu_propagate(G, w8, p0, q0)
+    assert g["amp"].shape == (3, 33, 201)
+    assert amp_err(g["amp"], ra, rg) < 1e-9
+
+
+def test_propagate_harmonic_closed_form(G):
+    """GPU amplitudes against the Glauber closed form directly (not via the oracle)."""
+    omegas = wl.cm1([1600.0, 3650.0, 3750.0])
+    dt, n_steps = 10.0, 800
+    gts = np.array([cf.harmonic_rotation(w, dt)[1] for w in omegas])
+    w8 = wl.Workload("harm", wl.harmonic_pes(omegas), gts, np.sqrt(gts)[None], np.zeros((1, 3)),
+                     5, n_steps, dt, 0.0, 0.1, 10, 0)
+    rng = np.random.default_rng(9)
+    q0 = rng.normal(0, 1, (3, 5)) / np.sqrt(gts)[:, None]
+    p0 = np.sqrt(gts)[:, None] * (1 + rng.normal(0, 1, (3, 5)))
+    g = gpu_propagate(G, w8, p0, q0)
+    assert g["good"].all()
+    for j in range(5):
+        ref, _, _ = cf.harmonic_amplitude(omegas, dt, n_steps, p0[:, j], q0[:, j], np.sqrt(gts), np.zeros(3))
+        assert np.max(np.abs(g["amp"][0, j] - ref)) < 1e-10
+
+
+def test_bad_trajectories_flagged_like_the_oracle(G):
+    """Strong couplings: a mix of escaping (non-finite) and stable trajectories."""
+    w8 = wl.config_generic(6, seed=1, n_traj=96, n_steps=500)
+    rng = np.random.default_rng(1)
+    w8.pes = wl.recipe_pes(6, rng, sigma3=1e-7, sigma4=1e-8)   # mass-weighted: many escape
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, 2)
+    p0[0, 5] = np.nan    # injected non-finite initial condition -> bad, not a fault
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0)
+    g = gpu_propagate(G, w8, p0, q0)
+    assert 0 < rg.sum() < rg.size
+    assert g["good"][5] == 0 and rg[5] == 0
+    assert np.array_equal(g["good"], rg)
+    assert amp_err(g["amp"], ra, rg) < 1e-9
+
+
+@pytest.mark.parametrize("n,n_steps,n_E", [(1, 1, 2), (130, 50, 77), (64, 15, 64), (257, 100, 130)])
+def test_spectrum_matches_oracle_random_amplitudes(G, n, n_steps, n_E):
+    rng = np.random.default_rng(n + n_steps)
+    K = n_steps + 1
+    amp = (rng.normal(size=(n, K)) + 1j * rng.normal(size=(n, K))) * 0.3
+    w = rng.uniform(0.2, 5.0, n)
+    good = (rng.uniform(size=n) > 0.2).astype(np.uint8)
+    good[0] = 1
+    bad = np.flatnonzero(good == 0)
+    if bad.size:
+        amp[bad[0], 3 % K] = np.nan          # bad rows must not leak NaN
+    dt, E_min, E_max = 10.0, 0.001, 0.06
+    ri, rng_ = oracle.spectrum(amp, w, good, n_steps, dt, E_min, E_max, n_E)
+    gi, gng = gpu_spectrum(G, amp, w, good, n_steps, dt, E_min, E_max, n_E)
+    assert gng == rng_
+    assert np.max(np.abs(gi - ri)) <= 1e-12 * np.max(np.abs(ri))
+
+
+def test_spectrum_all_bad_is_zero(G):
+    amp = np.ones((5, 11), dtype=complex)
+    gi, ng = gpu_spectrum(G, amp, np.ones(5), np.zeros(5, np.uint8), 10, 10.0, 0.0, 0.1, 9)
+    assert ng == 0 and np.all(gi == 0.0)
+
+
+def _full_path(G, w8, p0, q0, w):
+    import torch
+    n = p0.shape[1]
+    K = w8.n_steps + 1
+    pes = G.scivr_create_pes(w8.pes)
+    bufs = G.alloc_buffers(w8, n_traj=n)
+    bufs.p0.copy_(_t(p0))
+    bufs.q0.copy_(_t(q0))
+    bufs.w.copy_(_t(w))
+    G.run_spectrum_path(pes, w8, bufs, sample=False)
+    torch.cuda.synchronize()
+    return bufs
+
+
+def test_config_f3_full_spectrum_matches_oracle(G):
+    """F=3 workload at its full size: 1024 trajectories, 3000 steps, 2000 energies."""
+    w8 = wl.config_f3()
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, w8.seed)
+    ref = oracle.run_workload(w8, p0, q0, w)
+    bufs = _full_path(G, w8, p0, q0, w)
+    gi = bufs.I[0].cpu().numpy()
+    assert int(bufs.n_good.item()) == ref["n_good"]
+    assert np.array_equal(bufs.good.cpu().numpy(), ref["good"])
+    rel = np.max(np.abs(gi - ref["I"][0])) / np.max(np.abs(ref["I"][0]))
+    assert rel <= 1e-9, rel
+    E = w8.energies()
+    pr = wl.to_cm1(cf.find_peaks(E, ref["I"][0]))
+    pg = wl.to_cm1(cf.find_peaks(E, gi))
+    assert len(pr) == len(pg) and len(pr) > 0
+    assert np.max(np.abs(pr - pg)) <= 0.1
+
+
+def test_config_f6_full_size_sampled(G):
+    """F=6 workload at its full size and launch shape (16384 trajectories, 4000
+    steps, 4000 energies): amplitude rows of sampled trajectories against the
+    oracle, and the spectrum of that sample (selected through the good mask)."""
+    import torch
+    w8 = wl.config_f6()
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, w8.seed)
+    bufs = _full_path(G, w8, p0, q0, w)
+    idx = np.sort(np.random.default_rng(0).choice(w8.n_traj, 24, replace=False))
+    idx[-1] = w8.n_traj - 1   # the ragged last block
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps,
+                              p0[:, idx], q0[:, idx])
+    ga = bufs.amp[0, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    ga = ga[..., 0] + 1j * ga[..., 1]
+    gg = bufs.good.cpu().numpy()
+    assert np.array_equal(gg[idx], rg)
+    assert amp_err(ga[None], ra, rg) < 1e-9
+    # spectrum of the sampled trajectories only, through the full-size launch
+    mask = torch.zeros(w8.n_traj, dtype=torch.uint8, device="cuda")
+    mask[torch.as_tensor(idx, device="cuda")] = 1
+    sub_good = bufs.good * mask
+    I = torch.empty(w8.n_E, dtype=torch.float64, device="cuda")
+    ng = torch.zeros(1, dtype=torch.int64, device="cuda")
+    G.scivr_spectrum(bufs.amp[0], w8.n_steps + 1, bufs.w, sub_good, w8.n_traj, w8.n_steps, w8.dt,
+                     w8.E_min, w8.E_max, w8.n_E, I, ng)
+    torch.cuda.synchronize()
+    ri, rng_ = oracle.spectrum(ra[0], w[idx], rg, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E)
+    assert int(ng.item()) == rng_
+    gi = I.cpu().numpy()
+    assert np.max(np.abs(gi - ri)) <= 1e-9 * np.max(np.abs(ri))
+    # the whole-set spectrum is the n_good-weighted mean of the two halves' spectra
+    half = torch.zeros_like(mask)
+    half[: w8.n_traj // 2] = 1
+    parts = []
+    for msk in (half, 1 - half):
+        Ih = torch.empty_like(I)
+        ngh = torch.zeros_like(ng)
+        G.scivr_spectrum(bufs.amp[0], w8.n_steps + 1, bufs.w, bufs.good * msk, w8.n_traj,
+                         w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, Ih, ngh)
+        parts.append((Ih, ngh))
+    torch.cuda.synchronize()
+    comb = sum(Ih.cpu().numpy() * int(ngh.item()) for Ih, ngh in parts) / int(bufs.n_good.item())
+    full = bufs.I[0].cpu().numpy()
+    assert np.max(np.abs(comb - full)) <= 1e-12 * np.max(full)
