@@ -106,6 +106,8 @@ typedef struct {
     double *detM;           /* [n_traj] det M at T */
     double *detA;           /* [n_traj][2] det A at T (re, im) */
     double *M;              /* [n_traj][2F][2F] monodromy at T, rows (p, q), columns (p0, q0) */
+    double *stab;           /* [n_traj] max over steps of |det(M)^2 - 1| (+inf once not finite);
+                               the stability measure the good flag thresholds */
 } scivr_final_state;
 
 /* Create a potential from a descriptor (Sec. IV potentials; see scivr_pes_desc).

@@ -64,7 +64,8 @@ class _Cplx(C.Structure):
 
 class _Final(C.Structure):
     _fields_ = [("p", C.c_void_p), ("q", C.c_void_p), ("S", C.c_void_p), ("theta", C.c_void_p),
-                ("detM", C.c_void_p), ("detA", C.c_void_p), ("M", C.c_void_p)]
+                ("detM", C.c_void_p), ("detA", C.c_void_p), ("M", C.c_void_p),
+                ("stab", C.c_void_p)]
 
 
 def _load():
@@ -85,7 +86,7 @@ def _load():
             lib.or_propagate_one.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
             lib.or_propagate.restype = C.c_int
             lib.or_propagate.argtypes = [vp, vp, i64, vp, vp, vp, i64, vp,
-                                         vp, vp, vp, vp, vp, vp, vp, C.c_int]
+                                         vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
             lib.or_spectrum.restype = C.c_int
             lib.or_spectrum.argtypes = [vp, i64, vp, vp, i64, i32, d, d, d, i32, vp, vp, C.c_int]
             lib.or_philox4x32_10.restype = None
@@ -174,12 +175,13 @@ def propagate_one(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6):
     amp = np.zeros((n_chi, K), dtype=np.complex128)
     S = np.zeros(K); th = np.zeros(K); dA = np.zeros(K, dtype=np.complex128); dM = np.zeros(K)
     fp = np.zeros(F); fq = np.zeros(F); fS = np.zeros(1); fth = np.zeros(1); fdM = np.zeros(1)
-    fdA = np.zeros(1, dtype=np.complex128); fM = np.zeros((2 * F, 2 * F))
-    fin = _Final(_p(fp), _p(fq), _p(fS), _p(fth), _p(fdM), _p(fdA), _p(fM))
+    fdA = np.zeros(1, dtype=np.complex128); fM = np.zeros((2 * F, 2 * F)); fst = np.zeros(1)
+    fin = _Final(_p(fp), _p(fq), _p(fS), _p(fth), _p(fdM), _p(fdA), _p(fM), _p(fst))
     p0 = _f64(p0); q0 = _f64(q0)
     ok = lib.or_propagate_one(C.byref(P.s), C.byref(s), _p(p0), _p(q0), _p(amp), K,
                               C.byref(fin), _p(S), _p(th), _p(dA), _p(dM))
-    return dict(amp=amp, good=bool(ok), S=S, theta=th, detA=dA, detM=dM, p=fp, q=fq, M=fM)
+    return dict(amp=amp, good=bool(ok), S=S, theta=th, detA=dA, detM=dM, p=fp, q=fq, M=fM,
+                stab=float(fst[0]))
 
 
 def propagate(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6, n_threads=0,
@@ -202,10 +204,10 @@ def propagate(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6, n_thr
     if final:
         fin = dict(p=np.zeros((n, F)), q=np.zeros((n, F)), S=np.zeros(n), theta=np.zeros(n),
                    detM=np.zeros(n), detA=np.zeros(n, dtype=np.complex128),
-                   M=np.zeros((n, 2 * F, 2 * F)))
+                   M=np.zeros((n, 2 * F, 2 * F)), stab=np.zeros(n))
     g = (lambda k: _p(fin[k])) if final else (lambda k: None)
     lib.or_propagate(C.byref(P.s), C.byref(s), n, _p(p0), _p(q0), _p(amp), K, _p(good),
-                     g("p"), g("q"), g("S"), g("theta"), g("detM"), g("detA"), g("M"),
+                     g("p"), g("q"), g("S"), g("theta"), g("detM"), g("detA"), g("M"), g("stab"),
                      int(n_threads))
     return (amp, good, fin) if final else (amp, good)
 

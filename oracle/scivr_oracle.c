@@ -209,6 +209,7 @@ typedef struct {
     double *detM;           /* det M at T */
     double complex *detA;   /* det A at T */
     double *M;              /* [2F * 2F] at T, rows (p, q), columns (p0, q0) */
+    double *stab;           /* max over steps of |det(M)^2 - 1| (+inf once not finite) */
 } or_final;
 
 /* Yoshida (1990) fourth-order triple jump, written as position-Verlet
@@ -307,6 +308,7 @@ int or_propagate_one(const or_pes *pes, const or_prop *prm, const double *p0, co
     double ref_step = 0.0;
     for (int i = 0; i < F; ++i) ref_step += prm->gamma[i] * prm->dt;
     int good = 1;
+    double stab = 0.0;
 
     for (int step = 0; step <= prm->n_steps; ++step) {
         if (step > 0) {
@@ -322,7 +324,9 @@ int or_propagate_one(const or_pes *pes, const or_prop *prm, const double *p0, co
             /* stability monitor: |det(M^T M) - 1| = |det(M)^2 - 1| */
             memcpy(Mw, M, sizeof(double) * n * n);
             detM = or_det_real(n, Mw);
-            if (!isfinite(detM) || fabs(detM * detM - 1.0) > prm->stab_tol) good = 0;
+            double dev = isfinite(detM) ? fabs(detM * detM - 1.0) : INFINITY;
+            if (dev > stab) stab = dev;
+            if (dev > prm->stab_tol) good = 0;
 
             /* prefactor determinant and its continuous phase */
             or_prefactor_matrix(F, prm->gamma, M, A);
@@ -355,6 +359,7 @@ int or_propagate_one(const or_pes *pes, const or_prop *prm, const double *p0, co
         if (fin->detM) *fin->detM = detM;
         if (fin->detA) *fin->detA = detA;
         if (fin->M) memcpy(fin->M, M, sizeof(double) * n * n);
+        if (fin->stab) *fin->stab = stab;
     }
     free(p); free(q); free(M); free(Mw); free(g); free(H); free(A);
     return good;
@@ -363,11 +368,11 @@ int or_propagate_one(const or_pes *pes, const or_prop *prm, const double *p0, co
 /* Batch propagation.  p0, q0: [F][n_traj] (variable-major).  amp: complex
  * [n_chi][n_traj][amp_ld], amp_ld >= n_steps + 1.  good: [n_traj].  Optional
  * final-state arrays (may be NULL): fin_p, fin_q [n_traj][F]; fin_S, fin_theta,
- * fin_detM [n_traj]; fin_detA [n_traj]; fin_M [n_traj][2F][2F]. */
+ * fin_detM, fin_stab [n_traj]; fin_detA [n_traj]; fin_M [n_traj][2F][2F]. */
 int or_propagate(const or_pes *pes, const or_prop *prm, int64_t n_traj, const double *p0,
                  const double *q0, double complex *amp, int64_t amp_ld, uint8_t *good,
                  double *fin_p, double *fin_q, double *fin_S, double *fin_theta, double *fin_detM,
-                 double complex *fin_detA, double *fin_M, int n_threads)
+                 double complex *fin_detA, double *fin_M, double *fin_stab, int n_threads)
 {
     const int F = pes->F, n = 2 * F;
 #ifdef _OPENMP
@@ -381,7 +386,7 @@ int or_propagate(const or_pes *pes, const or_prop *prm, int64_t n_traj, const do
             fin_p ? fin_p + j * F : NULL, fin_q ? fin_q + j * F : NULL,
             fin_S ? fin_S + j : NULL, fin_theta ? fin_theta + j : NULL,
             fin_detM ? fin_detM + j : NULL, fin_detA ? fin_detA + j : NULL,
-            fin_M ? fin_M + j * n * n : NULL };
+            fin_M ? fin_M + j * n * n : NULL, fin_stab ? fin_stab + j : NULL };
         int ok = or_propagate_one(pes, prm, p_init, q_init, amp ? amp + j * amp_ld : NULL,
                                   n_traj * amp_ld, &fin, NULL, NULL, NULL, NULL);
         if (good) good[j] = (uint8_t)ok;

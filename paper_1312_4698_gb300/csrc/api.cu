@@ -285,7 +285,7 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
     L.amp_ld = amp_ld;
     L.chi_stride = n_traj * amp_ld;
     L.good = good;
-    if (fin) L.fin = FinalDev{fin->p, fin->q, fin->S, fin->theta, fin->detM, fin->detA, fin->M};
+    if (fin) L.fin = FinalDev{fin->p, fin->q, fin->S, fin->theta, fin->detM, fin->detA, fin->M, fin->stab};
     int nl = 0;
     cudaError_t e = launch_propagate(L, static_cast<cudaStream_t>(stream), &nl);
     g_launches += nl;

@@ -40,7 +40,7 @@ struct PropArgs {
 };
 
 struct FinalDev {
-    double *p, *q, *S, *theta, *detM, *detA, *M;
+    double *p, *q, *S, *theta, *detM, *detA, *M, *stab;
 };
 
 struct PropLaunch {

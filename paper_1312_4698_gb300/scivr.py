@@ -62,7 +62,8 @@ class scivr_prop_params(C.Structure):
 
 class scivr_final_state(C.Structure):
     _fields_ = [("p", C.c_void_p), ("q", C.c_void_p), ("S", C.c_void_p), ("theta", C.c_void_p),
-                ("detM", C.c_void_p), ("detA", C.c_void_p), ("M", C.c_void_p)]
+                ("detM", C.c_void_p), ("detA", C.c_void_p), ("M", C.c_void_p),
+                ("stab", C.c_void_p)]
 
 
 _vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
@@ -183,7 +184,8 @@ def scivr_propagate(pes: Pes, dt, n_steps, gamma, p_eq, q_eq, n_traj, p0, q0, am
                             g.ctypes.data, pe.ctypes.data, qe.ctypes.data, pe.shape[0])
     fs = None
     if fin:
-        fs = scivr_final_state(*[_ptr(fin.get(k)) for k in ("p", "q", "S", "theta", "detM", "detA", "M")])
+        fs = scivr_final_state(*[_ptr(fin.get(k)) for k in ("p", "q", "S", "theta", "detM", "detA", "M",
+                                                            "stab")])
     _check(_lib.scivr_propagate(pes.handle, C.byref(prm), int(n_traj), _ptr(p0), _ptr(q0), _ptr(amp),
                                 int(amp_ld), _ptr(good), C.byref(fs) if fs is not None else None,
                                 _stream(stream)), "scivr_propagate")
