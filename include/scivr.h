@@ -175,6 +175,29 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
                    double E_min, double E_max, int32_t n_E, int32_t ft_mode,
                    double *I_out, int64_t *n_good_out, void *stream);
 
+/* Same result as scivr_spectrum (same arguments, same checks) without allocating
+ * any device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc or cudaMallocAsync -- processes whose
+ * device memory is owned by another component's fixed pool or caching
+ * allocator, and latency-critical callers for which an allocation could block
+ * or fail under memory pressure.
+ *
+ * Its scratch (the good count and per-slice column sums) lives in one
+ * library-owned device array of 4 MiB (2^19 doubles) that every GPU which loads
+ * libscivr holds until the process exits.  Limit: n_E <= 524256; larger grids
+ * return SCIVR_EINVAL and launch nothing.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture begins.  All calls
+ * share the one array and overwrite what the previous call left there (nothing
+ * in it needs to start at zero), so calls that overlap on the GPU -- on
+ * different streams, or on different host threads -- race and must be
+ * serialised by the caller.  The caller still provides amp, w, good, I_out and
+ * n_good_out exactly as for scivr_spectrum. */
+int scivr_spectrum_noalloc(const void *amp, int64_t amp_ld, int32_t amp_prec, const double *w,
+                           const uint8_t *good, int64_t n_traj, int32_t n_steps, double dt,
+                           double E_min, double E_max, int32_t n_E, int32_t ft_mode,
+                           double *I_out, int64_t *n_good_out, void *stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *scivr_last_error(void);
 

@@ -326,4 +326,36 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
     return SCIVR_OK;
 }
 
+int scivr_spectrum_noalloc(const void *amp, int64_t amp_ld, int32_t amp_prec, const double *w,
+                           const uint8_t *good, int64_t n_traj, int32_t n_steps, double dt,
+                           double E_min, double E_max, int32_t n_E, int32_t ft_mode, double *I_out,
+                           int64_t *n_good_out, void *stream)
+{
+    if (!amp || !w || !good || !I_out) return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: NULL device pointer");
+    if (n_traj < 1) return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: n_traj=%lld < 1", (long long)n_traj);
+    if (n_steps < 1) return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: n_steps=%d < 1", n_steps);
+    if (n_E < 2) return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: n_E=%d < 2", n_E);
+    if (n_E > spectrum_noalloc_max_energies())
+        return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: n_E=%d exceeds the fixed scratch limit of %d energies",
+                    n_E, spectrum_noalloc_max_energies());
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: dt must be positive");
+    if (!std::isfinite(E_min) || !std::isfinite(E_max) || !(E_max > E_min))
+        return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: need finite E_min < E_max");
+    if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: amp_ld < n_steps+1");
+    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0)
+        return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: amp not 16-byte aligned");
+    if (amp_prec != SCIVR_FP64)
+        return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum_noalloc: amp_prec %d not supported", amp_prec);
+    if (ft_mode != SCIVR_FT_FP64)
+        return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum_noalloc: ft_mode %d not supported", ft_mode);
+    int nl = 0;
+    cudaError_t e = launch_spectrum_noalloc(static_cast<const double2 *>(amp), amp_ld, w, good, n_traj,
+                                            n_steps, dt, E_min, E_max, n_E, I_out, n_good_out,
+                                            static_cast<cudaStream_t>(stream), &nl);
+    g_launches += nl;
+    if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum_noalloc");
+    ok();
+    return SCIVR_OK;
+}
+
 }  // extern "C"

@@ -65,6 +65,11 @@ cudaError_t launch_spectrum_fp64(const double2 *amp, int64_t amp_ld, const doubl
                                  int64_t *n_good_out, void *scratch, cudaStream_t s,
                                  int *n_launch);
 size_t spectrum_fp64_scratch_bytes(int64_t n_traj, int n_steps, int n_E);
+cudaError_t launch_spectrum_noalloc(const double2 *amp, int64_t amp_ld, const double *w,
+                                    const uint8_t *good, int64_t n_traj, int n_steps, double dt,
+                                    double E_min, double E_max, int n_E, double *I_out,
+                                    int64_t *n_good_out, cudaStream_t s, int *n_launch);
+int spectrum_noalloc_max_energies();
 
 bool propagate_supported(int F, int precision);
 

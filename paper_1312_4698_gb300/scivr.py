@@ -81,13 +81,16 @@ _lib.scivr_propagate.restype = C.c_int
 _lib.scivr_spectrum.argtypes = [_vp, _i64, _i32, _vp, _vp, _i64, _i32, _d, _d, _d, _i32, _i32,
                                 _vp, _vp, _vp]
 _lib.scivr_spectrum.restype = C.c_int
+_lib.scivr_spectrum_noalloc.argtypes = list(_lib.scivr_spectrum.argtypes)
+_lib.scivr_spectrum_noalloc.restype = C.c_int
 _lib.scivr_last_error.argtypes = []
 _lib.scivr_last_error.restype = C.c_char_p
 _lib.scivr_launch_count.argtypes = [C.c_int]
 _lib.scivr_launch_count.restype = _i64
 
 EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_sample_initial",
-            "scivr_propagate", "scivr_spectrum", "scivr_last_error", "scivr_launch_count"]
+            "scivr_propagate", "scivr_spectrum", "scivr_spectrum_noalloc", "scivr_last_error",
+            "scivr_launch_count"]
 
 
 def last_error() -> str:
@@ -203,6 +206,15 @@ def scivr_spectrum(amp, amp_ld, w, good, n_traj, n_steps, dt, E_min, E_max, n_E,
 
 
 spectrum = scivr_spectrum
+
+
+def scivr_spectrum_noalloc(amp, amp_ld, w, good, n_traj, n_steps, dt, E_min, E_max, n_E, I_out,
+                           n_good_out=None, amp_prec=SCIVR_FP64, ft_mode=SCIVR_FT_FP64, stream=None):
+    """scivr_spectrum without device allocations (library-owned fixed scratch; calls must not overlap)."""
+    _check(_lib.scivr_spectrum_noalloc(_ptr(amp), int(amp_ld), int(amp_prec), _ptr(w), _ptr(good),
+                                       int(n_traj), int(n_steps), float(dt), float(E_min),
+                                       float(E_max), int(n_E), int(ft_mode), _ptr(I_out),
+                                       _ptr(n_good_out), _stream(stream)), "scivr_spectrum_noalloc")
 
 
 # --------------------------------------------------------------------------
