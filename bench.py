@@ -35,6 +35,11 @@ from paper_1312_4698_gb300 import workloads as wl  # noqa: E402
 METRIC = "trajectory-steps/s and spectra/s at ≤1 cm⁻¹ peak error vs FP64 oracle"
 L2_FLUSH_BYTES = 512 << 20
 FP64_PEAK_GFLOPS = 1250.0      # GB300 dense FP64 (nominal, CUDA cores and tensor cores alike)
+FP64_PEAK_NOTE = ("GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table); an FMA-chain "
+                  "probe on this pool measured 1.252 TFLOP/s")
+# dram read+write bytes per launch from ncu captures (profiles/), keyed by (kernel, workload);
+# scaled to the full launch where the capture used fewer trajectories
+TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9}
 
 
 def workload(name: str, seed: int):
@@ -45,6 +50,17 @@ def workload(name: str, seed: int):
     if name == "f9":
         return wl.config_f9(seed=seed)
     raise SystemExit(f"unknown workload {name}")
+
+
+def sized(w8, args):
+    kw = {}
+    if getattr(args, "n_traj", None):
+        kw["n_traj"] = args.n_traj
+    if getattr(args, "n_steps", None):
+        kw["n_steps"] = args.n_steps
+    if getattr(args, "n_E", None):
+        kw["n_E"] = args.n_E
+    return w8.with_(**kw) if kw else w8
 
 
 def describe(w8, precision="fp64", ft="fp64"):
@@ -171,7 +187,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w8 = workload(args.workload, 0)
+    w8 = sized(workload(args.workload, 0), args)
     n_sample = args.cpu_sample
     times = []
     for i in range(args.warmup + args.steps):
@@ -206,9 +222,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="f6", choices=["f3", "f6", "f9"])
-    ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--cpu-sample", type=int, default=768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-traj", type=int, default=None, help="override the workload's trajectory count")
+    ap.add_argument("--n-steps", type=int, default=None, help="override the workload's step count")
+    ap.add_argument("--n-E", type=int, default=None, help="override the workload's energy count")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -227,7 +246,7 @@ def main(argv=None):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w8 = workload(args.workload, seed=rank)        # weak scaling: one batch per rank
+    w8 = sized(workload(args.workload, seed=rank), args)   # weak scaling: one batch per rank
     pes = scivr.scivr_create_pes(w8.pes)
     bufs = scivr.alloc_buffers(w8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -335,13 +354,15 @@ def main(argv=None):
     pr_tf = pr_flops / (prop_avg * 1e-3) / 1e12
     peak_tf = FP64_PEAK_GFLOPS / 1e3
     if spec_avg >= prop_avg:
+        full = args.n_traj is None and args.n_steps is None and args.n_E is None
         roof = {"kernel": "k_ft_fp64 (scivr_spectrum)", "bound": "alu", "achieved": ft_tf,
-                "peak": peak_tf, "unit": "TFLOP/s", "frac": ft_tf / peak_tf, "traffic": None,
-                "peak_source": "GB300 nominal dense FP64 (profiling recipe table); no measured FP64 peak"}
+                "peak": peak_tf, "unit": "TFLOP/s", "frac": ft_tf / peak_tf,
+                "traffic": TRAFFIC.get(("k_ft_fp64", args.workload)) if full else None,
+                "peak_source": FP64_PEAK_NOTE}
     else:
         roof = {"kernel": "k_propagate (scivr_propagate)", "bound": "alu", "achieved": pr_tf,
                 "peak": peak_tf, "unit": "TFLOP/s", "frac": pr_tf / peak_tf, "traffic": None,
-                "peak_source": "GB300 nominal dense FP64 (profiling recipe table); no measured FP64 peak"}
+                "peak_source": FP64_PEAK_NOTE}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
