@@ -56,6 +56,11 @@ enum { SCIVR_FP64 = 0,            /* everything in IEEE double */
        SCIVR_MIXED = 1 };         /* monodromy + potential in FP32; p, q, S,
                                      prefactor determinant and phase in FP64 */
 
+/* Kernel schedule of scivr_propagate. */
+enum { SCIVR_KERNEL_AUTO = 0,     /* library choice (tuned per F, precision, n_traj) */
+       SCIVR_KERNEL_THREAD = 1,   /* one thread per trajectory */
+       SCIVR_KERNEL_GROUP = 2 };  /* a lane group per trajectory, batched FP64 determinants */
+
 /* Arithmetic of the time -> energy Fourier step. */
 enum { SCIVR_FT_FP64 = 0 };       /* FP64 fused-multiply-add contraction */
 
@@ -95,6 +100,7 @@ typedef struct {
     const double *p_eq;     /* [n_chi * F] reference-state momenta */
     const double *q_eq;     /* [n_chi * F] reference-state positions */
     int32_t n_chi;          /* number of reference states, 1..SCIVR_MAX_CHI */
+    int32_t kernel;         /* SCIVR_KERNEL_AUTO / _THREAD / _GROUP */
 } scivr_prop_params;
 
 /* Optional final-state outputs of scivr_propagate (device pointers, each may be NULL). */
@@ -151,9 +157,11 @@ int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
  * p0, q0: device [F][n_traj].  amp: device complex double (re, im interleaved)
  * [n_chi][n_traj][amp_ld], amp_ld >= n_steps + 1, 16-byte aligned.  good:
  * device [n_traj].  fin: host struct of optional device outputs (NULL = none).
+ * Precision SCIVR_MIXED keeps the monodromy, the potential and det M in FP32, so
+ * its det M deviation is FP32 rounding: give it a stab_tol scaled accordingly.
  * Errors: SCIVR_EINVAL (NULL pointers, n_traj < 1, n_steps < 1, dt <= 0,
  * gamma <= 0, amp_ld too small, F mismatch, n_chi out of range),
- * SCIVR_EUNSUPPORTED (precision not built for this F). */
+ * SCIVR_EUNSUPPORTED (precision or kernel not built for this F). */
 int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
                     const double *p0, const double *q0, void *amp, int64_t amp_ld,
                     uint8_t *good, const scivr_final_state *fin, void *stream);

@@ -250,8 +250,11 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
     if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "scivr_propagate: amp not 16-byte aligned");
     if (prm->precision != SCIVR_FP64 && prm->precision != SCIVR_MIXED)
         return fail(SCIVR_EINVAL, "scivr_propagate: precision %d invalid", prm->precision);
-    if (!propagate_supported(F, prm->precision))
-        return fail(SCIVR_EUNSUPPORTED, "scivr_propagate: precision %d not built for F=%d", prm->precision, F);
+    if (prm->kernel < SCIVR_KERNEL_AUTO || prm->kernel > SCIVR_KERNEL_GROUP)
+        return fail(SCIVR_EINVAL, "scivr_propagate: kernel %d invalid", prm->kernel);
+    if (!propagate_supported(F, prm->precision, prm->kernel))
+        return fail(SCIVR_EUNSUPPORTED, "scivr_propagate: precision %d / kernel %d not built for F=%d",
+                    prm->precision, prm->kernel, F);
 
     PropLaunch L{};
     L.pes = pes->dev;
@@ -260,6 +263,7 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
     A.n_steps = prm->n_steps;
     A.n_chi = prm->n_chi;
     A.precision = prm->precision;
+    A.kernel = prm->kernel;
     A.dt = prm->dt;
     A.stab_tol = prm->stab_tol;
     triple_jump(A.cdrift, A.dkick);

@@ -1,31 +1,63 @@
-// Propagation dispatch: picks the kernel instantiation for (F, precision).
+// Propagation dispatch: picks the kernel instantiation for (F, precision, schedule).
 #include "scivr_internal.cuh"
 
 namespace scivr {
 
 template <int F> cudaError_t launch_tpt_fp64(const PropLaunch &L, cudaStream_t s);
+template <int F> cudaError_t launch_group_mixed(const PropLaunch &L, cudaStream_t s);
+template <int F> cudaError_t launch_group_fp64(const PropLaunch &L, cudaStream_t s);
 
-bool propagate_supported(int F, int precision)
+namespace {
+
+constexpr int kMaxThreadF = 9;   // thread-per-trajectory FP64 kernel
+constexpr int kMaxGroupF = 8;    // lane-group kernels (2F <= 16 lanes)
+
+// Schedule choice when the caller leaves it to the library: the lane-group
+// kernel keeps every SM busy with few trajectories (it launches G lanes per
+// trajectory); the thread kernel wins in FP64 once there are enough
+// trajectories to fill the GPU with one warp per SM sub-partition.
+int choose(int F, int precision, int64_t n_traj)
 {
-    if (precision != SCIVR_FP64) return false;
-    return F >= 1 && F <= 9;
+    if (precision == SCIVR_MIXED) return SCIVR_KERNEL_GROUP;
+    if (F > kMaxGroupF) return SCIVR_KERNEL_THREAD;
+    return n_traj >= 16384 ? SCIVR_KERNEL_THREAD : SCIVR_KERNEL_GROUP;
 }
+
+}  // namespace
+
+bool propagate_supported(int F, int precision, int kernel)
+{
+    if (F < 1) return false;
+    if (precision == SCIVR_MIXED) return kernel != SCIVR_KERNEL_THREAD && F <= kMaxGroupF;
+    if (precision != SCIVR_FP64) return false;
+    if (kernel == SCIVR_KERNEL_THREAD) return F <= kMaxThreadF;
+    if (kernel == SCIVR_KERNEL_GROUP) return F <= kMaxGroupF;
+    return F <= kMaxThreadF;
+}
+
+#define SCIVR_CASES(M, X) \
+    case 1: return M<1>(X, s); case 2: return M<2>(X, s); case 3: return M<3>(X, s); \
+    case 4: return M<4>(X, s); case 5: return M<5>(X, s); case 6: return M<6>(X, s); \
+    case 7: return M<7>(X, s); case 8: return M<8>(X, s);
 
 cudaError_t launch_propagate(const PropLaunch &L, cudaStream_t s, int *n_launch)
 {
     *n_launch = 1;
-    switch (L.args.F) {
-    case 1: return launch_tpt_fp64<1>(L, s);
-    case 2: return launch_tpt_fp64<2>(L, s);
-    case 3: return launch_tpt_fp64<3>(L, s);
-    case 4: return launch_tpt_fp64<4>(L, s);
-    case 5: return launch_tpt_fp64<5>(L, s);
-    case 6: return launch_tpt_fp64<6>(L, s);
-    case 7: return launch_tpt_fp64<7>(L, s);
-    case 8: return launch_tpt_fp64<8>(L, s);
-    case 9: return launch_tpt_fp64<9>(L, s);
-    default: *n_launch = 0; return cudaErrorInvalidValue;
+    const int kern = L.args.kernel == SCIVR_KERNEL_AUTO ? choose(L.args.F, L.args.precision, L.n_traj)
+                                                          : L.args.kernel;
+    if (L.args.precision == SCIVR_MIXED) {
+        switch (L.args.F) { SCIVR_CASES(launch_group_mixed, L) default: break; }
+    } else if (kern == SCIVR_KERNEL_GROUP) {
+        switch (L.args.F) { SCIVR_CASES(launch_group_fp64, L) default: break; }
+    } else {
+        switch (L.args.F) {
+            SCIVR_CASES(launch_tpt_fp64, L)
+            case 9: return launch_tpt_fp64<9>(L, s);
+            default: break;
+        }
     }
+    *n_launch = 0;
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace scivr

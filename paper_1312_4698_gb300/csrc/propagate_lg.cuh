@@ -1,0 +1,457 @@
+// Lane-group propagation kernel (Sec. III.A / III.B of arXiv:1312.4698).
+//
+// A group of G lanes (G = 8, 16 or 32, 2F <= G) owns one trajectory; a warp
+// holds T = 32/G trajectories.  Work is split by what parallelises:
+//
+//   phase 1 (per step, group-parallel, arithmetic type Real):
+//     lane g < 2F owns column g of the monodromy matrix M (its p- and q-rows
+//     in registers); lane a < F owns mode a: p_a, q_a and the action
+//     partial sum in FP64.  The Hessian's packed entries e(a,b) are spread
+//     over the group; the tensors T3/T4 live in shared memory.  det M is an
+//     LU over the group's columns (pivot and multipliers by warp shuffle).
+//     The Herman-Kluk matrix A of the step is written to shared memory.
+//   phase 2 (once per G steps, job-parallel, FP64): lane j takes job j =
+//     (trajectory j / G, step j % G) and computes det A and its argument.
+//   phase 3: the continuous phase, a segmented prefix sum over each group.
+//   phase 4 (job-parallel, FP64): overlap <chi|p q>, action, phase and the
+//     amplitude; each group writes G consecutive samples of its row.
+//
+// Real = float is the mixed-precision path (monodromy, potential, det M and
+// A in FP32; p, q, S, det A, phase and amplitude in FP64); Real = double is
+// the same schedule in FP64 throughout.
+#pragma once
+
+#include <math_constants.h>
+
+#include "scivr_internal.cuh"
+
+namespace scivr {
+namespace lg {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <int F>
+__host__ __device__ constexpr int pidx(int a, int b)
+{
+    return a * F - a * (a - 1) / 2 + (b - a);
+}
+
+template <typename Real> __device__ __forceinline__ Real rexp(Real x);
+template <> __device__ __forceinline__ float rexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double rexp<double>(double x) { return exp(x); }
+
+template <typename Real> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
+template <int F, int G, typename Real>
+struct WarpShared {
+    static constexpr int P = F * (F + 1) / 2;
+    static constexpr int T = 32 / G;
+    double qd[T][F];
+    Real qr[T][F];
+    Real qq[T][P];
+    Real gc[T][P];
+    Real H[T][F][F];
+    typename Vec2<Real>::T A[F * F][32];   // prefactor matrix per job, entry-major
+    double pj[F][32], qj[F][32];           // state per job (for the overlap)
+    double Sj[32];                          // action per job
+};
+
+template <int F, int G, typename Real, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
+{
+    constexpr int N2 = 2 * F;
+    constexpr int P = F * (F + 1) / 2;
+    constexpr int T = 32 / G;
+    constexpr int C = G;                       // steps per chunk: T * C = 32 jobs
+    constexpr int EPL = (P + G - 1) / G;       // packed Hessian entries per lane
+    static_assert(N2 <= G, "group must hold all 2F columns");
+    using Sh = WarpShared<F, G, Real>;
+    using R2 = typename Vec2<Real>::T;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *sT3 = reinterpret_cast<Real *>(smem_raw);
+    Real *sT4 = sT3 + F * P;
+    size_t off = ((sizeof(Real) * (F * P + P * P)) + 15) & ~(size_t)15;
+    Sh *wsh_all = reinterpret_cast<Sh *>(smem_raw + off);
+
+    const PesDev &pes = L.pes;
+    const PropArgs &A = L.args;
+    const bool use3 = pes.has3, use4 = pes.has4;
+    // stage the coupling tensors once per CTA
+    {
+        const Real *g3 = nullptr, *g4 = nullptr;
+        if constexpr (sizeof(Real) == 4) { g3 = reinterpret_cast<const Real *>(pes.T3f); g4 = reinterpret_cast<const Real *>(pes.T4f); }
+        else { g3 = reinterpret_cast<const Real *>(pes.T3); g4 = reinterpret_cast<const Real *>(pes.T4); }
+        for (int i = threadIdx.x; i < F * P; i += blockDim.x) sT3[i] = use3 ? g3[i] : Real(0);
+        for (int i = threadIdx.x; i < P * P; i += blockDim.x) sT4[i] = use4 ? g4[i] : Real(0);
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    const int t = ln / G, g = ln % G, base = t * G;
+    Sh &sh = wsh_all[warp];
+    const int64_t n = L.n_traj;
+    const int64_t j_traj = ((int64_t)blockIdx.x * WARPS + warp) * T + t;
+    const bool active = j_traj < n;
+    const int64_t jl = active ? j_traj : n - 1;
+
+    // packed entries handled by this lane
+    int ea[EPL], eb[EPL];
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+        int e = g + i * G, a = 0;
+        if (e >= P) e = 0;
+        while (e >= F - a) { e -= F - a; ++a; }
+        ea[i] = a;
+        eb[i] = a + e;
+    }
+
+    // mode state (lane g < F)
+    const int mode = g < F ? g : 0;
+    double p = L.p0[mode * n + jl], q = L.q0[mode * n + jl];
+    double Spart = 0.0;
+    // column state (lane g < 2F): column g of M = d(p,q)/d(p0,q0)
+    Real Mp[F], Mq[F];
+#pragma unroll
+    for (int a = 0; a < F; ++a) {
+        Mp[a] = (g < F && a == g) ? Real(1) : Real(0);
+        Mq[a] = (g >= F && g < N2 && a == g - F) ? Real(1) : Real(0);
+    }
+    bool good = true;
+    double stab = 0.0, detM_last = 1.0;
+    double theta_last = 0.0, arg_last = 0.0;
+    double2 detA_last = make_double2(1.0, 0.0);
+
+    // amplitude at c = 0 (M = I, S = 0, theta = 0): lane 0 of each group
+    if (g == 0 && active) {
+        for (int x = 0; x < A.n_chi; ++x) {
+            double re = 0.0, im = 0.0;
+            for (int a = 0; a < F; ++a) {
+                const double pa = L.p0[a * n + jl], qa = L.q0[a * n + jl];
+                const double dq = A.q_eq[x * F + a] - qa, dp = A.p_eq[x * F + a] - pa;
+                re = fma(-A.qw[a] * dq, dq, re);
+                re = fma(-A.pw[a] * dp, dp, re);
+                im = fma(0.5 * (A.p_eq[x * F + a] + pa), dq, im);
+            }
+            double sn, cs;
+            sincos(im, &sn, &cs);
+            const double mag = exp(re);
+            L.amp[x * L.chi_stride + jl * L.amp_ld] = make_double2(mag * cs, mag * sn);
+        }
+    }
+
+    const Real rdt = (Real)A.dt;
+    for (int step0 = 0; step0 < A.n_steps; step0 += C) {
+        const int cnt = min(C, A.n_steps - step0);
+        // ---------------- phase 1: cnt steps, group-parallel ----------------
+        for (int c = 0; c < cnt; ++c) {
+#pragma unroll
+            for (int sub = 0; sub < 4; ++sub) {
+                // drift
+                {
+                    const double tau = A.cdrift[sub] * A.dt;
+                    if (g < F) {
+                        Spart = fma(tau * 0.5 * p, p, Spart);
+                        q = fma(tau, p, q);
+                    }
+                    const Real rt = (Real)A.cdrift[sub] * rdt;
+#pragma unroll
+                    for (int a = 0; a < F; ++a) Mq[a] = fma(rt, Mp[a], Mq[a]);
+                }
+                if (sub == 3) break;
+                // kick: potential at q
+                const double tk = A.dkick[sub] * A.dt;
+                const Real rtk = (Real)A.dkick[sub] * rdt;
+                __syncwarp();   // previous kick's readers of qr/H are done
+                if (g < F) {
+                    sh.qd[t][g] = q;
+                    sh.qr[t][g] = (Real)q;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < EPL; ++i) {
+                    const int e = g + i * G;
+                    if (e < P) sh.qq[t][e] = sh.qr[t][ea[i]] * sh.qr[t][eb[i]];
+                }
+                __syncwarp();
+                Real vpart = Real(0);
+#pragma unroll
+                for (int i = 0; i < EPL; ++i) {
+                    const int e = g + i * G;
+                    if (e < P) {
+                        Real h3 = Real(0), h4 = Real(0);
+                        if (use3) {
+#pragma unroll
+                            for (int k = 0; k < F; ++k) h3 = fma(sT3[k * P + e], sh.qr[t][k], h3);
+                        }
+                        if (use4) {
+#pragma unroll 8
+                            for (int kl = 0; kl < P; ++kl) h4 = fma(sT4[kl * P + e], sh.qq[t][kl], h4);
+                        }
+                        const int a = ea[i], b = eb[i];
+                        Real hd = Real(0);
+                        if (a == b) {
+                            if (pes.diag_kind == SCIVR_DIAG_MORSE) {
+                                const Real Dm = (Real)__ldg(pes.D + a), am = (Real)__ldg(pes.a + a);
+                                const Real u = rexp<Real>(-am * sh.qr[t][a]);
+                                hd = Real(2) * Dm * am * am * u * (Real(2) * u - Real(1));
+                            } else {
+                                const Real w = (Real)__ldg(pes.omega + a);
+                                hd = w * w;
+                            }
+                        }
+                        const Real h = h3 + h4;
+                        sh.H[t][a][b] = h + hd;
+                        sh.H[t][b][a] = h + hd;
+                        sh.gc[t][e] = fma(Real(0.5), h3, h4 * Real(1.0 / 3.0));
+                        const Real vc = fma(Real(1.0 / 6.0), h3, h4 * Real(1.0 / 12.0));
+                        vpart = fma(a == b ? vc : Real(2) * vc, sh.qq[t][e], vpart);
+                    }
+                }
+                __syncwarp();
+                // gradient, p and action (mode lanes)
+                double vlane = (double)vpart;
+                if (g < F) {
+                    Real gr = Real(0);
+#pragma unroll
+                    for (int b = 0; b < F; ++b) {
+                        const int e = g <= b ? g * F - g * (g - 1) / 2 + (b - g) : b * F - b * (b - 1) / 2 + (g - b);
+                        gr = fma(sh.gc[t][e], sh.qr[t][b], gr);
+                    }
+                    Real Vd, gd;
+                    if (pes.diag_kind == SCIVR_DIAG_MORSE) {
+                        const Real Dm = (Real)__ldg(pes.D + g), am = (Real)__ldg(pes.a + g);
+                        const Real u = rexp<Real>(-am * sh.qr[t][g]);
+                        const Real omu = Real(1) - u;
+                        Vd = Dm * omu * omu;
+                        gd = Real(2) * Dm * am * u * omu;
+                    } else {
+                        const Real w = (Real)__ldg(pes.omega + g);
+                        Vd = Real(0.5) * w * w * sh.qr[t][g] * sh.qr[t][g];
+                        gd = w * w * sh.qr[t][g];
+                    }
+                    p = fma(-tk, (double)(gr + gd), p);
+                    vlane += (double)Vd;
+                }
+                Spart = fma(-tk, vlane, Spart);
+                // monodromy kick: M_p -= tau H M_q (column lanes)
+#pragma unroll
+                for (int a = 0; a < F; ++a) {
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int b = 0; b < F; ++b) acc = fma(sh.H[t][a][b], Mq[b], acc);
+                    Mp[a] = fma(-rtk, acc, Mp[a]);
+                }
+            }
+            // ---- stability: det M by LU over the group's columns ----
+            {
+                Real W[N2];
+#pragma unroll
+                for (int a = 0; a < F; ++a) { W[a] = Mp[a]; W[F + a] = Mq[a]; }
+                Real det = Real(1);
+#pragma unroll
+                for (int k = 0; k < N2; ++k) {
+                    int piv = k;
+                    Real best = fabs(W[k]);
+#pragma unroll
+                    for (int i = k + 1; i < N2; ++i)
+                        if (fabs(W[i]) > best) { best = fabs(W[i]); piv = i; }
+                    piv = __shfl_sync(FULL, piv, base + k);
+                    Real wp = W[k];
+#pragma unroll
+                    for (int i = k + 1; i < N2; ++i) wp = (i == piv) ? W[i] : wp;
+#pragma unroll
+                    for (int i = k + 1; i < N2; ++i) W[i] = (i == piv) ? W[k] : W[i];
+                    W[k] = wp;
+                    const Real pk = __shfl_sync(FULL, W[k], base + k);
+                    det *= (piv != k) ? -pk : pk;
+                    const Real inv = Real(1) / pk;
+#pragma unroll
+                    for (int i = k + 1; i < N2; ++i) {
+                        const Real li = __shfl_sync(FULL, W[i], base + k) * inv;
+                        if (g > k) W[i] = fma(-li, W[k], W[i]);
+                    }
+                }
+                const double dd = (double)det;
+                const double dev = isfinite(dd) ? fabs(fma(dd, dd, -1.0)) : CUDART_INF;
+                stab = dev > stab ? dev : stab;
+                if (dev > A.stab_tol) good = false;
+                detM_last = dd;
+            }
+            // ---- Herman-Kluk matrix column b = g (needs column F + b) ----
+            {
+                const int src = base + F + (g < F ? g : 0);
+                const int job = t * C + c;
+#pragma unroll
+                for (int a = 0; a < F; ++a) {
+                    const Real mpq = __shfl_sync(FULL, Mp[a], src);
+                    const Real mqq = __shfl_sync(FULL, Mq[a], src);
+                    if (g < F) {
+                        const Real rga = (Real)A.rg[a], irga = (Real)A.irg[a];
+                        const Real rgb = (Real)A.rg[g], irgb = (Real)A.irg[g];
+                        const Real re = fma(rga * irgb, mqq, (rgb * irga) * Mp[a]);
+                        const Real im = fma(-(rga * rgb), Mq[a], (irga * irgb) * mpq);
+                        R2 v;
+                        v.x = Real(0.5) * re;
+                        v.y = Real(0.5) * im;
+                        sh.A[a * F + g][job] = v;
+                    }
+                }
+                if (g < F) {
+                    sh.pj[g][job] = p;
+                    sh.qj[g][job] = q;
+                }
+                double s = Spart;
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o, G);
+                if (g == 0) sh.Sj[job] = s;
+            }
+            {
+                // non-finite state in any mode lane of this group marks the trajectory bad
+                const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(isfinite(p) && isfinite(q)));
+                const unsigned gmask = (G == 32 ? FULL : (((1u << G) - 1u) << base));
+                if (bad_bits & gmask) good = false;
+            }
+        }
+        __syncwarp();
+        // ---------------- phase 2: det A per job (FP64) ----------------
+        const int jc = g;                 // this lane's job: trajectory t, step step0 + jc + 1
+        const bool jvalid = jc < cnt;
+        double2 detA = make_double2(1.0, 0.0);
+        {
+            double Ar[F][F], Ai[F][F];
+#pragma unroll
+            for (int a = 0; a < F; ++a)
+#pragma unroll
+                for (int b = 0; b < F; ++b) {
+                    const R2 v = sh.A[a * F + b][ln];
+                    Ar[a][b] = (double)v.x;
+                    Ai[a][b] = (double)v.y;
+                }
+            double dr = 1.0, di = 0.0;
+#pragma unroll
+            for (int k = 0; k < F; ++k) {
+                int piv = k;
+                double best = Ar[k][k] * Ar[k][k] + Ai[k][k] * Ai[k][k];
+#pragma unroll
+                for (int i = k + 1; i < F; ++i) {
+                    const double v = Ar[i][k] * Ar[i][k] + Ai[i][k] * Ai[i][k];
+                    if (v > best) { best = v; piv = i; }
+                }
+#pragma unroll
+                for (int i = k + 1; i < F; ++i) {
+                    if (i == piv) {
+#pragma unroll
+                        for (int cc = k; cc < F; ++cc) {
+                            double tr = Ar[k][cc]; Ar[k][cc] = Ar[i][cc]; Ar[i][cc] = tr;
+                            double ti = Ai[k][cc]; Ai[k][cc] = Ai[i][cc]; Ai[i][cc] = ti;
+                        }
+                    }
+                }
+                if (piv != k) { dr = -dr; di = -di; }
+                const double kr = Ar[k][k], ki = Ai[k][k];
+                const double nr = fma(dr, kr, -di * ki), ni = fma(dr, ki, di * kr);
+                dr = nr; di = ni;
+                const double rr = 1.0 / fma(kr, kr, ki * ki);
+                const double ir = kr * rr, ii = -ki * rr;
+#pragma unroll
+                for (int i = k + 1; i < F; ++i) {
+                    const double lr = fma(Ar[i][k], ir, -Ai[i][k] * ii);
+                    const double li = fma(Ar[i][k], ii, Ai[i][k] * ir);
+#pragma unroll
+                    for (int cc = k + 1; cc < F; ++cc) {
+                        Ar[i][cc] = fma(-lr, Ar[k][cc], fma(li, Ai[k][cc], Ar[i][cc]));
+                        Ai[i][cc] = fma(-lr, Ai[k][cc], fma(-li, Ar[k][cc], Ai[i][cc]));
+                    }
+                }
+            }
+            detA = make_double2(dr, di);
+        }
+        // ---------------- phase 3: continuous phase (segmented scan) ----------------
+        const double arg = atan2(detA.y, detA.x);
+        double arg_prev = __shfl_up_sync(FULL, arg, 1, G);
+        if (g == 0) arg_prev = arg_last;
+        double d = arg - arg_prev + A.ref_step;
+        d = fma(-kTwoPi, rint(d * kInvTwoPi), d);
+        double inc = jvalid ? d - A.ref_step : 0.0;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const double v = __shfl_up_sync(FULL, inc, o, G);
+            if (g >= o) inc += v;
+        }
+        const double theta = theta_last + inc;
+        const int lastlane = base + cnt - 1;
+        theta_last = __shfl_sync(FULL, theta, lastlane);
+        arg_last = __shfl_sync(FULL, arg, lastlane);
+        detA_last.x = __shfl_sync(FULL, detA.x, lastlane);
+        detA_last.y = __shfl_sync(FULL, detA.y, lastlane);
+        if (!isfinite(theta_last)) good = false;
+        // ---------------- phase 4: amplitudes (FP64, job-parallel) ----------------
+        if (jvalid && active) {
+            const double S = sh.Sj[ln];
+            for (int x = 0; x < A.n_chi; ++x) {
+                double re = 0.0, im = 0.0;
+#pragma unroll
+                for (int a = 0; a < F; ++a) {
+                    const double pa = sh.pj[a][ln], qa = sh.qj[a][ln];
+                    const double dq = A.q_eq[x * F + a] - qa, dp = A.p_eq[x * F + a] - pa;
+                    re = fma(-A.qw[a] * dq, dq, re);
+                    re = fma(-A.pw[a] * dp, dp, re);
+                    im = fma(0.5 * (A.p_eq[x * F + a] + pa), dq, im);
+                }
+                const double ph = im + S + 0.5 * theta;
+                double sn, cs;
+                sincos(ph, &sn, &cs);
+                const double mag = exp(re);
+                L.amp[x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1] = make_double2(mag * cs, mag * sn);
+            }
+        }
+        if (!isfinite(sh.Sj[base + cnt - 1])) good = false;
+        __syncwarp();
+    }
+
+    if (!active) return;
+    if (g == 0) L.good[jl] = good ? 1 : 0;
+    const FinalDev &fo = L.fin;
+    if (g < F) {
+        if (fo.p) fo.p[g * n + jl] = p;
+        if (fo.q) fo.q[g * n + jl] = q;
+    }
+    if (g == 0) {
+        if (fo.S) fo.S[jl] = sh.Sj[base + ((A.n_steps - 1) % C)];
+        if (fo.theta) fo.theta[jl] = theta_last;
+        if (fo.detM) fo.detM[jl] = detM_last;
+        if (fo.stab) fo.stab[jl] = stab;
+        if (fo.detA) { fo.detA[2 * jl] = detA_last.x; fo.detA[2 * jl + 1] = detA_last.y; }
+    }
+    if (fo.M && g < N2) {
+#pragma unroll
+        for (int a = 0; a < F; ++a) {
+            fo.M[jl * N2 * N2 + a * N2 + g] = (double)Mp[a];
+            fo.M[jl * N2 * N2 + (F + a) * N2 + g] = (double)Mq[a];
+        }
+    }
+}
+
+}  // namespace lg
+
+template <int F, int G, typename Real, int WARPS>
+cudaError_t launch_lg(const PropLaunch &L, cudaStream_t s)
+{
+    using namespace lg;
+    constexpr int P = F * (F + 1) / 2;
+    constexpr int T = 32 / G;
+    const size_t tensors = ((sizeof(Real) * (F * P + P * P)) + 15) & ~(size_t)15;
+    const size_t bytes = tensors + WARPS * sizeof(WarpShared<F, G, Real>);
+    auto kern = k_propagate_lg<F, G, Real, WARPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    const int64_t per_cta = (int64_t)WARPS * T;
+    const int64_t blocks = (L.n_traj + per_cta - 1) / per_cta;
+    kern<<<(unsigned)blocks, 32 * WARPS, bytes, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace scivr

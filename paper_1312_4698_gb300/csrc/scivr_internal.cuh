@@ -27,7 +27,7 @@ struct PesDev {
 
 // Kernel-side propagation parameters, passed by value.
 struct PropArgs {
-    int F, n_steps, n_chi, precision;
+    int F, n_steps, n_chi, precision, kernel;
     double dt, stab_tol, ref_step;   // ref_step = sum_i gamma_i dt
     double cdrift[4], dkick[3];      // triple-jump fractions of dt
     double gamma[SCIVR_MAX_F];
@@ -71,7 +71,7 @@ cudaError_t launch_spectrum_noalloc(const double2 *amp, int64_t amp_ld, const do
                                     int64_t *n_good_out, cudaStream_t s, int *n_launch);
 int spectrum_noalloc_max_energies();
 
-bool propagate_supported(int F, int precision);
+bool propagate_supported(int F, int precision, int kernel);
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kInvTwoPi = 0.15915494309189533576888376337251;

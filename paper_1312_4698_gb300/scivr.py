@@ -30,6 +30,9 @@ SCIVR_PES_POLY = 0
 SCIVR_FP64 = 0
 SCIVR_MIXED = 1
 SCIVR_FT_FP64 = 0
+SCIVR_KERNEL_AUTO = 0
+SCIVR_KERNEL_THREAD = 1
+SCIVR_KERNEL_GROUP = 2
 SCIVR_MAX_F = 24
 SCIVR_MAX_CHI = 8
 
@@ -57,7 +60,7 @@ class scivr_pes_desc(C.Structure):
 class scivr_prop_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_steps", C.c_int32), ("precision", C.c_int32),
                 ("stab_tol", C.c_double), ("gamma", C.c_void_p), ("p_eq", C.c_void_p),
-                ("q_eq", C.c_void_p), ("n_chi", C.c_int32)]
+                ("q_eq", C.c_void_p), ("n_chi", C.c_int32), ("kernel", C.c_int32)]
 
 
 class scivr_final_state(C.Structure):
@@ -178,13 +181,14 @@ sample_initial = scivr_sample_initial
 
 
 def scivr_propagate(pes: Pes, dt, n_steps, gamma, p_eq, q_eq, n_traj, p0, q0, amp, amp_ld, good,
-                    precision=SCIVR_FP64, stab_tol=1e-6, fin: Optional[dict] = None, stream=None):
+                    precision=SCIVR_FP64, stab_tol=1e-6, fin: Optional[dict] = None, stream=None,
+                    kernel=SCIVR_KERNEL_AUTO):
     """p_eq, q_eq: [n_chi, F] host arrays.  fin: optional dict of device tensors."""
     g = _f64(gamma)
     pe = _f64(np.atleast_2d(p_eq))
     qe = _f64(np.atleast_2d(q_eq))
     prm = scivr_prop_params(float(dt), int(n_steps), int(precision), float(stab_tol),
-                            g.ctypes.data, pe.ctypes.data, qe.ctypes.data, pe.shape[0])
+                            g.ctypes.data, pe.ctypes.data, qe.ctypes.data, pe.shape[0], int(kernel))
     fs = None
     if fin:
         fs = scivr_final_state(*[_ptr(fin.get(k)) for k in ("p", "q", "S", "theta", "detM", "detA", "M",

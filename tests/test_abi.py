@@ -76,7 +76,7 @@ def test_invalid_potentials_are_rejected(lib):
 def test_invalid_propagate_and_spectrum_arguments(lib):
     from paper_1312_4698_gb300 import scivr
     # NULL potential
-    prm = scivr.scivr_prop_params(10.0, 10, 0, 1e-6, None, None, None, 1)
+    prm = scivr.scivr_prop_params(10.0, 10, 0, 1e-6, None, None, None, 1, 0)
     rc = scivr._lib.scivr_propagate(None, C.byref(prm), 4, None, None, None, 11, None, None, None)
     assert rc == scivr.SCIVR_EINVAL
     assert "NULL" in scivr.last_error()

@@ -33,7 +33,10 @@ def _t(x, dtype=None):
     return torch.as_tensor(np.ascontiguousarray(x), device="cuda", dtype=dtype)
 
 
-def gpu_propagate(G, w8, p0, q0, precision=0, fin=False):
+MIXED_STAB_TOL = 1e-6 * 2.0 ** 29   # the FP64 threshold scaled by eps32 / eps64
+
+
+def gpu_propagate(G, w8, p0, q0, precision=0, fin=False, kernel=0, stab_tol=None):
     import torch
     F, n = p0.shape
     K = w8.n_steps + 1
@@ -50,8 +53,9 @@ def gpu_propagate(G, w8, p0, q0, precision=0, fin=False):
                   detA=torch.empty((n, 2), dtype=torch.float64, device="cuda"),
                   M=torch.empty((n, 2 * F, 2 * F), dtype=torch.float64, device="cuda"),
                   stab=torch.empty(n, dtype=torch.float64, device="cuda"))
+    tol = w8.stab_tol if stab_tol is None else stab_tol
     G.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, _t(p0), _t(q0), amp, K,
-                      good, precision=precision, stab_tol=w8.stab_tol, fin=fd)
+                      good, precision=precision, stab_tol=tol, fin=fd, kernel=kernel)
     torch.cuda.synchronize()
     a = amp.cpu().numpy()
     a = a[..., 0] + 1j * a[..., 1]
@@ -114,17 +118,19 @@ def test_sampler_matches_oracle(G):
     assert np.allclose(w.cpu().numpy(), rw, rtol=1e-12)
 
 
-@pytest.mark.parametrize("F", [1, 2, 3, 4, 5, 6, 7, 8, 9])
-def test_propagate_matches_oracle_small(G, F):
-    """Every supported F; 70 trajectories (ragged w.r.t. any block size)."""
+@pytest.mark.parametrize("F,kernel", [(F, 1) for F in range(1, 10)] + [(F, 2) for F in range(1, 9)])
+def test_propagate_matches_oracle_small(G, F, kernel):
+    """FP64 path, both schedules (1 = thread per trajectory, 2 = lane group),
+    every supported F; 70 trajectories (ragged w.r.t. any block size) and a
+    step count that is not a multiple of the group's chunk length."""
     if F == 3:
-        w8 = wl.config_f3(n_traj=70, n_steps=300)
+        w8 = wl.config_f3(n_traj=70, n_steps=301)
     else:
-        w8 = wl.config_generic(F, seed=F, n_traj=70, n_steps=300)
+        w8 = wl.config_generic(F, seed=F, n_traj=70, n_steps=301)
     p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, 11)
     ra, rg, rf = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0,
                                   final=True)
-    g = gpu_propagate(G, w8, p0, q0, fin=True)
+    g = gpu_propagate(G, w8, p0, q0, fin=True, kernel=kernel)
     check_flags(g["good"], g["stab"], rg, rf["stab"])
     assert amp_err(g["amp"], ra, rg) < 1e-9
     sel = rg.astype(bool)
@@ -307,3 +313,62 @@ def test_config_f6_full_size_sampled(G):
     comb = sum(Ih.cpu().numpy() * int(ngh.item()) for Ih, ngh in parts) / int(bufs.n_good.item())
     full = bufs.I[0].cpu().numpy()
     assert np.max(np.abs(comb - full)) <= 1e-12 * np.max(full)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_propagate_several_reference_states_both_schedules(G, kernel):
+    w8 = wl.config_f6(n_traj=37, n_steps=77)
+    om = w8.gamma
+    w8 = w8.with_(p_eq=np.stack([np.sqrt(om), np.sqrt(3 * om)]), q_eq=np.zeros((2, 6)))
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq[0], w8.q_eq[0], w8.n_traj, 4)
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0)
+    g = gpu_propagate(G, w8, p0, q0, kernel=kernel)
+    assert amp_err(g["amp"], ra, rg) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision (FP32 monodromy / potential / det M; FP64 p, q, S, det A,
+# phase).  Bounds: amplitudes within 5e-2 of the trajectory's largest
+# amplitude (FP32 rounding of the force and of M perturbs the trajectory and
+# the prefactor phase; measured 3e-3 typical, 2.3e-2 worst over 16384
+# trajectories of the F=6 workload); spectra within 1 cm^-1 per peak.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("F", [2, 3, 6, 8])
+def test_mixed_propagate_close_to_oracle(G, F):
+    w8 = wl.config_f3(n_traj=64, n_steps=400) if F == 3 else wl.config_generic(F, seed=F, n_traj=64, n_steps=400)
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, 3)
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0)
+    g = gpu_propagate(G, w8, p0, q0, precision=1, stab_tol=MIXED_STAB_TOL)
+    sel = rg.astype(bool) & g["good"].astype(bool)
+    assert sel.sum() >= 0.95 * rg.sum()
+    assert amp_err(g["amp"][:, sel], ra[:, sel], np.ones(sel.sum(), np.uint8)) < 5e-2
+
+
+def test_mixed_spectrum_peaks_within_1cm(G):
+    """F=3 workload at full size, mixed propagation + FP64 Fourier step, against the
+    FP64 oracle on the oracle's good set: every peak within 1 cm^-1."""
+    import torch
+    w8 = wl.config_f3()
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, w8.seed)
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0)
+    ri, rng_ = oracle.spectrum(ra[0], w, rg, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E)
+    n, K = w8.n_traj, w8.n_steps + 1
+    pes = G.scivr_create_pes(w8.pes)
+    amp = torch.empty((1, n, K, 2), dtype=torch.float64, device="cuda")
+    good = torch.empty(n, dtype=torch.uint8, device="cuda")
+    G.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, _t(p0), _t(q0), amp, K,
+                      good, precision=1, stab_tol=MIXED_STAB_TOL)
+    I = torch.empty(w8.n_E, dtype=torch.float64, device="cuda")
+    G.scivr_spectrum(amp[0], K, _t(w), _t(rg), n, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, I)
+    torch.cuda.synchronize()
+    gi = I.cpu().numpy()
+    gg = good.cpu().numpy()
+    flips = int(np.sum(gg.astype(bool) != rg.astype(bool)))
+    assert flips <= n // 100, flips
+    E = w8.energies()
+    pr = wl.to_cm1(cf.find_peaks(E, ri))
+    pg = wl.to_cm1(cf.find_peaks(E, gi))
+    assert len(pr) > 0 and len(pr) == len(pg)
+    assert np.max(np.abs(pr - pg)) <= 1.0
+    assert np.max(np.abs(gi - ri)) <= 2e-2 * np.max(ri)
