@@ -33,8 +33,12 @@ sys.path.insert(0, HERE)
 from paper_1312_4698_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "trajectory-steps/s and spectra/s at ≤1 cm⁻¹ peak error vs FP64 oracle"
+FT_MODES = {"fp64": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+MIXED_STAB_TOL = 1e-6 * 2.0 ** 29     # the FP64 threshold scaled by eps32 / eps64
 L2_FLUSH_BYTES = 512 << 20
 FP64_PEAK_GFLOPS = 1250.0      # GB300 dense FP64 (nominal, CUDA cores and tensor cores alike)
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07   # 80.5 TFLOP/s: SMs x FP32 lanes x 2 x max SM clock
 FP64_PEAK_NOTE = ("GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table); an FMA-chain "
                   "probe on this pool measured 1.252 TFLOP/s")
 # dram read+write bytes per launch from ncu captures (profiles/), keyed by (kernel, workload);
@@ -78,13 +82,19 @@ def propagate_flops_per_traj_step(F: int, n3: int, n4: int) -> float:
     det M by LU of 2F x 2F ((2/3)(2F)^3 flops), det A by complex LU of F x F
     (8/3 F^3 real flops) plus building A (6 F^2), phase (~30) and the
     amplitude per reference state (~10 F + 30)."""
+    fp32, fp64 = propagate_flops_split(F, n3, n4)
+    return fp32 + fp64
+
+
+def propagate_flops_split(F: int, n3: int, n4: int):
+    """(bulk, fp64-kept) split of propagate_flops_per_traj_step: in the mixed path
+    the bulk (potential, monodromy, det M, building A) runs in FP32 and the rest
+    (p, q, S updates, det A, phase, amplitude) in FP64."""
     P = F * (F + 1) // 2
     pes = 2 * (P + (P * F if n3 else 0) + (P * P if n4 else 0) + 4 * P) + 6 * F
-    kick = pes + 2 * (2 * F * F * F) + 2 * F
-    drift = 2 * (F + 2 * F * F) + 2 * F
-    lu_m = (2.0 / 3.0) * (2 * F) ** 3
-    lu_a = (8.0 / 3.0) * F ** 3 + 6 * F * F
-    return 3 * kick + 4 * drift + lu_m + lu_a + 30 + 10 * F + 30
+    bulk = 3 * (pes + 2 * (2 * F * F * F)) + 4 * (2 * 2 * F * F) + (2.0 / 3.0) * (2 * F) ** 3 + 6 * F * F
+    kept = 3 * (2 * F + 2) + 4 * (2 * F + 2 * F) + (8.0 / 3.0) * F ** 3 + 30 + 10 * F + 30
+    return bulk, kept
 
 
 class ClockSampler:
@@ -225,6 +235,10 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="propagation arithmetic (mixed: FP32 monodromy/potential, FP64 p, q, S, det A)")
+    ap.add_argument("--ft", default="bf16x3", choices=list(FT_MODES),
+                    help="Fourier step: fp64 CUDA cores or tensor-core BF16 digit splits")
     ap.add_argument("--n-traj", type=int, default=None, help="override the workload's trajectory count")
     ap.add_argument("--n-steps", type=int, default=None, help="override the workload's step count")
     ap.add_argument("--n-E", type=int, default=None, help="override the workload's energy count")
@@ -254,6 +268,9 @@ def main(argv=None):
     K = w8.n_steps + 1
     n = w8.n_traj
 
+    prec = PRECISIONS[args.precision]
+    ftm = FT_MODES[args.ft]
+    tol = MIXED_STAB_TOL if prec == 1 else w8.stab_tol
     ev = {k: [] for k in ("prop0", "prop1", "spec1")}
 
     def one_step(record):
@@ -262,11 +279,11 @@ def main(argv=None):
         if record:
             e0 = torch.cuda.Event(enable_timing=True); e0.record(stream); ev["prop0"].append(e0)
         scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0, bufs.q0,
-                              bufs.amp, K, bufs.good, stab_tol=w8.stab_tol, stream=stream)
+                              bufs.amp, K, bufs.good, precision=prec, stab_tol=tol, stream=stream)
         if record:
             e1 = torch.cuda.Event(enable_timing=True); e1.record(stream); ev["prop1"].append(e1)
         scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min,
-                             w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, stream=stream)
+                             w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, ft_mode=ftm, stream=stream)
         if record:
             e2 = torch.cuda.Event(enable_timing=True); e2.record(stream); ev["spec1"].append(e2)
         if world > 1:
@@ -325,9 +342,10 @@ def main(argv=None):
             bufs.q0.copy_(hq0, non_blocking=True)
             bufs.w.copy_(hw, non_blocking=True)
             scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0,
-                                  bufs.q0, bufs.amp, K, bufs.good, stab_tol=w8.stab_tol, stream=stream)
+                                  bufs.q0, bufs.amp, K, bufs.good, precision=prec, stab_tol=tol,
+                                  stream=stream)
             scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min,
-                                 w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, stream=stream)
+                                 w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, ft_mode=ftm, stream=stream)
             hI.copy_(bufs.I[0], non_blocking=True)
             hng.copy_(bufs.n_good, non_blocking=True)
         e1.record(stream)
@@ -349,20 +367,45 @@ def main(argv=None):
     prop_avg = float(np.mean(prop_ms))
     spec_avg = float(np.mean(spec_ms))
     ft_flops = 8.0 * n * K * w8.n_E
-    pr_flops = propagate_flops_per_traj_step(w8.F, w8.pes.c3.size, w8.pes.c4.size) * n * w8.n_steps
+    bulk, kept = propagate_flops_split(w8.F, w8.pes.c3.size, w8.pes.c4.size)
+    pr_flops = (bulk + kept) * n * w8.n_steps
     ft_tf = ft_flops / (spec_avg * 1e-3) / 1e12
     pr_tf = pr_flops / (prop_avg * 1e-3) / 1e12
-    peak_tf = FP64_PEAK_GFLOPS / 1e3
+    peaks = measured_peaks()
+    fp64_peak = FP64_PEAK_GFLOPS / 1e3
+    full = args.n_traj is None and args.n_steps is None and args.n_E is None
     if spec_avg >= prop_avg:
-        full = args.n_traj is None and args.n_steps is None and args.n_E is None
-        roof = {"kernel": "k_ft_fp64 (scivr_spectrum)", "bound": "alu", "achieved": ft_tf,
-                "peak": peak_tf, "unit": "TFLOP/s", "frac": ft_tf / peak_tf,
-                "traffic": TRAFFIC.get(("k_ft_fp64", args.workload)) if full else None,
-                "peak_source": FP64_PEAK_NOTE}
+        if ftm == 0:
+            roof = {"kernel": "k_ft_fp64 (scivr_spectrum)", "bound": "alu", "achieved": ft_tf,
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": ft_tf / fp64_peak,
+                    "traffic": TRAFFIC.get(("k_ft_fp64", args.workload)) if full else None,
+                    "peak_source": FP64_PEAK_NOTE}
+        else:
+            pk = float(peaks.get("bf16_tflops", 1900.0))
+            roof = {"kernel": f"k_ft_tc<{ftm}> (scivr_spectrum, {args.ft})", "bound": "tensor",
+                    "achieved": ft_tf, "peak": pk, "unit": "TFLOP/s", "frac": ft_tf / pk,
+                    "traffic": TRAFFIC.get((f"k_ft_tc{ftm}", args.workload)) if full else None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured"
+                                   if "bf16_tflops" in peaks else "fallback 1900 TFLOP/s",
+                    "note": "achieved counts the 8 N K N_E algorithmic flops; the digit "
+                            "products multiply the executed tensor flops"}
     else:
-        roof = {"kernel": "k_propagate (scivr_propagate)", "bound": "alu", "achieved": pr_tf,
-                "peak": peak_tf, "unit": "TFLOP/s", "frac": pr_tf / peak_tf, "traffic": None,
-                "peak_source": FP64_PEAK_NOTE}
+        if prec == 0:
+            roof = {"kernel": "k_propagate (scivr_propagate, fp64)", "bound": "alu", "achieved": pr_tf,
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": pr_tf / fp64_peak, "traffic": None,
+                    "peak_source": FP64_PEAK_NOTE}
+        else:
+            # two pipes: the FP32 bulk at the FP32 peak plus the FP64-kept part at the FP64 peak
+            t_bound = (bulk * n * w8.n_steps) / (FP32_PEAK_GFLOPS * 1e9) + \
+                      (kept * n * w8.n_steps) / (FP64_PEAK_GFLOPS * 1e9)
+            eff_peak = pr_flops / t_bound / 1e12
+            roof = {"kernel": "k_propagate_lg<float> (scivr_propagate, mixed)", "bound": "alu",
+                    "achieved": pr_tf, "peak": eff_peak, "unit": "TFLOP/s", "frac": pr_tf / eff_peak,
+                    "traffic": None,
+                    "peak_source": (f"two-pipe bound: FP32 bulk {bulk:.0f} flop/step at "
+                                    f"{FP32_PEAK_GFLOPS / 1e3:.1f} TFLOP/s + FP64-kept {kept:.0f} "
+                                    f"flop/step at {fp64_peak} TFLOP/s (FP32 peak = 152 SMs x 128 "
+                                    f"lanes x 2 x 2.07 GHz; FMA probe measured 73.3)")}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -375,9 +418,11 @@ def main(argv=None):
     line = {
         "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision] + ("" if ftm == 0 else f" + {args.ft} tensor FT"),
         "data": "synthetic",
-        "config": {"workload": describe(w8), "global_batch": world * n, "seed": "base 0 + rank",
+        "config": {"workload": describe(w8, args.precision, args.ft), "global_batch": world * n,
+                   "seed": "base 0 + rank",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); amplitudes "
                          f"({n * K * 16 / 1e9:.2f} GB) exceed L2",
                    "parallelism": f"replicas x{world}"},

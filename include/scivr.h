@@ -62,7 +62,10 @@ enum { SCIVR_KERNEL_AUTO = 0,     /* library choice (tuned per F, precision, n_t
        SCIVR_KERNEL_GROUP = 2 };  /* a lane group per trajectory, batched FP64 determinants */
 
 /* Arithmetic of the time -> energy Fourier step. */
-enum { SCIVR_FT_FP64 = 0 };       /* FP64 fused-multiply-add contraction */
+enum { SCIVR_FT_FP64 = 0,         /* FP64 fused-multiply-add contraction (CUDA cores) */
+       SCIVR_FT_TC_BF16 = 1,      /* tensor cores: one BF16 digit per operand, FP32 accumulation */
+       SCIVR_FT_TC_BF16X3 = 2,    /* tensor cores: two BF16 digits, three digit products */
+       SCIVR_FT_TC_BF16X6 = 3 };  /* tensor cores: three BF16 digits, six products (FP32-level) */
 
 #define SCIVR_MAX_F 24            /* largest number of modes */
 #define SCIVR_MAX_CHI 8           /* largest number of reference states per call */
@@ -173,11 +176,18 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
  * nothing, whatever their amplitudes hold.  If n_good = 0, I is all zeros.
  * amp: device complex double [n_traj][amp_ld] (amp_prec = SCIVR_FP64).  w:
  * device [n_traj].  good: device [n_traj].  I_out: device [n_E].  n_good_out:
- * device int64 (may be NULL).  Allocates stream-ordered scratch
- * (cudaMallocAsync) of about 16 (n_steps+1) n_E + 8 n_E ceil(n_traj/64) bytes.
+ * device int64 (may be NULL).  ft_mode SCIVR_FT_FP64 contracts in FP64 on
+ * the CUDA cores; the SCIVR_FT_TC_* modes split both operands into BF16
+ * digits and contract on the tensor cores (tcgen05) with FP32 accumulation,
+ * then sum tiles in FP64: their error is that of the digit count (about
+ * 2^-8, 2^-16, 2^-24 relative to the largest terms).  Allocates
+ * stream-ordered scratch (cudaMallocAsync): FP64 mode about
+ * 16 (n_steps+1) n_E + 8 n_E ceil(n_traj/64) bytes; tensor-core modes about
+ * 4 d (n_steps+1) (n_traj + 2 n_E) + 8 n_E ceil(n_traj/128) bytes, d digits.
  * Errors: SCIVR_EINVAL (NULL pointers, n_traj < 1, n_steps < 1, n_E < 2,
  * E_max <= E_min, dt <= 0, amp_ld < n_steps + 1), SCIVR_EUNSUPPORTED
- * (amp_prec or ft_mode not built), SCIVR_ENOMEM. */
+ * (amp_prec or ft_mode not built), SCIVR_ENOMEM.  A tensor-core wait that
+ * expires is reported by scivr_check_status. */
 int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const double *w,
                    const uint8_t *good, int64_t n_traj, int32_t n_steps, double dt,
                    double E_min, double E_max, int32_t n_E, int32_t ft_mode,
@@ -205,6 +215,17 @@ int scivr_spectrum_noalloc(const void *amp, int64_t amp_ld, int32_t amp_prec, co
                            const uint8_t *good, int64_t n_traj, int32_t n_steps, double dt,
                            double E_min, double E_max, int32_t n_E, int32_t ft_mode,
                            double *I_out, int64_t *n_good_out, void *stream);
+
+/* Synchronise `stream`, then read and clear this device's status word:
+ * SCIVR_ETIMEOUT if a bounded device-side wait (mbarrier) expired in a kernel
+ * since the last check, SCIVR_OK otherwise (SCIVR_ECUDA on a CUDA error). */
+int scivr_check_status(void *stream);
+
+/* Launch a one-CTA kernel that waits, with a limit of `seconds`, on an
+ * mbarrier that nothing completes, exercising the bounded-wait path that the
+ * tensor-core kernels use.  A following scivr_check_status must return
+ * SCIVR_ETIMEOUT.  seconds must lie in (0, 10]. */
+int scivr_selftest_wait_timeout(double seconds, void *stream);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *scivr_last_error(void);

@@ -313,8 +313,24 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
     if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "scivr_spectrum: amp_ld < n_steps+1");
     if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "scivr_spectrum: amp not 16-byte aligned");
     if (amp_prec != SCIVR_FP64) return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: amp_prec %d not supported", amp_prec);
-    if (ft_mode != SCIVR_FT_FP64) return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: ft_mode %d not supported", ft_mode);
+    if (ft_mode != SCIVR_FT_FP64 && ft_tc_digits(ft_mode) == 0)
+        return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: ft_mode %d not supported", ft_mode);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ft_mode != SCIVR_FT_FP64) {
+        const size_t tb = spectrum_tc_scratch_bytes(ft_mode, n_traj, n_steps, n_E);
+        void *scr = nullptr;
+        cudaError_t e = cudaMallocAsync(&scr, tb, s);
+        if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: cudaMallocAsync");
+        int nl = 0;
+        e = launch_spectrum_tc(ft_mode, static_cast<const double2 *>(amp), amp_ld, w, good, n_traj, n_steps,
+                               dt, E_min, E_max, n_E, I_out, n_good_out, scr, s, &nl);
+        g_launches += nl;
+        cudaError_t e2 = cudaFreeAsync(scr, s);
+        if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: tensor-core launch");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "scivr_spectrum: cudaFreeAsync");
+        ok();
+        return SCIVR_OK;
+    }
     const size_t bytes = spectrum_fp64_scratch_bytes(n_traj, n_steps, n_E);
     void *scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, bytes, s);
@@ -326,6 +342,30 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
     cudaError_t e2 = cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "scivr_spectrum: cudaFreeAsync");
+    ok();
+    return SCIVR_OK;
+}
+
+int scivr_check_status(void *stream)
+{
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "scivr_check_status: synchronize");
+    int st = 0;
+    e = read_and_clear_status(&st);
+    if (e != cudaSuccess) return cuda_fail(e, "scivr_check_status: status word");
+    if (st == SCIVR_ETIMEOUT) return fail(SCIVR_ETIMEOUT, "scivr_check_status: a bounded device wait expired");
+    if (st != 0) return fail(SCIVR_ECUDA, "scivr_check_status: device status %d", st);
+    ok();
+    return SCIVR_OK;
+}
+
+int scivr_selftest_wait_timeout(double seconds, void *stream)
+{
+    if (!(seconds > 0.0) || seconds > 10.0)
+        return fail(SCIVR_EINVAL, "scivr_selftest_wait_timeout: seconds must lie in (0, 10]");
+    cudaError_t e = launch_wait_selftest(seconds, static_cast<cudaStream_t>(stream));
+    g_launches += 1;
+    if (e != cudaSuccess) return cuda_fail(e, "scivr_selftest_wait_timeout: launch");
     ok();
     return SCIVR_OK;
 }

@@ -70,6 +70,14 @@ cudaError_t launch_spectrum_noalloc(const double2 *amp, int64_t amp_ld, const do
                                     double E_min, double E_max, int n_E, double *I_out,
                                     int64_t *n_good_out, cudaStream_t s, int *n_launch);
 int spectrum_noalloc_max_energies();
+int ft_tc_digits(int ft_mode);
+size_t spectrum_tc_scratch_bytes(int ft_mode, int64_t n_traj, int n_steps, int n_E);
+cudaError_t launch_spectrum_tc(int ft_mode, const double2 *amp, int64_t amp_ld, const double *w,
+                               const uint8_t *good, int64_t n_traj, int n_steps, double dt, double E_min,
+                               double E_max, int n_E, double *I_out, int64_t *n_good_out, void *scratch,
+                               cudaStream_t s, int *n_launch);
+cudaError_t launch_wait_selftest(double seconds, cudaStream_t s);
+cudaError_t read_and_clear_status(int *status);
 
 bool propagate_supported(int F, int precision, int kernel);
 

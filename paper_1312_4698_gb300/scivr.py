@@ -30,6 +30,9 @@ SCIVR_PES_POLY = 0
 SCIVR_FP64 = 0
 SCIVR_MIXED = 1
 SCIVR_FT_FP64 = 0
+SCIVR_FT_TC_BF16 = 1
+SCIVR_FT_TC_BF16X3 = 2
+SCIVR_FT_TC_BF16X6 = 3
 SCIVR_KERNEL_AUTO = 0
 SCIVR_KERNEL_THREAD = 1
 SCIVR_KERNEL_GROUP = 2
@@ -86,14 +89,27 @@ _lib.scivr_spectrum.argtypes = [_vp, _i64, _i32, _vp, _vp, _i64, _i32, _d, _d, _
 _lib.scivr_spectrum.restype = C.c_int
 _lib.scivr_spectrum_noalloc.argtypes = list(_lib.scivr_spectrum.argtypes)
 _lib.scivr_spectrum_noalloc.restype = C.c_int
+_lib.scivr_check_status.argtypes = [_vp]
+_lib.scivr_check_status.restype = C.c_int
+_lib.scivr_selftest_wait_timeout.argtypes = [_d, _vp]
+_lib.scivr_selftest_wait_timeout.restype = C.c_int
 _lib.scivr_last_error.argtypes = []
 _lib.scivr_last_error.restype = C.c_char_p
 _lib.scivr_launch_count.argtypes = [C.c_int]
 _lib.scivr_launch_count.restype = _i64
 
 EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_sample_initial",
-            "scivr_propagate", "scivr_spectrum", "scivr_spectrum_noalloc", "scivr_last_error",
-            "scivr_launch_count"]
+            "scivr_propagate", "scivr_spectrum", "scivr_spectrum_noalloc", "scivr_check_status",
+            "scivr_selftest_wait_timeout", "scivr_last_error", "scivr_launch_count"]
+
+
+def scivr_check_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device status (SCIVR_OK / SCIVR_ETIMEOUT)."""
+    return int(_lib.scivr_check_status(_stream(stream)))
+
+
+def scivr_selftest_wait_timeout(seconds: float, stream=None):
+    _check(_lib.scivr_selftest_wait_timeout(float(seconds), _stream(stream)), "scivr_selftest_wait_timeout")
 
 
 def last_error() -> str:
