@@ -43,7 +43,7 @@ FP64_PEAK_NOTE = ("GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table
                   "probe on this pool measured 1.252 TFLOP/s")
 # dram read+write bytes per launch from ncu captures (profiles/), keyed by (kernel, workload);
 # scaled to the full launch where the capture used fewer trajectories
-TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9}
+TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9, ("k_ft_tc2", "f6"): 7.98e9}
 
 
 def workload(name: str, seed: int):

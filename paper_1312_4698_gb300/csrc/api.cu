@@ -267,6 +267,8 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
     A.dt = prm->dt;
     A.stab_tol = prm->stab_tol;
     triple_jump(A.cdrift, A.dkick);
+    for (int i = 0; i < 4; ++i) A.tdrift[i] = A.cdrift[i] * prm->dt;
+    for (int i = 0; i < 3; ++i) A.tkick[i] = A.dkick[i] * prm->dt;
     double ref = 0.0;
     for (int i = 0; i < F; ++i) {
         const double g = prm->gamma[i];

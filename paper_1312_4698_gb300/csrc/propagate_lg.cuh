@@ -16,9 +16,15 @@
 //   phase 4 (job-parallel, FP64): overlap <chi|p q>, action, phase and the
 //     amplitude; each group writes G consecutive samples of its row.
 //
-// Real = float is the mixed-precision path (monodromy, potential, det M and
-// A in FP32; p, q, S, det A, phase and amplitude in FP64); Real = double is
-// the same schedule in FP64 throughout.
+// Real = float is the mixed-precision path: monodromy, potential, det M, A
+// and each step's action increment in FP32; positions, momenta, the
+// accumulated action, det A and the continuous phase in FP64; the amplitude's
+// phase is reduced modulo 2 pi in FP64 and its sine, cosine and magnitude are
+// evaluated in FP32.  Real = double is the same schedule in FP64 throughout.
+//
+// On GB300 a warp-wide FP64 instruction holds a sub-partition's FP64 pipe for
+// about 64 cycles, so phase 1 keeps FP64 to the state updates (one FMA per
+// drift and per kick in the mode lanes) and one FP64 add per step.
 #pragma once
 
 #include <math_constants.h>
@@ -40,9 +46,30 @@ template <typename Real> __device__ __forceinline__ Real rexp(Real x);
 template <> __device__ __forceinline__ float rexp<float>(float x) { return expf(x); }
 template <> __device__ __forceinline__ double rexp<double>(double x) { return exp(x); }
 
+// 1/x in FP64 from the FP32 reciprocal refined by two Newton steps
+// (e_{k+1} = e_k^2: 2^-23 -> 2^-46 -> below FP64 rounding); FP64 division
+// outside the FP32 exponent range.
+__device__ __forceinline__ double recip64(double x)
+{
+    const double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double r = (double)__frcp_rn((float)x);
+    r = r * fma(-x, r, 2.0);
+    r = r * fma(-x, r, 2.0);
+    return r;
+}
+
 template <typename Real> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<double> { using T = double2; };
+
+// Per-mode and per-reference-state constants, staged in shared memory so that
+// lane- or chi-dependent indexing never touches the kernel-parameter space.
+template <int F>
+struct CtaConst {
+    double rg[F], irg[F], qw[F], pw[F];
+    double p_eq[SCIVR_MAX_CHI][F], q_eq[SCIVR_MAX_CHI][F];
+};
 
 template <int F, int G, typename Real>
 struct WarpShared {
@@ -59,7 +86,7 @@ struct WarpShared {
 };
 
 template <int F, int G, typename Real, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
+__global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch L)
 {
     constexpr int N2 = 2 * F;
     constexpr int P = F * (F + 1) / 2;
@@ -74,6 +101,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
     Real *sT3 = reinterpret_cast<Real *>(smem_raw);
     Real *sT4 = sT3 + F * P;
     size_t off = ((sizeof(Real) * (F * P + P * P)) + 15) & ~(size_t)15;
+    CtaConst<F> &cc = *reinterpret_cast<CtaConst<F> *>(smem_raw + off);
+    off += (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
     Sh *wsh_all = reinterpret_cast<Sh *>(smem_raw + off);
 
     const PesDev &pes = L.pes;
@@ -86,6 +115,22 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
         else { g3 = reinterpret_cast<const Real *>(pes.T3); g4 = reinterpret_cast<const Real *>(pes.T4); }
         for (int i = threadIdx.x; i < F * P; i += blockDim.x) sT3[i] = use3 ? g3[i] : Real(0);
         for (int i = threadIdx.x; i < P * P; i += blockDim.x) sT4[i] = use4 ? g4[i] : Real(0);
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int a = 0; a < F; ++a) {
+            cc.rg[a] = A.rg[a];
+            cc.irg[a] = A.irg[a];
+            cc.qw[a] = A.qw[a];
+            cc.pw[a] = A.pw[a];
+        }
+#pragma unroll
+        for (int x = 0; x < SCIVR_MAX_CHI; ++x)
+#pragma unroll
+            for (int a = 0; a < F; ++a) {
+                cc.p_eq[x][a] = x < A.n_chi ? A.p_eq[x * F + a] : 0.0;
+                cc.q_eq[x][a] = x < A.n_chi ? A.q_eq[x * F + a] : 0.0;
+            }
     }
     __syncthreads();
 
@@ -111,7 +156,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
     // mode state (lane g < F)
     const int mode = g < F ? g : 0;
     double p = L.p0[mode * n + jl], q = L.q0[mode * n + jl];
-    double Spart = 0.0;
+    Real pr = (Real)p;          // the momentum as seen by the Real-precision bulk
+    double S = 0.0;             // accumulated action (lane 0 of the group holds the total)
     // column state (lane g < 2F): column g of M = d(p,q)/d(p0,q0)
     Real Mp[F], Mq[F];
 #pragma unroll
@@ -120,7 +166,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
         Mq[a] = (g >= F && g < N2 && a == g - F) ? Real(1) : Real(0);
     }
     bool good = true;
-    double stab = 0.0, detM_last = 1.0;
+    Real stab = Real(0);
+    double detM_last = 1.0;
     double theta_last = 0.0, arg_last = 0.0;
     double2 detA_last = make_double2(1.0, 0.0);
 
@@ -130,10 +177,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
             double re = 0.0, im = 0.0;
             for (int a = 0; a < F; ++a) {
                 const double pa = L.p0[a * n + jl], qa = L.q0[a * n + jl];
-                const double dq = A.q_eq[x * F + a] - qa, dp = A.p_eq[x * F + a] - pa;
-                re = fma(-A.qw[a] * dq, dq, re);
-                re = fma(-A.pw[a] * dp, dp, re);
-                im = fma(0.5 * (A.p_eq[x * F + a] + pa), dq, im);
+                const double dq = cc.q_eq[x][a] - qa, dp = cc.p_eq[x][a] - pa;
+                re = fma(-cc.qw[a] * dq, dq, re);
+                re = fma(-cc.pw[a] * dp, dp, re);
+                im = fma(0.5 * (cc.p_eq[x][a] + pa), dq, im);
             }
             double sn, cs;
             sincos(im, &sn, &cs);
@@ -148,22 +195,22 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
         // ---------------- phase 1: cnt steps, group-parallel ----------------
         for (int c = 0; c < cnt; ++c) {
 #pragma unroll
+            Real dS = Real(0);   // this lane's share of the step's action increment
             for (int sub = 0; sub < 4; ++sub) {
-                // drift
+                // drift: q += tau p, S += tau p.p/2, M_q += tau M_p
                 {
-                    const double tau = A.cdrift[sub] * A.dt;
+                    const Real rt = (Real)A.tdrift[sub];
                     if (g < F) {
-                        Spart = fma(tau * 0.5 * p, p, Spart);
-                        q = fma(tau, p, q);
+                        q = fma(A.tdrift[sub], p, q);
+                        dS = fma(rt * Real(0.5) * pr, pr, dS);
                     }
-                    const Real rt = (Real)A.cdrift[sub] * rdt;
 #pragma unroll
                     for (int a = 0; a < F; ++a) Mq[a] = fma(rt, Mp[a], Mq[a]);
                 }
                 if (sub == 3) break;
                 // kick: potential at q
-                const double tk = A.dkick[sub] * A.dt;
-                const Real rtk = (Real)A.dkick[sub] * rdt;
+                const double tk = A.tkick[sub];
+                const Real rtk = (Real)tk;
                 __syncwarp();   // previous kick's readers of qr/H are done
                 if (g < F) {
                     sh.qd[t][g] = q;
@@ -212,7 +259,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
                 }
                 __syncwarp();
                 // gradient, p and action (mode lanes)
-                double vlane = (double)vpart;
+                Real vlane = vpart;
                 if (g < F) {
                     Real gr = Real(0);
 #pragma unroll
@@ -233,9 +280,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
                         gd = w * w * sh.qr[t][g];
                     }
                     p = fma(-tk, (double)(gr + gd), p);
-                    vlane += (double)Vd;
+                    pr = (Real)p;
+                    vlane += Vd;
                 }
-                Spart = fma(-tk, vlane, Spart);
+                dS = fma(-rtk, vlane, dS);
                 // monodromy kick: M_p -= tau H M_q (column lanes)
 #pragma unroll
                 for (int a = 0; a < F; ++a) {
@@ -274,11 +322,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
                         if (g > k) W[i] = fma(-li, W[k], W[i]);
                     }
                 }
-                const double dd = (double)det;
-                const double dev = isfinite(dd) ? fabs(fma(dd, dd, -1.0)) : CUDART_INF;
+                const Real dev = isfinite(det) ? fabs(fma(det, det, Real(-1))) : Real(CUDART_INF);
                 stab = dev > stab ? dev : stab;
-                if (dev > A.stab_tol) good = false;
-                detM_last = dd;
+                if (dev > (Real)A.stab_tol) good = false;
+                if (c == cnt - 1) detM_last = (double)det;
             }
             // ---- Herman-Kluk matrix column b = g (needs column F + b) ----
             {
@@ -289,8 +336,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
                     const Real mpq = __shfl_sync(FULL, Mp[a], src);
                     const Real mqq = __shfl_sync(FULL, Mq[a], src);
                     if (g < F) {
-                        const Real rga = (Real)A.rg[a], irga = (Real)A.irg[a];
-                        const Real rgb = (Real)A.rg[g], irgb = (Real)A.irg[g];
+                        const Real rga = (Real)cc.rg[a], irga = (Real)cc.irg[a];
+                        const Real rgb = (Real)cc.rg[g], irgb = (Real)cc.irg[g];
                         const Real re = fma(rga * irgb, mqq, (rgb * irga) * Mp[a]);
                         const Real im = fma(-(rga * rgb), Mq[a], (irga * irgb) * mpq);
                         R2 v;
@@ -303,17 +350,20 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
                     sh.pj[g][job] = p;
                     sh.qj[g][job] = q;
                 }
-                double s = Spart;
+                // the step's action increment, summed over the group, joins the FP64 action
 #pragma unroll
-                for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o, G);
-                if (g == 0) sh.Sj[job] = s;
+                for (int o = G / 2; o > 0; o >>= 1) dS += __shfl_xor_sync(FULL, dS, o, G);
+                if (g == 0) {
+                    S += (double)dS;
+                    sh.Sj[job] = S;
+                }
             }
-            {
-                // non-finite state in any mode lane of this group marks the trajectory bad
-                const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(isfinite(p) && isfinite(q)));
-                const unsigned gmask = (G == 32 ? FULL : (((1u << G) - 1u) << base));
-                if (bad_bits & gmask) good = false;
-            }
+        }
+        {
+            // non-finite state persists, so testing once per chunk marks the same trajectories
+            const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(isfinite(p) && isfinite(q)));
+            const unsigned gmask = (G == 32 ? FULL : (((1u << G) - 1u) << base));
+            if (bad_bits & gmask) good = false;
         }
         __syncwarp();
         // ---------------- phase 2: det A per job (FP64) ----------------
@@ -354,7 +404,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
                 const double kr = Ar[k][k], ki = Ai[k][k];
                 const double nr = fma(dr, kr, -di * ki), ni = fma(dr, ki, di * kr);
                 dr = nr; di = ni;
-                const double rr = 1.0 / fma(kr, kr, ki * ki);
+                const double rr = recip64(fma(kr, kr, ki * ki));
                 const double ir = kr * rr, ii = -ki * rr;
 #pragma unroll
                 for (int i = k + 1; i < F; ++i) {
@@ -396,15 +446,24 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
 #pragma unroll
                 for (int a = 0; a < F; ++a) {
                     const double pa = sh.pj[a][ln], qa = sh.qj[a][ln];
-                    const double dq = A.q_eq[x * F + a] - qa, dp = A.p_eq[x * F + a] - pa;
-                    re = fma(-A.qw[a] * dq, dq, re);
-                    re = fma(-A.pw[a] * dp, dp, re);
-                    im = fma(0.5 * (A.p_eq[x * F + a] + pa), dq, im);
+                    const double dq = cc.q_eq[x][a] - qa, dp = cc.p_eq[x][a] - pa;
+                    re = fma(-cc.qw[a] * dq, dq, re);
+                    re = fma(-cc.pw[a] * dp, dp, re);
+                    im = fma(0.5 * (cc.p_eq[x][a] + pa), dq, im);
                 }
                 const double ph = im + S + 0.5 * theta;
-                double sn, cs;
-                sincos(ph, &sn, &cs);
-                const double mag = exp(re);
+                double sn, cs, mag;
+                if constexpr (sizeof(Real) == 4) {
+                    const double red = fma(-kTwoPi, rint(ph * kInvTwoPi), ph);   // FP64 reduction to [-pi, pi]
+                    float sf, cf;
+                    sincosf((float)red, &sf, &cf);
+                    sn = sf;
+                    cs = cf;
+                    mag = (double)expf((float)re);
+                } else {
+                    sincos(ph, &sn, &cs);
+                    mag = exp(re);
+                }
                 L.amp[x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1] = make_double2(mag * cs, mag * sn);
             }
         }
@@ -423,7 +482,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_propagate_lg(const PropLaunch L)
         if (fo.S) fo.S[jl] = sh.Sj[base + ((A.n_steps - 1) % C)];
         if (fo.theta) fo.theta[jl] = theta_last;
         if (fo.detM) fo.detM[jl] = detM_last;
-        if (fo.stab) fo.stab[jl] = stab;
+        if (fo.stab) fo.stab[jl] = (double)stab;
         if (fo.detA) { fo.detA[2 * jl] = detA_last.x; fo.detA[2 * jl + 1] = detA_last.y; }
     }
     if (fo.M && g < N2) {
@@ -444,7 +503,8 @@ cudaError_t launch_lg(const PropLaunch &L, cudaStream_t s)
     constexpr int P = F * (F + 1) / 2;
     constexpr int T = 32 / G;
     const size_t tensors = ((sizeof(Real) * (F * P + P * P)) + 15) & ~(size_t)15;
-    const size_t bytes = tensors + WARPS * sizeof(WarpShared<F, G, Real>);
+    const size_t consts = (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
+    const size_t bytes = tensors + consts + WARPS * sizeof(WarpShared<F, G, Real>);
     auto kern = k_propagate_lg<F, G, Real, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

@@ -30,6 +30,7 @@ struct PropArgs {
     int F, n_steps, n_chi, precision, kernel;
     double dt, stab_tol, ref_step;   // ref_step = sum_i gamma_i dt
     double cdrift[4], dkick[3];      // triple-jump fractions of dt
+    double tdrift[4], tkick[3];      // the sub-step lengths themselves (fraction x dt)
     double gamma[SCIVR_MAX_F];
     double rg[SCIVR_MAX_F];          // sqrt(gamma)
     double irg[SCIVR_MAX_F];         // 1 / sqrt(gamma)
