@@ -161,8 +161,14 @@ int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out)
     const size_t o_T3 = push(T3.data(), T3.size());
     const size_t o_T4 = push(T4.data(), T4.size());
     std::vector<float> T3f(T3.begin(), T3.end()), T4f(T4.begin(), T4.end());
+    std::vector<float> diagf(3 * 64, 0.0f);   // omega, D, a in FP32, 64-float slots
+    for (int i = 0; i < F; ++i) {
+        diagf[i] = (float)d->omega[i];
+        diagf[64 + i] = d->diag_kind == SCIVR_DIAG_MORSE ? (float)d->D[i] : 0.0f;
+        diagf[128 + i] = d->diag_kind == SCIVR_DIAG_MORSE ? (float)d->a[i] : 0.0f;
+    }
     const size_t nd = hostblob.size();
-    const size_t bytes = nd * sizeof(double) + (T3f.size() + T4f.size() + 128) * sizeof(float);
+    const size_t bytes = nd * sizeof(double) + (T3f.size() + T4f.size() + diagf.size() + 256) * sizeof(float);
 
     void *blob = nullptr;
     cudaError_t e = cudaMalloc(&blob, bytes);
@@ -173,6 +179,8 @@ int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out)
     const size_t o_T4f = o_T3f + ((T3f.size() * sizeof(float) + 255) & ~(size_t)255);
     if (e == cudaSuccess) e = cudaMemcpy(b + o_T3f, T3f.data(), T3f.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b + o_T4f, T4f.data(), T4f.size() * sizeof(float), cudaMemcpyHostToDevice);
+    const size_t o_diagf = o_T4f + ((T4f.size() * sizeof(float) + 255) & ~(size_t)255);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_diagf, diagf.data(), diagf.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blob);
         return cuda_fail(e, "scivr_create_pes: cudaMemcpy");
@@ -193,6 +201,9 @@ int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out)
     dv.T4 = db + o_T4;
     dv.T3f = reinterpret_cast<const float *>(b + o_T3f);
     dv.T4f = reinterpret_cast<const float *>(b + o_T4f);
+    dv.omega_f = reinterpret_cast<const float *>(b + o_diagf);
+    dv.D_f = dv.omega_f + 64;
+    dv.a_f = dv.omega_f + 128;
     *out = h;
     ok();
     return SCIVR_OK;
@@ -267,8 +278,9 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
     A.dt = prm->dt;
     A.stab_tol = prm->stab_tol;
     triple_jump(A.cdrift, A.dkick);
-    for (int i = 0; i < 4; ++i) A.tdrift[i] = A.cdrift[i] * prm->dt;
-    for (int i = 0; i < 3; ++i) A.tkick[i] = A.dkick[i] * prm->dt;
+    for (int i = 0; i < 4; ++i) { A.tdrift[i] = A.cdrift[i] * prm->dt; A.tdrift_f[i] = (float)A.tdrift[i]; }
+    for (int i = 0; i < 3; ++i) { A.tkick[i] = A.dkick[i] * prm->dt; A.tkick_f[i] = (float)A.tkick[i]; }
+    A.stab_tol_f = prm->stab_tol > 3.0e38 ? 3.0e38f : (float)prm->stab_tol;
     double ref = 0.0;
     for (int i = 0; i < F; ++i) {
         const double g = prm->gamma[i];

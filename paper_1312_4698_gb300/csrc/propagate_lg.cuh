@@ -69,7 +69,17 @@ template <int F>
 struct CtaConst {
     double rg[F], irg[F], qw[F], pw[F];
     double p_eq[SCIVR_MAX_CHI][F], q_eq[SCIVR_MAX_CHI][F];
+    float rgf[F], irgf[F];                 // FP32 copies: conversions occupy the FP64 pipe
+    float Df[F], af[F], w2f[F];            // diagonal parameters in FP32
+    double Dd[F], ad[F], w2d[F];           // and in FP64
 };
+
+// Real-typed views of the staged constants.
+template <typename Real, int F> __device__ __forceinline__ Real c_rg(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.rgf[i]; else return c.rg[i]; }
+template <typename Real, int F> __device__ __forceinline__ Real c_irg(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.irgf[i]; else return c.irg[i]; }
+template <typename Real, int F> __device__ __forceinline__ Real c_D(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.Df[i]; else return c.Dd[i]; }
+template <typename Real, int F> __device__ __forceinline__ Real c_a(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.af[i]; else return c.ad[i]; }
+template <typename Real, int F> __device__ __forceinline__ Real c_w2(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.w2f[i]; else return c.w2d[i]; }
 
 template <int F, int G, typename Real>
 struct WarpShared {
@@ -123,6 +133,14 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
             cc.irg[a] = A.irg[a];
             cc.qw[a] = A.qw[a];
             cc.pw[a] = A.pw[a];
+            cc.rgf[a] = (float)A.rg[a];
+            cc.irgf[a] = (float)A.irg[a];
+            cc.Dd[a] = pes.D[a];
+            cc.ad[a] = pes.a[a];
+            cc.w2d[a] = pes.omega[a] * pes.omega[a];
+            cc.Df[a] = pes.D_f[a];
+            cc.af[a] = pes.a_f[a];
+            cc.w2f[a] = pes.omega_f[a] * pes.omega_f[a];
         }
 #pragma unroll
         for (int x = 0; x < SCIVR_MAX_CHI; ++x)
@@ -189,7 +207,6 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
         }
     }
 
-    const Real rdt = (Real)A.dt;
     for (int step0 = 0; step0 < A.n_steps; step0 += C) {
         const int cnt = min(C, A.n_steps - step0);
         // ---------------- phase 1: cnt steps, group-parallel ----------------
@@ -199,7 +216,8 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
             for (int sub = 0; sub < 4; ++sub) {
                 // drift: q += tau p, S += tau p.p/2, M_q += tau M_p
                 {
-                    const Real rt = (Real)A.tdrift[sub];
+                    Real rt;
+                    if constexpr (sizeof(Real) == 4) rt = A.tdrift_f[sub]; else rt = A.tdrift[sub];
                     if (g < F) {
                         q = fma(A.tdrift[sub], p, q);
                         dS = fma(rt * Real(0.5) * pr, pr, dS);
@@ -210,7 +228,8 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
                 if (sub == 3) break;
                 // kick: potential at q
                 const double tk = A.tkick[sub];
-                const Real rtk = (Real)tk;
+                Real rtk;
+                if constexpr (sizeof(Real) == 4) rtk = A.tkick_f[sub]; else rtk = tk;
                 __syncwarp();   // previous kick's readers of qr/H are done
                 if (g < F) {
                     sh.qd[t][g] = q;
@@ -241,12 +260,11 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
                         Real hd = Real(0);
                         if (a == b) {
                             if (pes.diag_kind == SCIVR_DIAG_MORSE) {
-                                const Real Dm = (Real)__ldg(pes.D + a), am = (Real)__ldg(pes.a + a);
+                                const Real Dm = c_D<Real>(cc, a), am = c_a<Real>(cc, a);
                                 const Real u = rexp<Real>(-am * sh.qr[t][a]);
                                 hd = Real(2) * Dm * am * am * u * (Real(2) * u - Real(1));
                             } else {
-                                const Real w = (Real)__ldg(pes.omega + a);
-                                hd = w * w;
+                                hd = c_w2<Real>(cc, a);
                             }
                         }
                         const Real h = h3 + h4;
@@ -269,15 +287,15 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
                     }
                     Real Vd, gd;
                     if (pes.diag_kind == SCIVR_DIAG_MORSE) {
-                        const Real Dm = (Real)__ldg(pes.D + g), am = (Real)__ldg(pes.a + g);
+                        const Real Dm = c_D<Real>(cc, g), am = c_a<Real>(cc, g);
                         const Real u = rexp<Real>(-am * sh.qr[t][g]);
                         const Real omu = Real(1) - u;
                         Vd = Dm * omu * omu;
                         gd = Real(2) * Dm * am * u * omu;
                     } else {
-                        const Real w = (Real)__ldg(pes.omega + g);
-                        Vd = Real(0.5) * w * w * sh.qr[t][g] * sh.qr[t][g];
-                        gd = w * w * sh.qr[t][g];
+                        const Real w2 = c_w2<Real>(cc, g);
+                        Vd = Real(0.5) * w2 * sh.qr[t][g] * sh.qr[t][g];
+                        gd = w2 * sh.qr[t][g];
                     }
                     p = fma(-tk, (double)(gr + gd), p);
                     pr = (Real)p;
@@ -324,7 +342,9 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
                 }
                 const Real dev = isfinite(det) ? fabs(fma(det, det, Real(-1))) : Real(CUDART_INF);
                 stab = dev > stab ? dev : stab;
-                if (dev > (Real)A.stab_tol) good = false;
+                Real tolr;
+                if constexpr (sizeof(Real) == 4) tolr = A.stab_tol_f; else tolr = A.stab_tol;
+                if (dev > tolr) good = false;
                 if (c == cnt - 1) detM_last = (double)det;
             }
             // ---- Herman-Kluk matrix column b = g (needs column F + b) ----
@@ -336,8 +356,8 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
                     const Real mpq = __shfl_sync(FULL, Mp[a], src);
                     const Real mqq = __shfl_sync(FULL, Mq[a], src);
                     if (g < F) {
-                        const Real rga = (Real)cc.rg[a], irga = (Real)cc.irg[a];
-                        const Real rgb = (Real)cc.rg[g], irgb = (Real)cc.irg[g];
+                        const Real rga = c_rg<Real>(cc, a), irga = c_irg<Real>(cc, a);
+                        const Real rgb = c_rg<Real>(cc, g), irgb = c_irg<Real>(cc, g);
                         const Real re = fma(rga * irgb, mqq, (rgb * irga) * Mp[a]);
                         const Real im = fma(-(rga * rgb), Mq[a], (irga * irgb) * mpq);
                         R2 v;

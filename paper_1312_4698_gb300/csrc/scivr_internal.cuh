@@ -23,6 +23,7 @@ struct PesDev {
     const double *T3;                // [F][P]
     const double *T4;                // [P][P]
     const float *T3f, *T4f;          // FP32 copies for the mixed-precision path
+    const float *omega_f, *D_f, *a_f;   // FP32 copies of the diagonal parameters
 };
 
 // Kernel-side propagation parameters, passed by value.
@@ -31,6 +32,8 @@ struct PropArgs {
     double dt, stab_tol, ref_step;   // ref_step = sum_i gamma_i dt
     double cdrift[4], dkick[3];      // triple-jump fractions of dt
     double tdrift[4], tkick[3];      // the sub-step lengths themselves (fraction x dt)
+    float tdrift_f[4], tkick_f[3];   // FP32 copies (conversions run on the FP64 pipe on GB300)
+    float stab_tol_f;
     double gamma[SCIVR_MAX_F];
     double rg[SCIVR_MAX_F];          // sqrt(gamma)
     double irg[SCIVR_MAX_F];         // 1 / sqrt(gamma)
