@@ -250,7 +250,7 @@ def main(argv=None):
 
     import torch
     import torch.distributed as dist
-    from paper_1312_4698_gb300 import scivr
+    from paper_1312_4698_gb300 import scivr, shards
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -272,6 +272,7 @@ def main(argv=None):
     ftm = FT_MODES[args.ft]
     tol = MIXED_STAB_TOL if prec == 1 else w8.stab_tol
     ev = {k: [] for k in ("prop0", "prop1", "spec1")}
+    combined = [None]
 
     def one_step(record):
         scivr.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], n, w8.seed, bufs.p0,
@@ -287,9 +288,8 @@ def main(argv=None):
         if record:
             e2 = torch.cuda.Event(enable_timing=True); e2.record(stream); ev["spec1"].append(e2)
         if world > 1:
-            # combine spectra across ranks: sum of n_good * I and of n_good
-            v = torch.cat([bufs.I[0] * bufs.n_good.to(torch.float64), bufs.n_good.to(torch.float64)])
-            dist.all_reduce(v)
+            # combine spectra across ranks: one all-reduce of n_good * I and n_good
+            combined[0] = shards.combine_spectra_async(bufs.I[0], bufs.n_good)
 
     for _ in range(args.warmup):
         flush.zero_()
