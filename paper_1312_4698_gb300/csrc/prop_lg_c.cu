@@ -7,12 +7,12 @@ template <int F> constexpr int group_lanes() { return 2 * F <= 8 ? 8 : (2 * F <=
 
 template <int F> cudaError_t launch_group_mixed(const PropLaunch &L, cudaStream_t s)
 {
-    return launch_lg<F, group_lanes<F>(), float, 4>(L, s);
+    return launch_lg<F, group_lanes<F>(), float, group_lanes<F>() == 32 ? 2 : 4>(L, s);
 }
 
 template <int F> cudaError_t launch_group_fp64(const PropLaunch &L, cudaStream_t s)
 {
-    return launch_lg<F, group_lanes<F>(), double, 4>(L, s);
+    return launch_lg<F, group_lanes<F>(), double, group_lanes<F>() == 32 ? 2 : 4>(L, s);
 }
 
 template cudaError_t launch_group_mixed<7>(const PropLaunch &, cudaStream_t);

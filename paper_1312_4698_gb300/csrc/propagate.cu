@@ -10,7 +10,7 @@ template <int F> cudaError_t launch_group_fp64(const PropLaunch &L, cudaStream_t
 namespace {
 
 constexpr int kMaxThreadF = 9;   // thread-per-trajectory FP64 kernel
-constexpr int kMaxGroupF = 8;    // lane-group kernels (2F <= 16 lanes)
+constexpr int kMaxGroupF = 9;    // lane-group kernels (2F <= 32 lanes)
 
 // Schedule choice when the caller leaves it to the library: the lane-group
 // kernel keeps every SM busy with few trajectories (it launches G lanes per
@@ -46,9 +46,9 @@ cudaError_t launch_propagate(const PropLaunch &L, cudaStream_t s, int *n_launch)
     const int kern = L.args.kernel == SCIVR_KERNEL_AUTO ? choose(L.args.F, L.args.precision, L.n_traj)
                                                           : L.args.kernel;
     if (L.args.precision == SCIVR_MIXED) {
-        switch (L.args.F) { SCIVR_CASES(launch_group_mixed, L) default: break; }
+        switch (L.args.F) { SCIVR_CASES(launch_group_mixed, L) case 9: return launch_group_mixed<9>(L, s); default: break; }
     } else if (kern == SCIVR_KERNEL_GROUP) {
-        switch (L.args.F) { SCIVR_CASES(launch_group_fp64, L) default: break; }
+        switch (L.args.F) { SCIVR_CASES(launch_group_fp64, L) case 9: return launch_group_fp64<9>(L, s); default: break; }
     } else {
         switch (L.args.F) {
             SCIVR_CASES(launch_tpt_fp64, L)

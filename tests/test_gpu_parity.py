@@ -118,7 +118,7 @@ def test_sampler_matches_oracle(G):
     assert np.allclose(w.cpu().numpy(), rw, rtol=1e-12)
 
 
-@pytest.mark.parametrize("F,kernel", [(F, 1) for F in range(1, 10)] + [(F, 2) for F in range(1, 9)])
+@pytest.mark.parametrize("F,kernel", [(F, 1) for F in range(1, 10)] + [(F, 2) for F in range(1, 10)])
 def test_propagate_matches_oracle_small(G, F, kernel):
     """FP64 path, both schedules (1 = thread per trajectory, 2 = lane group),
     every supported F; 70 trajectories (ragged w.r.t. any block size) and a
@@ -334,7 +334,7 @@ def test_propagate_several_reference_states_both_schedules(G, kernel):
 # trajectories of the F=6 workload); spectra within 1 cm^-1 per peak.
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("F", [2, 3, 6, 8])
+@pytest.mark.parametrize("F", [2, 3, 6, 8, 9])
 def test_mixed_propagate_close_to_oracle(G, F):
     w8 = wl.config_f3(n_traj=64, n_steps=400) if F == 3 else wl.config_generic(F, seed=F, n_traj=64, n_steps=400)
     p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, 3)
