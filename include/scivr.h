@@ -193,6 +193,59 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
                    double E_min, double E_max, int32_t n_E, int32_t ft_mode,
                    double *I_out, int64_t *n_good_out, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched runs: many molecules (different F, n_traj, n_steps) in one call    */
+/* ------------------------------------------------------------------------ */
+
+/* One molecule of a batch.  Device pointers as for scivr_propagate and
+ * scivr_spectrum; the host arrays inside prm are copied by scivr_batch_create. */
+typedef struct {
+    scivr_pes pes;
+    scivr_prop_params prm;
+    int64_t n_traj;
+    const double *p0, *q0;        /* device [F][n_traj] */
+    const double *w;              /* device [n_traj] */
+    void *amp;                    /* device complex double [n_chi][n_traj][amp_ld] */
+    int64_t amp_ld;
+    uint8_t *good;                /* device [n_traj] */
+    double E_min, E_max;
+    int32_t n_E;
+    double *I_out;                /* device [n_chi][n_E] */
+    int64_t *n_good_out;          /* device [1], may be NULL */
+} scivr_batch_item;
+
+typedef struct scivr_batch_s *scivr_batch;   /* opaque plan, library-owned */
+
+/* Build a plan for a batch (Sec. III.B: trajectories of all molecules are
+ * independent).  Molecules are grouped by (F, precision); each group runs as
+ * one persistent lane-group launch whose CTAs pull (molecule, trajectory
+ * tile) work items, largest cost first, so molecules of different sizes
+ * share the GPU.  The CTA shape of each group is chosen by the library's
+ * autotuner (timed once per (F, precision, device) and cached, in-process
+ * and in the file named by SCIVR_TUNE_CACHE if set).  All device memory
+ * the launches need (work lists, per-molecule launch records, Fourier
+ * scratch for the largest molecule) is allocated here; the caller's
+ * buffers are not touched until scivr_batch_launch.  ft_mode as for
+ * scivr_spectrum.  Synchronises the device.  Errors: SCIVR_EINVAL (any item
+ * invalid; the message names it), SCIVR_EUNSUPPORTED (F > 9 or precision
+ * not built), SCIVR_ENOMEM, SCIVR_ECUDA. */
+int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t ft_mode,
+                       scivr_batch *out);
+
+/* Enqueue the whole batch on `stream`: per group a counter reset and one
+ * persistent propagation launch, then every molecule's spectra.  Performs
+ * no allocation and no synchronisation, so a stream capture of this call
+ * yields a CUDA graph that can be replayed while the plan lives. */
+int scivr_batch_launch(scivr_batch b, void *stream);
+
+/* Number of propagation groups of a plan and, for group g, its F, precision
+ * and the CTA warps the autotuner chose (any pointer may be NULL). */
+int scivr_batch_info(scivr_batch b, int32_t g, int32_t *n_groups, int32_t *F, int32_t *precision,
+                     int32_t *warps);
+
+/* Free a plan (synchronises the device).  NULL is accepted. */
+int scivr_batch_destroy(scivr_batch b);
+
 /* Same result as scivr_spectrum (same arguments, same checks) without allocating
  * any device memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc or cudaMallocAsync -- processes whose

@@ -70,6 +70,106 @@ void triple_jump(double c[4], double d[3])
 
 }  // namespace
 
+namespace scivr {
+
+// Validate scivr_propagate's arguments and fill the kernel launch record.
+// Returns SCIVR_OK or an error code (with the message set).
+int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj, const double *p0,
+                      const double *q0, void *amp, int64_t amp_ld, uint8_t *good,
+                      const scivr_final_state *fin, PropLaunch *out)
+{
+    if (!pes || !prm) return fail(SCIVR_EINVAL, "scivr_propagate: NULL potential or parameters");
+    const int F = pes->dev.F;
+    if (!p0 || !q0 || !amp || !good) return fail(SCIVR_EINVAL, "scivr_propagate: NULL device pointer");
+    if (n_traj < 1) return fail(SCIVR_EINVAL, "scivr_propagate: n_traj=%lld < 1", (long long)n_traj);
+    if (prm->n_steps < 1) return fail(SCIVR_EINVAL, "scivr_propagate: n_steps=%d < 1", prm->n_steps);
+    if (!(prm->dt > 0.0) || !std::isfinite(prm->dt)) return fail(SCIVR_EINVAL, "scivr_propagate: dt must be positive");
+    if (!(prm->stab_tol >= 0.0)) return fail(SCIVR_EINVAL, "scivr_propagate: stab_tol must be >= 0");
+    if (prm->n_chi < 1 || prm->n_chi > SCIVR_MAX_CHI)
+        return fail(SCIVR_EINVAL, "scivr_propagate: n_chi=%d not in [1,%d]", prm->n_chi, SCIVR_MAX_CHI);
+    if (!prm->gamma || !prm->p_eq || !prm->q_eq) return fail(SCIVR_EINVAL, "scivr_propagate: NULL gamma/chi");
+    if (!all_positive_finite(prm->gamma, F)) return fail(SCIVR_EINVAL, "scivr_propagate: gamma must be positive");
+    if (!all_finite(prm->p_eq, F * prm->n_chi) || !all_finite(prm->q_eq, F * prm->n_chi))
+        return fail(SCIVR_EINVAL, "scivr_propagate: chi not finite");
+    if (amp_ld < (int64_t)prm->n_steps + 1)
+        return fail(SCIVR_EINVAL, "scivr_propagate: amp_ld=%lld < n_steps+1", (long long)amp_ld);
+    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "scivr_propagate: amp not 16-byte aligned");
+    if (prm->precision != SCIVR_FP64 && prm->precision != SCIVR_MIXED)
+        return fail(SCIVR_EINVAL, "scivr_propagate: precision %d invalid", prm->precision);
+    if (prm->kernel < SCIVR_KERNEL_AUTO || prm->kernel > SCIVR_KERNEL_GROUP)
+        return fail(SCIVR_EINVAL, "scivr_propagate: kernel %d invalid", prm->kernel);
+    if (!propagate_supported(F, prm->precision, prm->kernel))
+        return fail(SCIVR_EUNSUPPORTED, "scivr_propagate: precision %d / kernel %d not built for F=%d",
+                    prm->precision, prm->kernel, F);
+
+    PropLaunch L{};
+    L.pes = pes->dev;
+    PropArgs &A = L.args;
+    A.F = F;
+    A.n_steps = prm->n_steps;
+    A.n_chi = prm->n_chi;
+    A.precision = prm->precision;
+    A.kernel = prm->kernel;
+    A.dt = prm->dt;
+    A.stab_tol = prm->stab_tol;
+    triple_jump(A.cdrift, A.dkick);
+    for (int i = 0; i < 4; ++i) { A.tdrift[i] = A.cdrift[i] * prm->dt; A.tdrift_f[i] = (float)A.tdrift[i]; }
+    for (int i = 0; i < 3; ++i) { A.tkick[i] = A.dkick[i] * prm->dt; A.tkick_f[i] = (float)A.tkick[i]; }
+    A.stab_tol_f = prm->stab_tol > 3.0e38 ? 3.0e38f : (float)prm->stab_tol;
+    double ref = 0.0;
+    for (int i = 0; i < F; ++i) {
+        const double g = prm->gamma[i];
+        A.gamma[i] = g;
+        A.rg[i] = std::sqrt(g);
+        A.irg[i] = 1.0 / std::sqrt(g);
+        A.qw[i] = 0.25 * g;
+        A.pw[i] = 0.25 / g;
+        ref += g * prm->dt;
+    }
+    A.ref_step = ref;
+    for (int i = 0; i < F * prm->n_chi; ++i) {
+        A.p_eq[i] = prm->p_eq[i];
+        A.q_eq[i] = prm->q_eq[i];
+    }
+    L.n_traj = n_traj;
+    L.p0 = p0;
+    L.q0 = q0;
+    L.amp = static_cast<double2 *>(amp);
+    L.amp_ld = amp_ld;
+    L.chi_stride = n_traj * amp_ld;
+    L.good = good;
+    if (fin) L.fin = FinalDev{fin->p, fin->q, fin->S, fin->theta, fin->detM, fin->detA, fin->M, fin->stab};
+    *out = L;
+    return SCIVR_OK;
+}
+
+// Validate scivr_spectrum's arguments (shared with the batch path).
+int check_spectrum_args(const void *amp, int64_t amp_ld, int32_t amp_prec, const double *w, const uint8_t *good,
+                        int64_t n_traj, int32_t n_steps, double dt, double E_min, double E_max, int32_t n_E,
+                        int32_t ft_mode, const double *I_out)
+{
+    if (!amp || !w || !good || !I_out) return fail(SCIVR_EINVAL, "scivr_spectrum: NULL device pointer");
+    if (n_traj < 1) return fail(SCIVR_EINVAL, "scivr_spectrum: n_traj=%lld < 1", (long long)n_traj);
+    if (n_steps < 1) return fail(SCIVR_EINVAL, "scivr_spectrum: n_steps=%d < 1", n_steps);
+    if (n_E < 2) return fail(SCIVR_EINVAL, "scivr_spectrum: n_E=%d < 2", n_E);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SCIVR_EINVAL, "scivr_spectrum: dt must be positive");
+    if (!std::isfinite(E_min) || !std::isfinite(E_max) || !(E_max > E_min))
+        return fail(SCIVR_EINVAL, "scivr_spectrum: need finite E_min < E_max");
+    if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "scivr_spectrum: amp_ld < n_steps+1");
+    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "scivr_spectrum: amp not 16-byte aligned");
+    if (amp_prec != SCIVR_FP64) return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: amp_prec %d not supported", amp_prec);
+    if (ft_mode != SCIVR_FT_FP64 && ft_tc_digits(ft_mode) == 0)
+        return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: ft_mode %d not supported", ft_mode);
+    return SCIVR_OK;
+}
+
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+void clear_error() { ok(); }
+void count_launches(int n) { g_launches += n; }
+int cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+
+}  // namespace scivr
+
 extern "C" {
 
 const char *scivr_last_error(void) { return g_last_error.c_str(); }
@@ -243,67 +343,9 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
                     const double *q0, void *amp, int64_t amp_ld, uint8_t *good,
                     const scivr_final_state *fin, void *stream)
 {
-    if (!pes || !prm) return fail(SCIVR_EINVAL, "scivr_propagate: NULL potential or parameters");
-    const int F = pes->dev.F;
-    if (!p0 || !q0 || !amp || !good) return fail(SCIVR_EINVAL, "scivr_propagate: NULL device pointer");
-    if (n_traj < 1) return fail(SCIVR_EINVAL, "scivr_propagate: n_traj=%lld < 1", (long long)n_traj);
-    if (prm->n_steps < 1) return fail(SCIVR_EINVAL, "scivr_propagate: n_steps=%d < 1", prm->n_steps);
-    if (!(prm->dt > 0.0) || !std::isfinite(prm->dt)) return fail(SCIVR_EINVAL, "scivr_propagate: dt must be positive");
-    if (!(prm->stab_tol >= 0.0)) return fail(SCIVR_EINVAL, "scivr_propagate: stab_tol must be >= 0");
-    if (prm->n_chi < 1 || prm->n_chi > SCIVR_MAX_CHI)
-        return fail(SCIVR_EINVAL, "scivr_propagate: n_chi=%d not in [1,%d]", prm->n_chi, SCIVR_MAX_CHI);
-    if (!prm->gamma || !prm->p_eq || !prm->q_eq) return fail(SCIVR_EINVAL, "scivr_propagate: NULL gamma/chi");
-    if (!all_positive_finite(prm->gamma, F)) return fail(SCIVR_EINVAL, "scivr_propagate: gamma must be positive");
-    if (!all_finite(prm->p_eq, F * prm->n_chi) || !all_finite(prm->q_eq, F * prm->n_chi))
-        return fail(SCIVR_EINVAL, "scivr_propagate: chi not finite");
-    if (amp_ld < (int64_t)prm->n_steps + 1)
-        return fail(SCIVR_EINVAL, "scivr_propagate: amp_ld=%lld < n_steps+1", (long long)amp_ld);
-    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "scivr_propagate: amp not 16-byte aligned");
-    if (prm->precision != SCIVR_FP64 && prm->precision != SCIVR_MIXED)
-        return fail(SCIVR_EINVAL, "scivr_propagate: precision %d invalid", prm->precision);
-    if (prm->kernel < SCIVR_KERNEL_AUTO || prm->kernel > SCIVR_KERNEL_GROUP)
-        return fail(SCIVR_EINVAL, "scivr_propagate: kernel %d invalid", prm->kernel);
-    if (!propagate_supported(F, prm->precision, prm->kernel))
-        return fail(SCIVR_EUNSUPPORTED, "scivr_propagate: precision %d / kernel %d not built for F=%d",
-                    prm->precision, prm->kernel, F);
-
     PropLaunch L{};
-    L.pes = pes->dev;
-    PropArgs &A = L.args;
-    A.F = F;
-    A.n_steps = prm->n_steps;
-    A.n_chi = prm->n_chi;
-    A.precision = prm->precision;
-    A.kernel = prm->kernel;
-    A.dt = prm->dt;
-    A.stab_tol = prm->stab_tol;
-    triple_jump(A.cdrift, A.dkick);
-    for (int i = 0; i < 4; ++i) { A.tdrift[i] = A.cdrift[i] * prm->dt; A.tdrift_f[i] = (float)A.tdrift[i]; }
-    for (int i = 0; i < 3; ++i) { A.tkick[i] = A.dkick[i] * prm->dt; A.tkick_f[i] = (float)A.tkick[i]; }
-    A.stab_tol_f = prm->stab_tol > 3.0e38 ? 3.0e38f : (float)prm->stab_tol;
-    double ref = 0.0;
-    for (int i = 0; i < F; ++i) {
-        const double g = prm->gamma[i];
-        A.gamma[i] = g;
-        A.rg[i] = std::sqrt(g);
-        A.irg[i] = 1.0 / std::sqrt(g);
-        A.qw[i] = 0.25 * g;
-        A.pw[i] = 0.25 / g;
-        ref += g * prm->dt;
-    }
-    A.ref_step = ref;
-    for (int i = 0; i < F * prm->n_chi; ++i) {
-        A.p_eq[i] = prm->p_eq[i];
-        A.q_eq[i] = prm->q_eq[i];
-    }
-    L.n_traj = n_traj;
-    L.p0 = p0;
-    L.q0 = q0;
-    L.amp = static_cast<double2 *>(amp);
-    L.amp_ld = amp_ld;
-    L.chi_stride = n_traj * amp_ld;
-    L.good = good;
-    if (fin) L.fin = FinalDev{fin->p, fin->q, fin->S, fin->theta, fin->detM, fin->detA, fin->M, fin->stab};
+    const int rc = prepare_propagate(pes, prm, n_traj, p0, q0, amp, amp_ld, good, fin, &L);
+    if (rc != SCIVR_OK) return rc;
     int nl = 0;
     cudaError_t e = launch_propagate(L, static_cast<cudaStream_t>(stream), &nl);
     g_launches += nl;
@@ -317,18 +359,11 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
                    double E_max, int32_t n_E, int32_t ft_mode, double *I_out, int64_t *n_good_out,
                    void *stream)
 {
-    if (!amp || !w || !good || !I_out) return fail(SCIVR_EINVAL, "scivr_spectrum: NULL device pointer");
-    if (n_traj < 1) return fail(SCIVR_EINVAL, "scivr_spectrum: n_traj=%lld < 1", (long long)n_traj);
-    if (n_steps < 1) return fail(SCIVR_EINVAL, "scivr_spectrum: n_steps=%d < 1", n_steps);
-    if (n_E < 2) return fail(SCIVR_EINVAL, "scivr_spectrum: n_E=%d < 2", n_E);
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SCIVR_EINVAL, "scivr_spectrum: dt must be positive");
-    if (!std::isfinite(E_min) || !std::isfinite(E_max) || !(E_max > E_min))
-        return fail(SCIVR_EINVAL, "scivr_spectrum: need finite E_min < E_max");
-    if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "scivr_spectrum: amp_ld < n_steps+1");
-    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "scivr_spectrum: amp not 16-byte aligned");
-    if (amp_prec != SCIVR_FP64) return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: amp_prec %d not supported", amp_prec);
-    if (ft_mode != SCIVR_FT_FP64 && ft_tc_digits(ft_mode) == 0)
-        return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: ft_mode %d not supported", ft_mode);
+    {
+        const int rc = check_spectrum_args(amp, amp_ld, amp_prec, w, good, n_traj, n_steps, dt, E_min, E_max, n_E,
+                                           ft_mode, I_out);
+        if (rc != SCIVR_OK) return rc;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (ft_mode != SCIVR_FT_FP64) {
         const size_t tb = spectrum_tc_scratch_bytes(ft_mode, n_traj, n_steps, n_E);

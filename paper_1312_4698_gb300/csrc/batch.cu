@@ -1,0 +1,342 @@
+// Batched runs (scivr_batch_*): many molecules with different F, trajectory
+// counts and step counts.  Trajectories of all molecules are independent
+// (Sec. III.B of arXiv:1312.4698), so the plan groups molecules by
+// (F, precision) and runs each mixed-precision group as one persistent
+// lane-group launch whose CTAs pull (molecule, tile) work items, the
+// longest first.  FP64 molecules are launched one by one.  Each molecule's
+// spectra follow.  The launch sequence allocates nothing and never
+// synchronises, so it can be captured into a CUDA graph.
+//
+// The CTA shape (warps per CTA) of each group is picked by timing the
+// candidates on a short probe of the group's first molecule (64 steps,
+// enough trajectories to fill the GPU) and cached per (F, precision,
+// device name) in-process and, when SCIVR_TUNE_CACHE names a file, on disk.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "scivr_internal.cuh"
+
+namespace {
+
+using namespace scivr;
+
+struct Group {
+    int F = 0, precision = 0, warps = 0;
+    std::vector<int> members;          // indices into the plan's items
+    PropLaunch *d_items = nullptr;
+    int2 *d_work = nullptr;
+    int n_work = 0;
+    int *d_counter = nullptr;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tuned;
+
+std::string tune_key(int F, int precision)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp p{};
+    cudaGetDeviceProperties(&p, dev);
+    std::string name = p.name;
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    return "F" + std::to_string(F) + ":prec" + std::to_string(precision) + ":" + name;
+}
+
+void load_tune_file()
+{
+    const char *path = std::getenv("SCIVR_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int w = 0;
+    while (std::fscanf(f, "%255s %d", key, &w) == 2) g_tuned[key] = w;
+    std::fclose(f);
+}
+
+void save_tune_file()
+{
+    const char *path = std::getenv("SCIVR_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return;
+    for (auto &kv : g_tuned) std::fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+    std::fclose(f);
+}
+
+// Time one candidate CTA shape on a probe copy of launch record L.
+cudaError_t time_candidate(const PropLaunch &L, int warps, int n_sm, float *ms)
+{
+    const int G = 2 * L.args.F <= 8 ? 8 : (2 * L.args.F <= 16 ? 16 : 32);
+    const int per_tile = warps * (32 / G);
+    PropLaunch P = L;
+    P.args.n_steps = std::min(L.args.n_steps, 64);
+    P.n_traj = std::min<int64_t>(L.n_traj, (int64_t)n_sm * 4 * per_tile);
+    P.amp_ld = P.args.n_steps + 1;
+    P.chi_stride = P.n_traj * P.amp_ld;
+    P.fin = FinalDev{};
+    const int tiles = (int)((P.n_traj + per_tile - 1) / per_tile);
+    std::vector<int2> work(tiles);
+    for (int i = 0; i < tiles; ++i) work[i] = make_int2(0, i);
+    void *mem = nullptr;
+    const size_t amp_bytes = sizeof(double2) * (size_t)P.args.n_chi * P.chi_stride;
+    const size_t bytes = amp_bytes + P.n_traj + sizeof(PropLaunch) + sizeof(int2) * tiles + 256 * 4;
+    cudaError_t e = cudaMalloc(&mem, bytes);
+    if (e != cudaSuccess) return e;
+    char *b = static_cast<char *>(mem);
+    P.amp = reinterpret_cast<double2 *>(b);
+    P.good = reinterpret_cast<uint8_t *>(b + amp_bytes);
+    size_t off = (amp_bytes + P.n_traj + 255) & ~(size_t)255;
+    PropLaunch *d_items = reinterpret_cast<PropLaunch *>(b + off);
+    off = (off + sizeof(PropLaunch) + 255) & ~(size_t)255;
+    int2 *d_work = reinterpret_cast<int2 *>(b + off);
+    off = (off + sizeof(int2) * tiles + 255) & ~(size_t)255;
+    int *d_counter = reinterpret_cast<int *>(b + off);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaMemcpy(d_items, &P, sizeof(PropLaunch), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_work, work.data(), sizeof(int2) * tiles, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        e = cudaMemset(d_counter, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+        if (e == cudaSuccess) e = launch_group_batch_mixed(P.args.F, warps, d_items, d_work, tiles, d_counter, n_sm, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && rep > 0) best = std::min(best, t);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(mem);
+    *ms = best;
+    return e;
+}
+
+cudaError_t choose_warps(const PropLaunch &L, int precision, int n_sm, int *warps)
+{
+    int cand[2];
+    const int nc = batch_warp_candidates(L.args.F, cand);
+    if (nc == 0) return cudaErrorInvalidValue;
+    const std::string key = tune_key(L.args.F, precision);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tuned.empty()) load_tune_file();
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end() && (it->second == cand[0] || it->second == cand[1])) {
+            *warps = it->second;
+            return cudaSuccess;
+        }
+    }
+    int best_w = cand[0];
+    float best_t = 1e30f;
+    for (int i = 0; i < nc; ++i) {
+        float t = 0.0f;
+        cudaError_t e = time_candidate(L, cand[i], n_sm, &t);
+        if (e != cudaSuccess) return e;
+        if (t < best_t) { best_t = t; best_w = cand[i]; }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best_w;
+    save_tune_file();
+    *warps = best_w;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+struct scivr_batch_s {
+    std::vector<scivr_batch_item> items;
+    std::vector<PropLaunch> launches;     // one per item
+    std::vector<Group> groups;            // mixed-precision persistent groups
+    std::vector<int> fp64_items;          // launched one by one
+    int ft_mode = 0;
+    int n_sm = 0;
+    void *blob = nullptr;                 // work lists, launch records, counters
+    void *scratch = nullptr;              // Fourier scratch for the largest molecule
+};
+
+extern "C" {
+
+int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t ft_mode, scivr_batch *out)
+{
+    if (!items || !out || n_items < 1) return set_error(SCIVR_EINVAL, "scivr_batch_create: need items and n_items >= 1");
+    *out = nullptr;
+    if (ft_mode != SCIVR_FT_FP64 && ft_tc_digits(ft_mode) == 0)
+        return set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: ft_mode not supported");
+    scivr_batch_s *B = new scivr_batch_s;
+    B->ft_mode = ft_mode;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&B->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    size_t scratch = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const scivr_batch_item &it = items[i];
+        PropLaunch L{};
+        int rc = prepare_propagate(it.pes, &it.prm, it.n_traj, it.p0, it.q0, it.amp, it.amp_ld, it.good, nullptr, &L);
+        if (rc == SCIVR_OK)
+            rc = check_spectrum_args(it.amp, it.amp_ld, SCIVR_FP64, it.w, it.good, it.n_traj, it.prm.n_steps,
+                                     it.prm.dt, it.E_min, it.E_max, it.n_E, ft_mode, it.I_out);
+        if (rc == SCIVR_OK && it.prm.precision == SCIVR_MIXED && it.pes->dev.F > 9)
+            rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: mixed precision is built for F <= 9");
+        if (rc != SCIVR_OK) {
+            char msg[600];
+            std::snprintf(msg, sizeof msg, "scivr_batch_create: item %d: %s", i, scivr_last_error());
+            delete B;
+            return set_error(rc, msg);
+        }
+        B->items.push_back(it);
+        B->launches.push_back(L);
+        const size_t sb = ft_mode == SCIVR_FT_FP64 ? spectrum_fp64_scratch_bytes(it.n_traj, it.prm.n_steps, it.n_E)
+                                                   : spectrum_tc_scratch_bytes(ft_mode, it.n_traj, it.prm.n_steps, it.n_E);
+        scratch = std::max(scratch, sb);
+    }
+    // groups
+    std::map<int, int> gidx;
+    for (int i = 0; i < n_items; ++i) {
+        const PropLaunch &L = B->launches[i];
+        if (L.args.precision != SCIVR_MIXED) { B->fp64_items.push_back(i); continue; }
+        auto f = gidx.find(L.args.F);
+        if (f == gidx.end()) {
+            gidx[L.args.F] = (int)B->groups.size();
+            Group g;
+            g.F = L.args.F;
+            g.precision = SCIVR_MIXED;
+            B->groups.push_back(g);
+            f = gidx.find(L.args.F);
+        }
+        B->groups[f->second].members.push_back(i);
+    }
+    // autotune each group's CTA shape, then build its work list
+    size_t blob_bytes = 0;
+    std::vector<std::vector<int2>> works(B->groups.size());
+    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+        Group &g = B->groups[gi];
+        cudaError_t e = choose_warps(B->launches[g.members[0]], g.precision, B->n_sm, &g.warps);
+        if (e != cudaSuccess) {
+            delete B;
+            return cuda_error(e, "scivr_batch_create: autotune");
+        }
+        const int G = 2 * g.F <= 8 ? 8 : (2 * g.F <= 16 ? 16 : 32);
+        const int per_tile = g.warps * (32 / G);
+        std::vector<int2> &w = works[gi];
+        for (int k = 0; k < (int)g.members.size(); ++k) {
+            const PropLaunch &L = B->launches[g.members[k]];
+            const int tiles = (int)((L.n_traj + per_tile - 1) / per_tile);
+            for (int t = 0; t < tiles; ++t) w.push_back(make_int2(k, t));
+        }
+        std::stable_sort(w.begin(), w.end(), [&](const int2 &a, const int2 &b) {
+            return B->launches[g.members[a.x]].args.n_steps > B->launches[g.members[b.x]].args.n_steps;
+        });
+        g.n_work = (int)w.size();
+        blob_bytes += ((sizeof(PropLaunch) * g.members.size() + 255) & ~(size_t)255) +
+                      ((sizeof(int2) * w.size() + 255) & ~(size_t)255) + 256;
+    }
+    cudaError_t e = cudaSuccess;
+    if (blob_bytes) e = cudaMalloc(&B->blob, blob_bytes);
+    if (e == cudaSuccess && scratch) e = cudaMalloc(&B->scratch, scratch);
+    char *b = static_cast<char *>(B->blob);
+    for (size_t gi = 0; gi < B->groups.size() && e == cudaSuccess; ++gi) {
+        Group &g = B->groups[gi];
+        std::vector<PropLaunch> recs;
+        for (int m : g.members) recs.push_back(B->launches[m]);
+        g.d_items = reinterpret_cast<PropLaunch *>(b);
+        b += (sizeof(PropLaunch) * recs.size() + 255) & ~(size_t)255;
+        g.d_work = reinterpret_cast<int2 *>(b);
+        b += (sizeof(int2) * works[gi].size() + 255) & ~(size_t)255;
+        g.d_counter = reinterpret_cast<int *>(b);
+        b += 256;
+        e = cudaMemcpy(g.d_items, recs.data(), sizeof(PropLaunch) * recs.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_work, works[gi].data(), sizeof(int2) * works[gi].size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        if (B->blob) cudaFree(B->blob);
+        if (B->scratch) cudaFree(B->scratch);
+        delete B;
+        return cuda_error(e, "scivr_batch_create: device setup");
+    }
+    *out = B;
+    clear_error();
+    return SCIVR_OK;
+}
+
+int scivr_batch_launch(scivr_batch B, void *stream)
+{
+    if (!B) return set_error(SCIVR_EINVAL, "scivr_batch_launch: NULL plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    int launches = 0;
+    for (const Group &g : B->groups) {
+        e = cudaMemsetAsync(g.d_counter, 0, sizeof(int), s);
+        if (e == cudaSuccess)
+            e = launch_group_batch_mixed(g.F, g.warps, g.d_items, g.d_work, g.n_work, g.d_counter, B->n_sm, s);
+        if (e != cudaSuccess) return cuda_error(e, "scivr_batch_launch: propagation group");
+        ++launches;
+    }
+    for (int i : B->fp64_items) {
+        int nl = 0;
+        e = launch_propagate(B->launches[i], s, &nl);
+        launches += nl;
+        if (e != cudaSuccess) return cuda_error(e, "scivr_batch_launch: FP64 propagation");
+    }
+    for (size_t i = 0; i < B->items.size(); ++i) {
+        const scivr_batch_item &it = B->items[i];
+        for (int x = 0; x < it.prm.n_chi; ++x) {
+            const double2 *amp = static_cast<const double2 *>(it.amp) + (int64_t)x * it.n_traj * it.amp_ld;
+            double *I = it.I_out + (int64_t)x * it.n_E;
+            int nl = 0;
+            if (B->ft_mode == SCIVR_FT_FP64)
+                e = launch_spectrum_fp64(amp, it.amp_ld, it.w, it.good, it.n_traj, it.prm.n_steps, it.prm.dt,
+                                         it.E_min, it.E_max, it.n_E, I, it.n_good_out, B->scratch, s, &nl);
+            else
+                e = launch_spectrum_tc(B->ft_mode, amp, it.amp_ld, it.w, it.good, it.n_traj, it.prm.n_steps,
+                                       it.prm.dt, it.E_min, it.E_max, it.n_E, I, it.n_good_out, B->scratch, s, &nl);
+            launches += nl;
+            if (e != cudaSuccess) return cuda_error(e, "scivr_batch_launch: spectrum");
+        }
+    }
+    count_launches(launches);
+    clear_error();
+    return SCIVR_OK;
+}
+
+int scivr_batch_info(scivr_batch B, int32_t g, int32_t *n_groups, int32_t *F, int32_t *precision, int32_t *warps)
+{
+    if (!B) return set_error(SCIVR_EINVAL, "scivr_batch_info: NULL plan");
+    if (n_groups) *n_groups = (int32_t)B->groups.size();
+    if (g >= 0 && g < (int32_t)B->groups.size()) {
+        if (F) *F = B->groups[g].F;
+        if (precision) *precision = B->groups[g].precision;
+        if (warps) *warps = B->groups[g].warps;
+    } else if (F || precision || warps) {
+        return set_error(SCIVR_EINVAL, "scivr_batch_info: group index out of range");
+    }
+    clear_error();
+    return SCIVR_OK;
+}
+
+int scivr_batch_destroy(scivr_batch B)
+{
+    if (!B) { clear_error(); return SCIVR_OK; }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (B->blob) cudaFree(B->blob);
+    if (B->scratch) cudaFree(B->scratch);
+    delete B;
+    if (e != cudaSuccess) return cuda_error(e, "scivr_batch_destroy: synchronize");
+    clear_error();
+    return SCIVR_OK;
+}
+
+}  // extern "C"

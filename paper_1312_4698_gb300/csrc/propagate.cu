@@ -6,6 +6,28 @@ namespace scivr {
 template <int F> cudaError_t launch_tpt_fp64(const PropLaunch &L, cudaStream_t s);
 template <int F> cudaError_t launch_group_mixed(const PropLaunch &L, cudaStream_t s);
 template <int F> cudaError_t launch_group_fp64(const PropLaunch &L, cudaStream_t s);
+template <int F>
+cudaError_t launch_group_batch_mixed_F(int warps, const PropLaunch *items, const int2 *work, int n_work,
+                                      int *counter, int n_sm, cudaStream_t s);
+
+int batch_warp_candidates(int F, int *out)
+{
+    if (F < 1 || F > 9) return 0;
+    if (2 * F > 16) { out[0] = 1; out[1] = 2; }
+    else { out[0] = 2; out[1] = 4; }
+    return 2;
+}
+
+cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, const int2 *work, int n_work,
+                                     int *counter, int n_sm, cudaStream_t s)
+{
+    switch (F) {
+#define SCIVR_B(FF) case FF: return launch_group_batch_mixed_F<FF>(warps, items, work, n_work, counter, n_sm, s);
+    SCIVR_B(1) SCIVR_B(2) SCIVR_B(3) SCIVR_B(4) SCIVR_B(5) SCIVR_B(6) SCIVR_B(7) SCIVR_B(8) SCIVR_B(9)
+#undef SCIVR_B
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 namespace {
 

@@ -95,8 +95,12 @@ struct WarpShared {
     double Sj[32];                          // action per job
 };
 
+// One CTA's share of a propagation: trajectories (cta * WARPS + warp) * T + t.
+// Called by the per-molecule kernel (cta = blockIdx.x) and by the batched
+// persistent kernel (cta = the work item's tile).  Stages the molecule's
+// constants itself and leaves shared memory free for the next call.
 template <int F, int G, typename Real, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch L)
+__device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsigned char *smem_raw)
 {
     constexpr int N2 = 2 * F;
     constexpr int P = F * (F + 1) / 2;
@@ -107,7 +111,6 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
     using Sh = WarpShared<F, G, Real>;
     using R2 = typename Vec2<Real>::T;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *sT3 = reinterpret_cast<Real *>(smem_raw);
     Real *sT4 = sT3 + F * P;
     size_t off = ((sizeof(Real) * (F * P + P * P)) + 15) & ~(size_t)15;
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
     const int t = ln / G, g = ln % G, base = t * G;
     Sh &sh = wsh_all[warp];
     const int64_t n = L.n_traj;
-    const int64_t j_traj = ((int64_t)blockIdx.x * WARPS + warp) * T + t;
+    const int64_t j_traj = (cta * WARPS + warp) * T + t;
     const bool active = j_traj < n;
     const int64_t jl = active ? j_traj : n - 1;
 
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
         __syncwarp();
     }
 
-    if (!active) return;
+    if (active) {
     if (g == 0) L.good[jl] = good ? 1 : 0;
     const FinalDev &fo = L.fin;
     if (g < F) {
@@ -512,19 +515,76 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
             fo.M[jl * N2 * N2 + (F + a) * N2 + g] = (double)Mq[a];
         }
     }
+    }
+    __syncthreads();   // the caller may restage shared memory next
+}
+
+template <int F, int G, typename Real, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    lg_body<F, G, Real, WARPS>(L, blockIdx.x, smem_raw);
+}
+
+// Batched persistent kernel: CTAs pull (molecule, tile) work items from a
+// list sorted by decreasing cost until it is exhausted.  items: device array
+// of per-molecule launches (all of this F); work: (item, tile) pairs.
+template <int F, int G, typename Real, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg_batch(const PropLaunch *__restrict__ items,
+                                                                       const int2 *__restrict__ work,
+                                                                       int n_work, int *__restrict__ counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int next;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = next;
+        __syncthreads();
+        if (w >= n_work) break;
+        const int2 it = work[w];
+        lg_body<F, G, Real, WARPS>(items[it.x], it.y, smem_raw);
+    }
 }
 
 }  // namespace lg
 
 template <int F, int G, typename Real, int WARPS>
-cudaError_t launch_lg(const PropLaunch &L, cudaStream_t s)
+size_t lg_smem_bytes()
 {
     using namespace lg;
     constexpr int P = F * (F + 1) / 2;
-    constexpr int T = 32 / G;
     const size_t tensors = ((sizeof(Real) * (F * P + P * P)) + 15) & ~(size_t)15;
     const size_t consts = (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
-    const size_t bytes = tensors + consts + WARPS * sizeof(WarpShared<F, G, Real>);
+    return tensors + consts + WARPS * sizeof(WarpShared<F, G, Real>);
+}
+
+template <int F, int G, typename Real, int WARPS>
+cudaError_t launch_lg_batch(const PropLaunch *items, const int2 *work, int n_work, int *counter, int n_sm,
+                            cudaStream_t s)
+{
+    using namespace lg;
+    const size_t bytes = lg_smem_bytes<F, G, Real, WARPS>();
+    auto kern = k_propagate_lg_batch<F, G, Real, WARPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WARPS, bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid = n_sm * per_sm;
+    if (grid > n_work) grid = n_work;
+    if (grid < 1) return cudaSuccess;
+    kern<<<grid, 32 * WARPS, bytes, s>>>(items, work, n_work, counter);
+    return cudaGetLastError();
+}
+
+template <int F, int G, typename Real, int WARPS>
+cudaError_t launch_lg(const PropLaunch &L, cudaStream_t s)
+{
+    using namespace lg;
+    constexpr int T = 32 / G;
+    const size_t bytes = lg_smem_bytes<F, G, Real, WARPS>();
     auto kern = k_propagate_lg<F, G, Real, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

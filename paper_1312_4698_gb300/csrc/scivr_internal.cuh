@@ -84,6 +84,21 @@ cudaError_t launch_wait_selftest(double seconds, cudaStream_t s);
 cudaError_t read_and_clear_status(int *status);
 
 bool propagate_supported(int F, int precision, int kernel);
+int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj, const double *p0,
+                      const double *q0, void *amp, int64_t amp_ld, uint8_t *good,
+                      const scivr_final_state *fin, PropLaunch *out);
+int check_spectrum_args(const void *amp, int64_t amp_ld, int32_t amp_prec, const double *w, const uint8_t *good,
+                        int64_t n_traj, int32_t n_steps, double dt, double E_min, double E_max, int32_t n_E,
+                        int32_t ft_mode, const double *I_out);
+int set_error(int code, const char *msg);
+void clear_error();
+void count_launches(int n);
+int cuda_error(cudaError_t e, const char *where);
+// Batched persistent lane-group launch for mixed precision; warps must be one of
+// batch_warp_candidates(F).
+cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, const int2 *work, int n_work,
+                                     int *counter, int n_sm, cudaStream_t s);
+int batch_warp_candidates(int F, int *out);   // returns the count (<= 2)
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kInvTwoPi = 0.15915494309189533576888376337251;

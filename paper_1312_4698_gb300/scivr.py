@@ -72,6 +72,14 @@ class scivr_final_state(C.Structure):
                 ("stab", C.c_void_p)]
 
 
+class scivr_batch_item(C.Structure):
+    _fields_ = [("pes", C.c_void_p), ("prm", scivr_prop_params), ("n_traj", C.c_int64),
+                ("p0", C.c_void_p), ("q0", C.c_void_p), ("w", C.c_void_p), ("amp", C.c_void_p),
+                ("amp_ld", C.c_int64), ("good", C.c_void_p), ("E_min", C.c_double),
+                ("E_max", C.c_double), ("n_E", C.c_int32), ("I_out", C.c_void_p),
+                ("n_good_out", C.c_void_p)]
+
+
 _vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
 _lib.scivr_create_pes.argtypes = [C.POINTER(scivr_pes_desc), C.POINTER(_vp)]
 _lib.scivr_create_pes.restype = C.c_int
@@ -89,6 +97,14 @@ _lib.scivr_spectrum.argtypes = [_vp, _i64, _i32, _vp, _vp, _i64, _i32, _d, _d, _
 _lib.scivr_spectrum.restype = C.c_int
 _lib.scivr_spectrum_noalloc.argtypes = list(_lib.scivr_spectrum.argtypes)
 _lib.scivr_spectrum_noalloc.restype = C.c_int
+_lib.scivr_batch_create.argtypes = [C.POINTER(scivr_batch_item), _i32, _i32, C.POINTER(_vp)]
+_lib.scivr_batch_create.restype = C.c_int
+_lib.scivr_batch_launch.argtypes = [_vp, _vp]
+_lib.scivr_batch_launch.restype = C.c_int
+_lib.scivr_batch_info.argtypes = [_vp, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)]
+_lib.scivr_batch_info.restype = C.c_int
+_lib.scivr_batch_destroy.argtypes = [_vp]
+_lib.scivr_batch_destroy.restype = C.c_int
 _lib.scivr_check_status.argtypes = [_vp]
 _lib.scivr_check_status.restype = C.c_int
 _lib.scivr_selftest_wait_timeout.argtypes = [_d, _vp]
@@ -100,7 +116,8 @@ _lib.scivr_launch_count.restype = _i64
 
 EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_sample_initial",
             "scivr_propagate", "scivr_spectrum", "scivr_spectrum_noalloc", "scivr_check_status",
-            "scivr_selftest_wait_timeout", "scivr_last_error", "scivr_launch_count"]
+            "scivr_selftest_wait_timeout", "scivr_last_error", "scivr_launch_count",
+            "scivr_batch_create", "scivr_batch_launch", "scivr_batch_info", "scivr_batch_destroy"]
 
 
 def scivr_check_status(stream=None) -> int:
@@ -280,3 +297,65 @@ def run_spectrum_path(pes: Pes, wl, bufs: Buffers, sample=True, precision=SCIVR_
     for x in range(wl.n_chi):
         scivr_spectrum(bufs.amp[x], K, bufs.w, bufs.good, n, wl.n_steps, wl.dt, wl.E_min, wl.E_max,
                        wl.n_E, bufs.I[x], bufs.n_good, ft_mode=ft_mode, stream=stream)
+
+
+# --------------------------------------------------------------------------
+# Batched runs
+# --------------------------------------------------------------------------
+
+class Batch:
+    """Owning handle of a scivr_batch plan; keeps the host arrays its items point at alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def groups(self):
+        n = _i32()
+        _check(_lib.scivr_batch_info(self.handle, -1, C.byref(n), None, None, None), "scivr_batch_info")
+        out = []
+        for g in range(n.value):
+            F, pr, w = _i32(), _i32(), _i32()
+            _check(_lib.scivr_batch_info(self.handle, g, None, C.byref(F), C.byref(pr), C.byref(w)),
+                   "scivr_batch_info")
+            out.append((F.value, pr.value, w.value))
+        return out
+
+    def close(self):
+        if self.handle:
+            _lib.scivr_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scivr_batch_create(entries, ft_mode=SCIVR_FT_FP64) -> Batch:
+    """entries: list of dicts with keys pes (Pes), wl (workloads.Workload), bufs (Buffers),
+    precision, stab_tol.  Each molecule uses its own buffers (p0, q0, w, amp, good, I, n_good)."""
+    n = len(entries)
+    arr = (scivr_batch_item * n)()
+    keep = []
+    for i, e in enumerate(entries):
+        wl, bufs = e["wl"], e["bufs"]
+        g = _f64(wl.gamma)
+        pe = _f64(np.atleast_2d(wl.p_eq))
+        qe = _f64(np.atleast_2d(wl.q_eq))
+        keep += [g, pe, qe, e["pes"]]
+        prm = scivr_prop_params(float(wl.dt), int(wl.n_steps), int(e.get("precision", SCIVR_MIXED)),
+                                float(e.get("stab_tol", wl.stab_tol)), g.ctypes.data, pe.ctypes.data,
+                                qe.ctypes.data, pe.shape[0], int(e.get("kernel", SCIVR_KERNEL_AUTO)))
+        arr[i] = scivr_batch_item(e["pes"].handle, prm, int(bufs.w.shape[0]), _ptr(bufs.p0), _ptr(bufs.q0),
+                                  _ptr(bufs.w), _ptr(bufs.amp), int(wl.n_steps) + 1, _ptr(bufs.good),
+                                  float(wl.E_min), float(wl.E_max), int(wl.n_E), _ptr(bufs.I),
+                                  _ptr(bufs.n_good))
+    h = _vp()
+    _check(_lib.scivr_batch_create(arr, n, int(ft_mode), C.byref(h)), "scivr_batch_create")
+    return Batch(h.value, keep)
+
+
+def scivr_batch_launch(batch: Batch, stream=None):
+    _check(_lib.scivr_batch_launch(batch.handle, _stream(stream)), "scivr_batch_launch")
