@@ -45,11 +45,18 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class _Mlp(C.Structure):
+    _fields_ = [("H", C.c_int32), ("s_in", C.c_void_p), ("s_out", C.c_double),
+                ("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_void_p),
+                ("W3", C.c_void_p), ("b3", C.c_void_p), ("w4", C.c_void_p), ("b4", C.c_double)]
+
+
 class _Pes(C.Structure):
     _fields_ = [("F", C.c_int32), ("diag_kind", C.c_int32),
                 ("omega", C.c_void_p), ("D", C.c_void_p), ("a", C.c_void_p),
                 ("n3", C.c_int32), ("idx3", C.c_void_p), ("c3", C.c_void_p),
-                ("n4", C.c_int32), ("idx4", C.c_void_p), ("c4", C.c_void_p)]
+                ("n4", C.c_int32), ("idx4", C.c_void_p), ("c4", C.c_void_p),
+                ("mlp", C.c_void_p)]
 
 
 class _Prop(C.Structure):
@@ -94,6 +101,11 @@ def _load():
             lib.or_sample_initial.restype = C.c_int
             lib.or_sample_initial.argtypes = [i32, vp, vp, vp, i64, C.c_uint64, vp, vp, vp]
             lib.or_max_threads.restype = C.c_int
+            lib.or_mlp_eval.restype = None
+            lib.or_mlp_eval.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+            lib.or_mlp_loss_grad.restype = d
+            lib.or_mlp_loss_grad.argtypes = [vp, C.c_int, i64, vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp,
+                                             vp, vp]
             _lib = lib
     return _lib
 
@@ -106,6 +118,17 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+class Mlp:
+    """Owns FP64 copies of an MlpParams and the C struct pointing at them."""
+
+    def __init__(self, m):
+        self._keep = [_f64(m.s_in), _f64(m.W1), _f64(m.b1), _f64(m.W2), _f64(m.b2), _f64(m.W3),
+                      _f64(m.b3), _f64(m.w4)]
+        s_in, W1, b1, W2, b2, W3, b3, w4 = self._keep
+        self.s = _Mlp(int(m.H), _p(s_in), float(m.s_out), _p(W1), _p(b1), _p(W2), _p(b2), _p(W3),
+                      _p(b3), _p(w4), float(m.b4))
+
+
 class Pes:
     """Owns contiguous copies of a descriptor's arrays and the C struct pointing at them."""
 
@@ -115,8 +138,11 @@ class Pes:
                       np.ascontiguousarray(desc.idx3, dtype=np.int32), _f64(desc.c3),
                       np.ascontiguousarray(desc.idx4, dtype=np.int32), _f64(desc.c4)]
         om, D, a, i3, c3, i4, c4 = self._keep
+        mlp = getattr(desc, "mlp", None)
+        self._mlp = Mlp(mlp) if mlp is not None else None
         self.s = _Pes(self.F, int(desc.diag_kind), _p(om), _p(D), _p(a),
-                      c3.size, _p(i3), _p(c3), c4.size, _p(i4), _p(c4))
+                      c3.size, _p(i3), _p(c3), c4.size, _p(i4), _p(c4),
+                      C.addressof(self._mlp.s) if self._mlp is not None else None)
 
 
 def max_threads() -> int:
@@ -259,3 +285,26 @@ def run_workload(wl, p0=None, q0=None, w=None, n_threads=0):
                          n_threads)
         spectra.append(I)
     return dict(p0=p0, q0=q0, w=w, amp=amp, good=good, I=np.stack(spectra), n_good=ng)
+
+
+def mlp_eval(m, q):
+    """V_mlp, its gradient [F] and Hessian [F, F] at one point q."""
+    F = m.W1.shape[1]
+    M = Mlp(m)
+    q = _f64(q)
+    V = np.zeros(1); g = np.zeros(F); H = np.zeros((F, F))
+    _load().or_mlp_eval(C.byref(M.s), F, _p(q), _p(V), _p(g), _p(H))
+    return float(V[0]), g, H
+
+
+def mlp_loss_grad(m, q, Vref, gref, alpha, beta):
+    """Training objective over samples q [n, F] and its parameter gradient (an MlpParams-shaped
+    flat vector, same order as MlpParams.flat())."""
+    F = m.W1.shape[1]
+    H = m.H
+    M = Mlp(m)
+    q = _f64(q); Vref = _f64(Vref); gref = _f64(gref)
+    d = [np.zeros(s) for s in m.sizes(F, H)]
+    L = _load().or_mlp_loss_grad(C.byref(M.s), F, q.shape[0], _p(q), _p(Vref), _p(gref), float(alpha),
+                                 float(beta), *[_p(x) for x in d])
+    return float(L), np.concatenate(d)

@@ -46,6 +46,17 @@
 /* Potential: V(q) = sum_i diag_i(q_i) + sum_m c3_m q_i q_j q_k + sum_m c4_m q_i q_j q_k q_l */
 /* ------------------------------------------------------------------------ */
 
+/* Optional learned residual: a multilayer perceptron on x_i = s_in_i q_i,
+ * z1 = W1 x + b1, a_l = silu(z_l), z_{l+1} = W_{l+1} a_l + b_{l+1} (l = 1, 2),
+ * y = w4 . a3 + b4, V_mlp = s_out y.  W1: [H][F], W2, W3: [H][H], row-major. */
+typedef struct {
+    int32_t H;                /* hidden width */
+    const double *s_in;       /* [F] */
+    double s_out;
+    const double *W1, *b1, *W2, *b2, *W3, *b3, *w4;
+    double b4;
+} or_mlp;
+
 typedef struct {
     int32_t F;
     int32_t diag_kind;        /* 0: harmonic omega^2 q^2 / 2, 1: Morse D (1 - e^{-a q})^2 */
@@ -58,7 +69,86 @@ typedef struct {
     int32_t n4;
     const int32_t *idx4;      /* [n4 * 4] */
     const double *c4;         /* [n4] */
+    const or_mlp *mlp;        /* NULL: no learned residual */
 } or_pes;
+
+static double or_sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+/* silu(z) = z sigma(z) and its first two derivatives. */
+static void or_silu(double z, double *f, double *f1, double *f2)
+{
+    double s = or_sigmoid(z);
+    *f = z * s;
+    *f1 = s * (1.0 + z * (1.0 - s));
+    *f2 = s * (1.0 - s) * (2.0 + z * (1.0 - 2.0 * s));
+}
+
+/* V_mlp(q), its gradient (added into g) and Hessian (added into H).
+ * The Hessian of a chain of affine maps and elementwise activations is
+ * sum_l J_l^T diag(abar_l * silu''(z_l)) J_l with J_l = dz_l/dx and
+ * abar_l = dy/da_l (second-order chain rule, written layer by layer). */
+void or_mlp_eval(const or_mlp *m, int F, const double *q, double *V, double *g, double *Hm)
+{
+    const int Hd = m->H;
+    double *x = malloc(sizeof(double) * F);
+    double *z[3], *a[3], *d1[3], *d2[3], *abar[3], *J[3];
+    for (int l = 0; l < 3; ++l) {
+        z[l] = malloc(sizeof(double) * Hd); a[l] = malloc(sizeof(double) * Hd);
+        d1[l] = malloc(sizeof(double) * Hd); d2[l] = malloc(sizeof(double) * Hd);
+        abar[l] = malloc(sizeof(double) * Hd); J[l] = malloc(sizeof(double) * Hd * F);
+    }
+    const double *W[3] = {m->W1, m->W2, m->W3}, *b[3] = {m->b1, m->b2, m->b3};
+    for (int i = 0; i < F; ++i) x[i] = m->s_in[i] * q[i];
+    for (int l = 0; l < 3; ++l) {
+        const int nin = l == 0 ? F : Hd;
+        const double *in = l == 0 ? x : a[l - 1];
+        for (int o = 0; o < Hd; ++o) {
+            double acc = b[l][o];
+            for (int i = 0; i < nin; ++i) acc += W[l][o * nin + i] * in[i];
+            z[l][o] = acc;
+            or_silu(acc, &a[l][o], &d1[l][o], &d2[l][o]);
+        }
+    }
+    double y = m->b4;
+    for (int o = 0; o < Hd; ++o) y += m->w4[o] * a[2][o];
+    *V += m->s_out * y;
+    /* backward: abar_3 = w4, abar_l = W_{l+1}^T (abar_{l+1} * silu'(z_{l+1})) */
+    for (int o = 0; o < Hd; ++o) abar[2][o] = m->w4[o];
+    for (int l = 1; l >= 0; --l)
+        for (int i = 0; i < Hd; ++i) {
+            double acc = 0.0;
+            for (int o = 0; o < Hd; ++o) acc += W[l + 1][o * Hd + i] * abar[l + 1][o] * d1[l + 1][o];
+            abar[l][i] = acc;
+        }
+    if (g) {
+        for (int i = 0; i < F; ++i) {
+            double acc = 0.0;
+            for (int o = 0; o < Hd; ++o) acc += m->W1[o * F + i] * abar[0][o] * d1[0][o];
+            g[i] += m->s_out * m->s_in[i] * acc;
+        }
+    }
+    if (Hm) {
+        /* J_1 = W1, J_{l+1} = W_{l+1} diag(silu'(z_l)) J_l */
+        for (int o = 0; o < Hd; ++o)
+            for (int k = 0; k < F; ++k) J[0][o * F + k] = m->W1[o * F + k];
+        for (int l = 1; l < 3; ++l)
+            for (int o = 0; o < Hd; ++o)
+                for (int k = 0; k < F; ++k) {
+                    double acc = 0.0;
+                    for (int i = 0; i < Hd; ++i) acc += W[l][o * Hd + i] * d1[l - 1][i] * J[l - 1][i * F + k];
+                    J[l][o * F + k] = acc;
+                }
+        for (int k = 0; k < F; ++k)
+            for (int kk = 0; kk < F; ++kk) {
+                double acc = 0.0;
+                for (int l = 0; l < 3; ++l)
+                    for (int o = 0; o < Hd; ++o) acc += abar[l][o] * d2[l][o] * J[l][o * F + k] * J[l][o * F + kk];
+                Hm[k * F + kk] += m->s_out * m->s_in[k] * m->s_in[kk] * acc;
+            }
+    }
+    free(x);
+    for (int l = 0; l < 3; ++l) { free(z[l]); free(a[l]); free(d1[l]); free(d2[l]); free(abar[l]); free(J[l]); }
+}
 
 /* One monomial c * prod_s q[idx[s]] and its derivatives by the product rule
  * over index positions (repeated indices are handled automatically). */
@@ -111,6 +201,7 @@ double or_pes_eval(const or_pes *pes, const double *q, double *g, double *H)
     }
     for (int m = 0; m < pes->n3; ++m) or_monomial(3, pes->idx3 + 3 * m, pes->c3[m], q, F, &V, g, H);
     for (int m = 0; m < pes->n4; ++m) or_monomial(4, pes->idx4 + 4 * m, pes->c4[m], q, F, &V, g, H);
+    if (pes->mlp) or_mlp_eval(pes->mlp, F, q, &V, g, H);
     return V;
 }
 
@@ -511,4 +602,121 @@ int or_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Surrogate training objective and its parameter gradient                   */
+/* ------------------------------------------------------------------------ */
+
+/* Loss over n samples (rows of q [n][F], Vref [n], gref [n][F]) of the MLP
+ * alone (its output V_mlp = s_out y and gradient):
+ *   L = (1/n) sum_j [ alpha (V_mlp - Vref_j)^2 + beta |grad V_mlp - gref_j|^2 ].
+ * Parameter gradients (same layout as the weights) are written to the d*
+ * arrays.  The gradient-matching term is differentiated as the directional
+ * derivative D_u V with u = dL/dgrad held fixed, propagated forward as a
+ * tangent through the network and then back (second-order chain rule). */
+double or_mlp_loss_grad(const or_mlp *m, int F, int64_t n, const double *q, const double *Vref,
+                        const double *gref, double alpha, double beta,
+                        double *dW1, double *db1, double *dW2, double *db2, double *dW3, double *db3,
+                        double *dw4, double *db4)
+{
+    const int Hd = m->H;
+    const double *W[3] = {m->W1, m->W2, m->W3}, *b[3] = {m->b1, m->b2, m->b3};
+    double *dW[3] = {dW1, dW2, dW3}, *db[3] = {db1, db2, db3};
+    memset(dW1, 0, sizeof(double) * Hd * F); memset(dW2, 0, sizeof(double) * Hd * Hd);
+    memset(dW3, 0, sizeof(double) * Hd * Hd); memset(db1, 0, sizeof(double) * Hd);
+    memset(db2, 0, sizeof(double) * Hd); memset(db3, 0, sizeof(double) * Hd);
+    memset(dw4, 0, sizeof(double) * Hd); *db4 = 0.0;
+    double *x = malloc(sizeof(double) * F), *u = malloc(sizeof(double) * F), *xt = malloc(sizeof(double) * F);
+    double *z[3], *a[3], *f1[3], *f2[3], *zt[3], *at[3], *abar[3], *zb[3], *ztb[3], *ab[3], *atb[3];
+    for (int l = 0; l < 3; ++l) {
+        z[l] = malloc(sizeof(double) * Hd); a[l] = malloc(sizeof(double) * Hd);
+        f1[l] = malloc(sizeof(double) * Hd); f2[l] = malloc(sizeof(double) * Hd);
+        zt[l] = malloc(sizeof(double) * Hd); at[l] = malloc(sizeof(double) * Hd);
+        abar[l] = malloc(sizeof(double) * Hd); zb[l] = malloc(sizeof(double) * Hd);
+        ztb[l] = malloc(sizeof(double) * Hd); ab[l] = malloc(sizeof(double) * Hd);
+        atb[l] = malloc(sizeof(double) * Hd);
+    }
+    double loss = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        const double *qj = q + j * F;
+        for (int i = 0; i < F; ++i) x[i] = m->s_in[i] * qj[i];
+        for (int l = 0; l < 3; ++l) {
+            const int nin = l == 0 ? F : Hd;
+            const double *in = l == 0 ? x : a[l - 1];
+            for (int o = 0; o < Hd; ++o) {
+                double acc = b[l][o];
+                for (int i = 0; i < nin; ++i) acc += W[l][o * nin + i] * in[i];
+                z[l][o] = acc;
+                or_silu(acc, &a[l][o], &f1[l][o], &f2[l][o]);
+            }
+        }
+        double y = m->b4;
+        for (int o = 0; o < Hd; ++o) y += m->w4[o] * a[2][o];
+        /* input gradient dy/dx via abar */
+        for (int o = 0; o < Hd; ++o) abar[2][o] = m->w4[o];
+        for (int l = 1; l >= 0; --l)
+            for (int i = 0; i < Hd; ++i) {
+                double acc = 0.0;
+                for (int o = 0; o < Hd; ++o) acc += W[l + 1][o * Hd + i] * abar[l + 1][o] * f1[l + 1][o];
+                abar[l][i] = acc;
+            }
+        double ev = m->s_out * y - Vref[j];
+        loss += alpha * ev * ev;
+        for (int i = 0; i < F; ++i) {
+            double acc = 0.0;
+            for (int o = 0; o < Hd; ++o) acc += m->W1[o * F + i] * abar[0][o] * f1[0][o];
+            double gi = m->s_out * m->s_in[i] * acc;
+            double e = gi - gref[j * F + i];
+            loss += beta * e * e;
+            u[i] = 2.0 * beta * e / (double)n;        /* dL/dgrad_i, held fixed */
+        }
+        /* tangent along u: D_u V = s_out * d/de y(x + e s_in u) */
+        for (int i = 0; i < F; ++i) xt[i] = m->s_in[i] * u[i];
+        for (int l = 0; l < 3; ++l) {
+            const int nin = l == 0 ? F : Hd;
+            const double *in = l == 0 ? xt : at[l - 1];
+            for (int o = 0; o < Hd; ++o) {
+                double acc = 0.0;
+                for (int i = 0; i < nin; ++i) acc += W[l][o * nin + i] * in[i];
+                zt[l][o] = acc;
+                at[l][o] = f1[l][o] * acc;
+            }
+        }
+        /* reverse pass of (y, y_t) with seeds ybar = 2 alpha ev s_out / n, ytbar = s_out */
+        const double ybar = 2.0 * alpha * ev * m->s_out / (double)n, ytbar = m->s_out;
+        *db4 += ybar;
+        for (int o = 0; o < Hd; ++o) {
+            dw4[o] += ybar * a[2][o] + ytbar * at[2][o];
+            ab[2][o] = ybar * m->w4[o];
+            atb[2][o] = ytbar * m->w4[o];
+        }
+        for (int l = 2; l >= 0; --l) {
+            const int nin = l == 0 ? F : Hd;
+            const double *in = l == 0 ? x : a[l - 1];
+            const double *int_ = l == 0 ? xt : at[l - 1];
+            for (int o = 0; o < Hd; ++o) {
+                zb[l][o] = ab[l][o] * f1[l][o] + atb[l][o] * f2[l][o] * zt[l][o];
+                ztb[l][o] = atb[l][o] * f1[l][o];
+                db[l][o] += zb[l][o];
+                for (int i = 0; i < nin; ++i) dW[l][o * nin + i] += zb[l][o] * in[i] + ztb[l][o] * int_[i];
+            }
+            if (l > 0)
+                for (int i = 0; i < Hd; ++i) {
+                    double s1 = 0.0, s2 = 0.0;
+                    for (int o = 0; o < Hd; ++o) {
+                        s1 += W[l][o * Hd + i] * zb[l][o];
+                        s2 += W[l][o * Hd + i] * ztb[l][o];
+                    }
+                    ab[l - 1][i] = s1;
+                    atb[l - 1][i] = s2;
+                }
+        }
+    }
+    free(x); free(u); free(xt);
+    for (int l = 0; l < 3; ++l) {
+        free(z[l]); free(a[l]); free(f1[l]); free(f2[l]); free(zt[l]); free(at[l]); free(abar[l]);
+        free(zb[l]); free(ztb[l]); free(ab[l]); free(atb[l]);
+    }
+    return loss / (double)n;
 }

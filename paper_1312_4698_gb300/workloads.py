@@ -64,6 +64,7 @@ class PesDesc:
     c3: np.ndarray
     idx4: np.ndarray
     c4: np.ndarray
+    mlp: Optional["MlpParams"] = None   # learned residual added to V (None: analytic only)
 
     def __post_init__(self):
         self.omega = np.ascontiguousarray(self.omega, dtype=np.float64)
@@ -73,6 +74,56 @@ class PesDesc:
         self.c3 = np.ascontiguousarray(self.c3, dtype=np.float64).reshape(-1)
         self.idx4 = np.ascontiguousarray(np.asarray(self.idx4, dtype=np.int32).reshape(-1, 4))
         self.c4 = np.ascontiguousarray(self.c4, dtype=np.float64).reshape(-1)
+
+
+@dataclasses.dataclass
+class MlpParams:
+    """Learned residual V_mlp(q) = s_out * (w4 . a3 + b4) on x = s_in * q (a_l = silu(z_l)).
+    W1: [H, F], W2, W3: [H, H] (row-major, output index first)."""
+    H: int
+    s_in: np.ndarray
+    s_out: float
+    W1: np.ndarray
+    b1: np.ndarray
+    W2: np.ndarray
+    b2: np.ndarray
+    W3: np.ndarray
+    b3: np.ndarray
+    w4: np.ndarray
+    b4: float
+
+    def copy(self):
+        return MlpParams(self.H, self.s_in.copy(), float(self.s_out), self.W1.copy(), self.b1.copy(),
+                         self.W2.copy(), self.b2.copy(), self.W3.copy(), self.b3.copy(), self.w4.copy(),
+                         float(self.b4))
+
+    def flat(self) -> np.ndarray:
+        return np.concatenate([self.W1.ravel(), self.b1, self.W2.ravel(), self.b2, self.W3.ravel(),
+                               self.b3, self.w4, [self.b4]])
+
+    @staticmethod
+    def sizes(F, H):
+        return [H * F, H, H * H, H, H * H, H, H, 1]
+
+    def with_flat(self, v: np.ndarray) -> "MlpParams":
+        F = self.W1.shape[1]
+        H = self.H
+        o = np.cumsum([0] + self.sizes(F, H))
+        return MlpParams(H, self.s_in.copy(), float(self.s_out), v[o[0]:o[1]].reshape(H, F).copy(),
+                         v[o[1]:o[2]].copy(), v[o[2]:o[3]].reshape(H, H).copy(), v[o[3]:o[4]].copy(),
+                         v[o[4]:o[5]].reshape(H, H).copy(), v[o[5]:o[6]].copy(), v[o[6]:o[7]].copy(),
+                         float(v[o[7]]))
+
+
+def init_mlp(F: int, H: int = 256, seed: int = 0, s_in=None, s_out: float = 1e-6) -> MlpParams:
+    """Seeded random initialisation (scaled normal, zero biases)."""
+    rng = np.random.default_rng(seed)
+    s_in = np.ones(F) if s_in is None else np.asarray(s_in, dtype=np.float64)
+    return MlpParams(H, s_in, float(s_out),
+                     rng.normal(0, 1 / np.sqrt(F), (H, F)), np.zeros(H),
+                     rng.normal(0, 1 / np.sqrt(H), (H, H)), np.zeros(H),
+                     rng.normal(0, 1 / np.sqrt(H), (H, H)), np.zeros(H),
+                     rng.normal(0, 1 / np.sqrt(H), H), 0.0)
 
 
 @dataclasses.dataclass
