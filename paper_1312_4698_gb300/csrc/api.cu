@@ -285,8 +285,9 @@ int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out)
         cudaFree(blob);
         return cuda_fail(e, "scivr_create_pes: cudaMemcpy");
     }
-    scivr_pes h = new scivr_pes_s;
+    scivr_pes h = new scivr_pes_s{};
     h->blob = blob;
+    h->mlp_blob = nullptr;
     PesDev &dv = h->dev;
     const double *db = reinterpret_cast<const double *>(b);
     dv.F = F;
@@ -314,6 +315,10 @@ int scivr_destroy_pes(scivr_pes pes)
     if (!pes) { ok(); return SCIVR_OK; }
     cudaError_t e = cudaDeviceSynchronize();
     cudaError_t e2 = cudaFree(pes->blob);
+    if (pes->mlp_blob) {
+        cudaError_t e3 = cudaFree(pes->mlp_blob);
+        if (e2 == cudaSuccess) e2 = e3;
+    }
     delete pes;
     if (e != cudaSuccess) return cuda_fail(e, "scivr_destroy_pes: synchronize");
     if (e2 != cudaSuccess) return cuda_fail(e2, "scivr_destroy_pes: cudaFree");
@@ -347,7 +352,14 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
     const int rc = prepare_propagate(pes, prm, n_traj, p0, q0, amp, amp_ld, good, fin, &L);
     if (rc != SCIVR_OK) return rc;
     int nl = 0;
-    cudaError_t e = launch_propagate(L, static_cast<cudaStream_t>(stream), &nl);
+    cudaError_t e;
+    if (pes->dev.mlp.H != 0) {
+        if (prm->precision != SCIVR_MIXED || prm->kernel != SCIVR_KERNEL_AUTO)
+            return fail(SCIVR_EUNSUPPORTED, "scivr_propagate: a learned residual needs SCIVR_MIXED and SCIVR_KERNEL_AUTO");
+        e = launch_propagate_mlp(L, static_cast<cudaStream_t>(stream), &nl);
+    } else {
+        e = launch_propagate(L, static_cast<cudaStream_t>(stream), &nl);
+    }
     g_launches += nl;
     if (e != cudaSuccess) return cuda_fail(e, "scivr_propagate: launch");
     ok();
@@ -399,9 +411,11 @@ int scivr_check_status(void *stream)
 {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "scivr_check_status: synchronize");
-    int st = 0;
+    int st = 0, st_mlp = 0;
     e = read_and_clear_status(&st);
+    if (e == cudaSuccess) e = read_and_clear_status_mlp(&st_mlp);
     if (e != cudaSuccess) return cuda_fail(e, "scivr_check_status: status word");
+    if (st == 0) st = st_mlp;
     if (st == SCIVR_ETIMEOUT) return fail(SCIVR_ETIMEOUT, "scivr_check_status: a bounded device wait expired");
     if (st != 0) return fail(SCIVR_ECUDA, "scivr_check_status: device status %d", st);
     ok();

@@ -1,0 +1,288 @@
+// Propagation on a potential with a learned residual (Sec. III.A schedule,
+// split into stages so that every force evaluation of the network is one
+// batched tensor-core evaluation over all trajectories).
+//
+// Per step of the fourth-order triple jump  D(c0) K(d0) D(c1) K(d1) D(c2) K(d2) D(c3):
+//   network at q  ->  stage 1: K(d0) D(c1)
+//   network at q  ->  stage 2: K(d1) D(c2)
+//   network at q  ->  stage 3: K(d2) D(c3), det M (stability), det A and the
+//                     continuous phase, the amplitude of Eq. I(E)_discreto,
+//                     then D(c0) of the next step
+// and stage 0 (before the first step) sets M = I, records c = 0 and drifts
+// D(c0).  A kick uses V, grad V and the Hessian of the analytic surface (FP64,
+// at q) plus those of the network (FP32, at q rounded to FP32).  State between
+// stages lives in HBM: p, q, S, theta (FP64, structure of arrays) and M (FP32,
+// element (r, c) of trajectory j at (r 2F + c) n + j).  One thread per
+// trajectory; the kick and drift stream M column by column.
+#include "propagate_tpt.cuh"
+
+namespace scivr {
+namespace pm {
+
+struct State {
+    double *p, *q;        // [F][n]
+    float *M;             // [(2F)^2][n]
+    double *S, *theta, *arg_old, *stab;
+    float *qf;            // [n][F] network input
+    const float *Vm, *gm, *Hm;   // network output at qf: [n], [n][F], [n][F][F]
+    int *step;            // device step counter (column of the amplitude)
+};
+
+template <int F>
+__device__ __forceinline__ void record(const PropLaunch &L, int64_t j, int step, const double (&p)[F],
+                                       const double (&q)[F], double S, double theta)
+{
+    const PropArgs &A = L.args;
+    for (int x = 0; x < A.n_chi; ++x) {
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int a = 0; a < F; ++a) {
+            const double dq = A.q_eq[x * F + a] - q[a];
+            const double dp = A.p_eq[x * F + a] - p[a];
+            re = fma(-A.qw[a] * dq, dq, re);
+            re = fma(-A.pw[a] * dp, dp, re);
+            im = fma(0.5 * (A.p_eq[x * F + a] + p[a]), dq, im);
+        }
+        double sn, cs;
+        sincos(im + S + 0.5 * theta, &sn, &cs);
+        const double mag = exp(re);
+        L.amp[x * L.chi_stride + j * L.amp_ld + step] = make_double2(mag * cs, mag * sn);
+    }
+}
+
+// Drift of length td for (q, S) and M_q += td M_p, all columns.
+template <int F>
+__device__ __forceinline__ void drift(State &st, int64_t j, int64_t n, double td, float tdf, double (&p)[F],
+                                      double (&q)[F], double &S)
+{
+    constexpr int N2 = 2 * F;
+    double kin = 0.0;
+#pragma unroll
+    for (int a = 0; a < F; ++a) kin = fma(0.5 * p[a], p[a], kin);
+    S = fma(td, kin, S);
+#pragma unroll
+    for (int a = 0; a < F; ++a) q[a] = fma(td, p[a], q[a]);
+#pragma unroll 1
+    for (int c = 0; c < N2; ++c) {
+#pragma unroll
+        for (int a = 0; a < F; ++a) {
+            float *mq = st.M + ((int64_t)(F + a) * N2 + c) * n + j;
+            *mq = fmaf(tdf, st.M[((int64_t)a * N2 + c) * n + j], *mq);
+        }
+    }
+}
+
+template <int F>
+__global__ void __launch_bounds__(128) k_mlp_stage(const PropLaunch L, State st, int stage)
+{
+    constexpr int N2 = 2 * F;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = L.n_traj;
+    const PropArgs &A = L.args;
+    if (stage == 1 && j == 0) *st.step += 1;   // read by stage 3 of this step (later in stream order)
+    if (j >= n) return;
+    double p[F], q[F], S;
+    if (stage == 0) {
+#pragma unroll
+        for (int a = 0; a < F; ++a) {
+            p[a] = L.p0[a * n + j];
+            q[a] = L.q0[a * n + j];
+        }
+        S = 0.0;
+        for (int r = 0; r < N2; ++r)
+            for (int c = 0; c < N2; ++c) st.M[((int64_t)r * N2 + c) * n + j] = r == c ? 1.0f : 0.0f;
+        st.theta[j] = 0.0;
+        st.arg_old[j] = 0.0;
+        st.stab[j] = 0.0;
+        L.good[j] = 1;
+        record<F>(L, j, 0, p, q, 0.0, 0.0);
+    } else {
+#pragma unroll
+        for (int a = 0; a < F; ++a) {
+            p[a] = st.p[a * n + j];
+            q[a] = st.q[a * n + j];
+        }
+        S = st.S[j];
+        // kick d_{stage-1}: analytic part (FP64) + network part (FP32)
+        double H[F][F], g[F], V;
+        tpt::pes_fp64<F>(L.pes, q, H, g, V);
+        const double tk = A.tkick[stage - 1];
+        V += (double)st.Vm[j];
+        S = fma(-tk, V, S);
+#pragma unroll
+        for (int a = 0; a < F; ++a) p[a] = fma(-tk, g[a] + (double)st.gm[j * F + a], p[a]);
+        float Hk[F][F];
+#pragma unroll
+        for (int a = 0; a < F; ++a)
+#pragma unroll
+            for (int b = 0; b < F; ++b) Hk[a][b] = (float)(tk * H[a][b]) + A.tkick_f[stage - 1] * st.Hm[(j * F + a) * F + b];
+#pragma unroll 1
+        for (int c = 0; c < N2; ++c) {
+            float mq[F];
+#pragma unroll
+            for (int b = 0; b < F; ++b) mq[b] = st.M[((int64_t)(F + b) * N2 + c) * n + j];
+#pragma unroll
+            for (int a = 0; a < F; ++a) {
+                float hm = 0.0f;
+#pragma unroll
+                for (int b = 0; b < F; ++b) hm = fmaf(Hk[a][b], mq[b], hm);
+                float *mp = st.M + ((int64_t)a * N2 + c) * n + j;
+                *mp -= hm;
+            }
+        }
+    }
+    drift<F>(st, j, n, A.tdrift[stage], A.tdrift_f[stage], p, q, S);
+    if (stage == 3) {
+        const int step = *st.step;
+        bool good = L.good[j] != 0;
+        // stability |det(M)^2 - 1| (FP32 LU with partial pivoting)
+        float W[N2][N2];
+        for (int r = 0; r < N2; ++r)
+            for (int c = 0; c < N2; ++c) W[r][c] = st.M[((int64_t)r * N2 + c) * n + j];
+        float det = 1.0f;
+        for (int k = 0; k < N2; ++k) {
+            int piv = k;
+            float best = fabsf(W[k][k]);
+            for (int i = k + 1; i < N2; ++i)
+                if (fabsf(W[i][k]) > best) { best = fabsf(W[i][k]); piv = i; }
+            if (piv != k) {
+                for (int c = k; c < N2; ++c) { const float t = W[k][c]; W[k][c] = W[piv][c]; W[piv][c] = t; }
+                det = -det;
+            }
+            const float akk = W[k][k];
+            det *= akk;
+            const float inv = 1.0f / akk;
+            for (int i = k + 1; i < N2; ++i) {
+                const float l = W[i][k] * inv;
+                for (int c = k + 1; c < N2; ++c) W[i][c] = fmaf(-l, W[k][c], W[i][c]);
+            }
+        }
+        const float dev = isfinite(det) ? fabsf(fmaf(det, det, -1.0f)) : __int_as_float(0x7f800000);
+        const double stab = fmax(st.stab[j], (double)dev);
+        st.stab[j] = stab;
+        if (dev > A.stab_tol_f) good = false;
+        // Herman-Kluk prefactor determinant (FP64) and the continuous phase
+        tpt::cplx Am[F][F];
+        for (int a = 0; a < F; ++a)
+            for (int b = 0; b < F; ++b) {
+                const double mqq = st.M[((int64_t)(F + a) * N2 + F + b) * n + j];
+                const double mpp = st.M[((int64_t)a * N2 + b) * n + j];
+                const double mqp = st.M[((int64_t)(F + a) * N2 + b) * n + j];
+                const double mpq = st.M[((int64_t)a * N2 + F + b) * n + j];
+                const double re = fma(A.rg[a] * A.irg[b], mqq, A.rg[b] * A.irg[a] * mpp);
+                const double im = fma(-A.rg[a] * A.rg[b], mqp, A.irg[a] * A.irg[b] * mpq);
+                Am[a][b] = {0.5 * re, 0.5 * im};
+            }
+        const tpt::cplx dA = tpt::det_complex<F>(Am);
+        const double arg_new = atan2(dA.im, dA.re);
+        double d = arg_new - st.arg_old[j] + A.ref_step;
+        d = fma(-kTwoPi, rint(d * kInvTwoPi), d);
+        const double theta = st.theta[j] + d - A.ref_step;
+        st.theta[j] = theta;
+        st.arg_old[j] = arg_new;
+        bool finite = isfinite(S) && isfinite(theta);
+#pragma unroll
+        for (int a = 0; a < F; ++a) finite = finite && isfinite(p[a]) && isfinite(q[a]);
+        if (!finite) good = false;
+        L.good[j] = good ? 1 : 0;
+        record<F>(L, j, step, p, q, S, theta);
+        if (step == A.n_steps) {
+            const FinalDev &fo = L.fin;
+            if (fo.p) for (int a = 0; a < F; ++a) fo.p[a * n + j] = p[a];
+            if (fo.q) for (int a = 0; a < F; ++a) fo.q[a * n + j] = q[a];
+            if (fo.S) fo.S[j] = S;
+            if (fo.theta) fo.theta[j] = theta;
+            if (fo.detM) fo.detM[j] = (double)det;
+            if (fo.stab) fo.stab[j] = stab;
+            if (fo.detA) { fo.detA[2 * j] = dA.re; fo.detA[2 * j + 1] = dA.im; }
+            if (fo.M)
+                for (int r = 0; r < N2; ++r)
+                    for (int c = 0; c < N2; ++c) fo.M[j * N2 * N2 + r * N2 + c] = st.M[((int64_t)r * N2 + c) * n + j];
+            return;
+        }
+        drift<F>(st, j, n, A.tdrift[0], A.tdrift_f[0], p, q, S);
+    }
+#pragma unroll
+    for (int a = 0; a < F; ++a) {
+        st.p[a * n + j] = p[a];
+        st.q[a * n + j] = q[a];
+        st.qf[j * F + a] = (float)q[a];
+    }
+    st.S[j] = S;
+}
+
+inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <int F>
+cudaError_t run(const PropLaunch &L, cudaStream_t s, int *n_launch)
+{
+    constexpr int N2 = 2 * F;
+    const int64_t n = L.n_traj;
+    size_t o = 0;
+    const size_t oP = o; o += a256((size_t)F * n * 8);
+    const size_t oQ = o; o += a256((size_t)F * n * 8);
+    const size_t oM = o; o += a256((size_t)N2 * N2 * n * 4);
+    const size_t oS = o; o += a256((size_t)n * 8);
+    const size_t oT = o; o += a256((size_t)n * 8);
+    const size_t oA = o; o += a256((size_t)n * 8);
+    const size_t oB = o; o += a256((size_t)n * 8);
+    const size_t oQf = o; o += a256((size_t)n * F * 4);
+    const size_t oV = o; o += a256((size_t)n * 4);
+    const size_t oG = o; o += a256((size_t)n * F * 4);
+    const size_t oH = o; o += a256((size_t)n * F * F * 4);
+    const size_t oStep = o; o += 256;
+    const size_t oEval = o; o += mlp_eval_scratch_bytes(F, n, true);
+    void *scr = nullptr;
+    cudaError_t e = cudaMallocAsync(&scr, o, s);
+    if (e != cudaSuccess) return e;
+    char *b = static_cast<char *>(scr);
+    State st{};
+    st.p = reinterpret_cast<double *>(b + oP);
+    st.q = reinterpret_cast<double *>(b + oQ);
+    st.M = reinterpret_cast<float *>(b + oM);
+    st.S = reinterpret_cast<double *>(b + oS);
+    st.theta = reinterpret_cast<double *>(b + oT);
+    st.arg_old = reinterpret_cast<double *>(b + oA);
+    st.stab = reinterpret_cast<double *>(b + oB);
+    st.qf = reinterpret_cast<float *>(b + oQf);
+    float *Vm = reinterpret_cast<float *>(b + oV), *gm = reinterpret_cast<float *>(b + oG);
+    float *Hm = reinterpret_cast<float *>(b + oH);
+    st.Vm = Vm; st.gm = gm; st.Hm = Hm;
+    st.step = reinterpret_cast<int *>(b + oStep);
+    int nl = 0;
+    e = cudaMemsetAsync(st.step, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = mlp_prepare();
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    if (e == cudaSuccess) {
+        k_mlp_stage<F><<<blocks, 128, 0, s>>>(L, st, 0);
+        nl += 1;
+        for (int step = 1; step <= L.args.n_steps && e == cudaSuccess; ++step) {
+            for (int stage = 1; stage <= 3; ++stage) {
+                int ne = 0;
+                e = mlp_eval(L.pes.mlp, F, n, st.qf, Vm, gm, Hm, b + oEval, s, &ne);
+                nl += ne;
+                if (e != cudaSuccess) break;
+                k_mlp_stage<F><<<blocks, 128, 0, s>>>(L, st, stage);
+                nl += 1;
+            }
+            if (e == cudaSuccess) e = cudaGetLastError();
+        }
+    }
+    cudaError_t e2 = cudaFreeAsync(scr, s);
+    *n_launch = nl;
+    return e != cudaSuccess ? e : e2;
+}
+
+}  // namespace pm
+
+cudaError_t launch_propagate_mlp(const PropLaunch &L, cudaStream_t s, int *n_launch)
+{
+    switch (L.args.F) {
+#define SCIVR_PM(FF) case FF: return pm::run<FF>(L, s, n_launch);
+    SCIVR_PM(1) SCIVR_PM(2) SCIVR_PM(3) SCIVR_PM(4) SCIVR_PM(5) SCIVR_PM(6) SCIVR_PM(7) SCIVR_PM(8) SCIVR_PM(9)
+#undef SCIVR_PM
+    default: *n_launch = 0; return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace scivr

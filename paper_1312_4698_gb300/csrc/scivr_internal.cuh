@@ -5,8 +5,23 @@
 #include <stdint.h>
 
 #include "scivr.h"
+#include "scivr_mlp.h"
 
 namespace scivr {
+
+// Learned residual (MLP surrogate) weights on the device: FP32 masters and
+// BF16 tiles of the 256 x 256 layers for the tensor-core GEMMs.
+// theta is the flat parameter vector [W1 (H x F), b1, W2 (H x H), b2, W3, b3,
+// w4, b4]; the named pointers point into it.
+struct MlpWeightsDev {
+    int H;                                   // 256 (0: no residual)
+    int64_t n_params;
+    float *theta;
+    const float *W1, *b1, *W2, *b2, *W3, *b3, *w4, *b4;
+    float s_out;
+    const float *s_in;                       // [F]
+    uint8_t *W2t, *W3t, *W2Tt, *W3Tt;        // BF16 tiles (refreshed whenever theta changes)
+};
 
 // Device-resident potential.  The coupling polynomial is stored in the
 // Hessian-generating form used by the kernels:
@@ -24,6 +39,7 @@ struct PesDev {
     const double *T4;                // [P][P]
     const float *T3f, *T4f;          // FP32 copies for the mixed-precision path
     const float *omega_f, *D_f, *a_f;   // FP32 copies of the diagonal parameters
+    MlpWeightsDev mlp;                  // mlp.H == 0: analytic surface only
 };
 
 // Kernel-side propagation parameters, passed by value.
@@ -82,6 +98,22 @@ cudaError_t launch_spectrum_tc(int ft_mode, const double2 *amp, int64_t amp_ld, 
                                cudaStream_t s, int *n_launch);
 cudaError_t launch_wait_selftest(double seconds, cudaStream_t s);
 cudaError_t read_and_clear_status(int *status);
+cudaError_t read_and_clear_status_mlp(int *status);
+size_t mlp_eval_scratch_bytes(int F, int64_t n, bool hess);
+size_t mlp_train_scratch_bytes(int F, int64_t n);
+cudaError_t mlp_prepare();   // kernel attributes (current device); call before the first launch
+cudaError_t mlp_eval(const MlpWeightsDev &w, int F, int64_t n, const float *q, float *V, float *g, float *H,
+                     void *scratch, cudaStream_t s, int *n_launch);   // H == NULL: V and g only
+cudaError_t mlp_loss_grad(const MlpWeightsDev &w, int F, int64_t n, const float *q, const float *Vref,
+                          const float *gref, float alpha, float beta, float *grad, float *loss, void *scratch,
+                          cudaStream_t s, int *n_launch);
+cudaError_t mlp_tile_weights(const MlpWeightsDev &w, cudaStream_t s);   // 4 launches
+cudaError_t mlp_adamw(const MlpWeightsDev &w, const float *grad, float *m1, float *m2, float lr, float beta1,
+                      float beta2, float eps, float wd, float c1, float c2, cudaStream_t s);   // 5 launches
+// Split-step propagation on a potential with a learned residual (pes.mlp.H != 0).
+cudaError_t launch_propagate_mlp(const PropLaunch &L, cudaStream_t s, int *n_launch);
+cudaError_t launch_pes_eval(const PesDev &pes, int64_t n, const double *q, int terms, double *V, double *g,
+                            double *H, cudaStream_t s);
 
 bool propagate_supported(int F, int precision, int kernel);
 int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj, const double *p0,
@@ -108,4 +140,5 @@ constexpr double kInvTwoPi = 0.15915494309189533576888376337251;
 struct scivr_pes_s {
     scivr::PesDev dev;
     void *blob;          // single device allocation holding all arrays
+    void *mlp_blob;      // learned-residual weights and tiles (or NULL)
 };

@@ -117,7 +117,9 @@ _lib.scivr_launch_count.restype = _i64
 EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_sample_initial",
             "scivr_propagate", "scivr_spectrum", "scivr_spectrum_noalloc", "scivr_check_status",
             "scivr_selftest_wait_timeout", "scivr_last_error", "scivr_launch_count",
-            "scivr_batch_create", "scivr_batch_launch", "scivr_batch_info", "scivr_batch_destroy"]
+            "scivr_batch_create", "scivr_batch_launch", "scivr_batch_info", "scivr_batch_destroy",
+            "scivr_mlp_param_count", "scivr_pes_set_mlp", "scivr_mlp_eval", "scivr_mlp_get_params",
+            "scivr_mlp_set_params", "scivr_mlp_loss_grad", "scivr_mlp_adamw", "scivr_pes_eval"]
 
 
 def scivr_check_status(stream=None) -> int:
@@ -197,7 +199,10 @@ def scivr_create_pes(desc) -> Pes:
                        i4.ctypes.data if c4.size else None, c4.ctypes.data if c4.size else None)
     h = _vp()
     _check(_lib.scivr_create_pes(C.byref(d), C.byref(h)), "scivr_create_pes")
-    return Pes(h.value, int(desc.F))
+    pes = Pes(h.value, int(desc.F))
+    if getattr(desc, "mlp", None) is not None:
+        scivr_pes_set_mlp(pes, desc.mlp)
+    return pes
 
 
 create_pes = scivr_create_pes
@@ -359,3 +364,79 @@ def scivr_batch_create(entries, ft_mode=SCIVR_FT_FP64) -> Batch:
 
 def scivr_batch_launch(batch: Batch, stream=None):
     _check(_lib.scivr_batch_launch(batch.handle, _stream(stream)), "scivr_batch_launch")
+
+
+# ---------------------------------------------------------------- learned residual (include/scivr_mlp.h)
+SCIVR_MLP_HIDDEN = 256
+SCIVR_TERMS_ALL = 0
+SCIVR_TERMS_DIAG = 1
+SCIVR_TERMS_COUPLING = 2
+
+
+class scivr_mlp_desc(C.Structure):
+    _fields_ = [("H", _i32), ("s_in", _vp), ("s_out", _d), ("W1", _vp), ("b1", _vp), ("W2", _vp),
+                ("b2", _vp), ("W3", _vp), ("b3", _vp), ("w4", _vp), ("b4", _d)]
+
+
+_lib.scivr_mlp_param_count.argtypes = [_i32, _i32]
+_lib.scivr_mlp_param_count.restype = _i64
+_lib.scivr_pes_set_mlp.argtypes = [_vp, C.POINTER(scivr_mlp_desc)]
+_lib.scivr_pes_set_mlp.restype = C.c_int
+_lib.scivr_mlp_eval.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp]
+_lib.scivr_mlp_eval.restype = C.c_int
+_lib.scivr_mlp_get_params.argtypes = [_vp, _vp, _vp]
+_lib.scivr_mlp_get_params.restype = C.c_int
+_lib.scivr_mlp_set_params.argtypes = [_vp, _vp, _vp]
+_lib.scivr_mlp_set_params.restype = C.c_int
+_lib.scivr_mlp_loss_grad.argtypes = [_vp, _i64, _vp, _vp, _vp, _d, _d, _vp, _vp, _vp]
+_lib.scivr_mlp_loss_grad.restype = C.c_int
+_lib.scivr_mlp_adamw.argtypes = [_vp, _vp, _vp, _vp, _i32, _d, _d, _d, _d, _d, _vp]
+_lib.scivr_mlp_adamw.restype = C.c_int
+_lib.scivr_pes_eval.argtypes = [_vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp]
+_lib.scivr_pes_eval.restype = C.c_int
+
+
+def scivr_mlp_param_count(F: int, H: int = SCIVR_MLP_HIDDEN) -> int:
+    return int(_lib.scivr_mlp_param_count(int(F), int(H)))
+
+
+def scivr_pes_set_mlp(pes: Pes, m):
+    """Attach (or with m=None detach) a learned residual; m: workloads.MlpParams-like."""
+    if m is None:
+        _check(_lib.scivr_pes_set_mlp(pes.handle, None), "scivr_pes_set_mlp")
+        return
+    keep = [_f64(m.s_in), _f64(m.W1), _f64(m.b1), _f64(m.W2), _f64(m.b2), _f64(m.W3), _f64(m.b3), _f64(m.w4)]
+    si, W1, b1, W2, b2, W3, b3, w4 = keep
+    d = scivr_mlp_desc(int(m.H), si.ctypes.data, float(m.s_out), W1.ctypes.data, b1.ctypes.data,
+                       W2.ctypes.data, b2.ctypes.data, W3.ctypes.data, b3.ctypes.data, w4.ctypes.data,
+                       float(m.b4))
+    _check(_lib.scivr_pes_set_mlp(pes.handle, C.byref(d)), "scivr_pes_set_mlp")
+
+
+def scivr_mlp_eval(pes: Pes, n, q, V, g, H=None, stream=None):
+    _check(_lib.scivr_mlp_eval(pes.handle, int(n), _ptr(q), _ptr(V), _ptr(g), _ptr(H), _stream(stream)),
+           "scivr_mlp_eval")
+
+
+def scivr_mlp_get_params(pes: Pes, theta, stream=None):
+    _check(_lib.scivr_mlp_get_params(pes.handle, _ptr(theta), _stream(stream)), "scivr_mlp_get_params")
+
+
+def scivr_mlp_set_params(pes: Pes, theta, stream=None):
+    _check(_lib.scivr_mlp_set_params(pes.handle, _ptr(theta), _stream(stream)), "scivr_mlp_set_params")
+
+
+def scivr_mlp_loss_grad(pes: Pes, n, q, Vref, gref, alpha, beta, grad, loss, stream=None):
+    _check(_lib.scivr_mlp_loss_grad(pes.handle, int(n), _ptr(q), _ptr(Vref), _ptr(gref), float(alpha),
+                                    float(beta), _ptr(grad), _ptr(loss), _stream(stream)), "scivr_mlp_loss_grad")
+
+
+def scivr_mlp_adamw(pes: Pes, grad, m1, m2, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0,
+                    stream=None):
+    _check(_lib.scivr_mlp_adamw(pes.handle, _ptr(grad), _ptr(m1), _ptr(m2), int(t), float(lr), float(beta1),
+                                float(beta2), float(eps), float(weight_decay), _stream(stream)), "scivr_mlp_adamw")
+
+
+def scivr_pes_eval(pes: Pes, n, q, terms, V, g=None, H=None, stream=None):
+    _check(_lib.scivr_pes_eval(pes.handle, int(n), _ptr(q), int(terms), _ptr(V), _ptr(g), _ptr(H),
+                               _stream(stream)), "scivr_pes_eval")

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "scivr.h")).read()
+    import glob
+    text = "".join(open(f).read() for f in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(scivr_[a-z_0-9]+)\s*\(", text)))
 
@@ -96,3 +97,15 @@ def test_invalid_propagate_and_spectrum_arguments(lib):
     assert rc == scivr.SCIVR_EUNSUPPORTED
     rc = scivr._lib.scivr_spectrum(fake + 8, 11, 0, fake, fake, 4, 10, 10.0, 0.0, 0.1, 16, 0, fake, None, None)
     assert rc == scivr.SCIVR_EINVAL   # misaligned amplitudes
+
+
+def test_learned_residual_entry_points_validate_before_any_launch(lib):
+    from paper_1312_4698_gb300 import scivr
+    assert scivr.scivr_mlp_param_count(9) == 9 * 256 + 2 * 256 * 256 + 4 * 256 + 1
+    assert scivr.scivr_mlp_param_count(0) == 0
+    assert scivr._lib.scivr_pes_set_mlp(None, None) == scivr.SCIVR_EINVAL
+    assert scivr._lib.scivr_mlp_eval(None, 4, 1, 1, 1, None, None) == scivr.SCIVR_EINVAL
+    assert "NULL potential" in scivr.last_error()
+    assert scivr._lib.scivr_mlp_loss_grad(None, 4, 1, 1, 1, 1.0, 1.0, 1, 1, None) == scivr.SCIVR_EINVAL
+    assert scivr._lib.scivr_mlp_adamw(None, 1, 1, 1, 1, 1e-3, 0.9, 0.999, 1e-8, 0.0, None) == scivr.SCIVR_EINVAL
+    assert scivr._lib.scivr_pes_eval(None, 4, 1, 0, 1, None, None, None) == scivr.SCIVR_EINVAL
