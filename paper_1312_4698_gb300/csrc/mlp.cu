@@ -634,6 +634,501 @@ __global__ void k_adamw(float *__restrict__ theta, const float *__restrict__ gra
     theta[i] -= lr * (step + wd * theta[i]);
 }
 
+// ---------------------------------------------------------------- fused evaluation
+// V, grad V and the Hessian with every intermediate on chip.  A persistent CTA
+// (one per SM: 512 TMEM columns, ~225 KB of shared memory) walks 128-row tiles
+// of 12 points x (1 + F) rows.  Per tile:
+//   layer 1 (CUDA cores) -> A tile X2 in shared memory
+//   GEMM X2 W2^T -> TMEM[0:256)     epilogue: X3 = [silu(z2); silu'(z2) J2] -> A tile
+//   GEMM X3 W3^T -> TMEM[256:512)   epilogue: V, delta3 -> A tile, Hessian term of layer 3
+//   GEMM D3 W3   -> TMEM[256:512)   epilogue: delta2 -> A tile, Hessian term of layer 2 (J2 still in TMEM[0:256))
+//   GEMM D2 W2   -> TMEM[256:512)   epilogue: grad V and the layer-1 Hessian term, outputs
+// Warp roles: warps 0-7 compute (tile row r = TMEM lane r is shared by warps
+// r/32 and r/32 + 4, which take the column halves [0,128) and [128,256)),
+// warp 8 streams the BF16 weight tiles (16 KB k-blocks through a 3-stage ring,
+// cp.async.bulk), warp 9 issues tcgen05.mma.  Elementwise work on the point
+// rows is spread over all 256 compute threads through shared memory; the row
+// loops are branch-free (each row picks its source and factor pointers once).
+// The J^T diag(c) J products pair the tangent rows of a point through a shared
+// exchange buffer, 32 columns at a time; direction d takes the partners
+// d, d+1, ..., d + floor(F/2) (mod F), which covers every unordered pair once.
+constexpr int FU_STAGES = 3;
+constexpr int FU_NC = 256;                        // compute threads
+constexpr int FU_SPT = 12;                        // points per tile (F <= 9: 12 (F+1) <= 120 rows)
+constexpr int FU_PS = HW + 4;                     // padded row stride of the per-point buffers
+constexpr int FU_XS = 36;                         // row stride (floats) of the exchange buffer
+constexpr int FU_BUF = FU_SPT * FU_PS * 4;
+constexpr int FU_O_A = 0;                         // A tile: 8 k-blocks of 128 x 32 BF16
+constexpr int FU_O_B = FU_O_A + BM * HW * 2;      // weight ring
+constexpr int FU_O_Z1 = FU_O_B + FU_STAGES * TILE_B;
+constexpr int FU_O_Z2 = FU_O_Z1 + FU_BUF;
+constexpr int FU_O_P = FU_O_Z2 + FU_BUF;
+constexpr int FU_O_Q = FU_O_P + FU_BUF;
+constexpr int FU_O_ZB = FU_O_Q + FU_BUF;
+constexpr int FU_O_X = FU_O_ZB + FU_BUF;          // exchange rows [2][128][FU_XS]
+constexpr int FU_O_W1 = FU_O_X + 2 * BM * FU_XS * 4;  // W1 [256][F]
+constexpr int FU_O_PAR = FU_O_W1 + HW * kMaxF * 4;    // b1, b2, b3, w4 [256] each; s_in [16]; one
+constexpr int FU_O_XQ = FU_O_PAR + (4 * HW + 32) * 4; // x = s_in q [12][F]
+constexpr int FU_O_Y = FU_O_XQ + FU_SPT * kMaxF * 4;  // y per point
+constexpr int FU_SMEM = FU_O_Y + FU_SPT * 4;
+static_assert(FU_SMEM + 256 <= 227 * 1024, "fused evaluation exceeds shared memory");
+
+template <int F> struct FuCfg {
+    static constexpr int R = F + 1;
+    static constexpr int NE = F * (F + 1) / 2;
+    static constexpr int NJ = F / 2 + 1;          // partners per direction
+    static_assert(FU_SPT * R <= BM, "points of a tile exceed 128 rows");
+};
+
+__device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// silu and its first two derivatives (fast exponential and division: the
+// results feed BF16 operands)
+__device__ __forceinline__ void silu3f(float z, float &f, float &f1, float &f2)
+{
+    const float s = __fdividef(1.0f, 1.0f + __expf(-fmaxf(z, -80.0f)));
+    f = z * s;
+    f1 = s * (1.0f + z * (1.0f - s));
+    f2 = s * (1.0f - s) * (2.0f + z * (1.0f - 2.0f * s));
+}
+
+// Row r of the shared A tile, k = 32 ch .. 32 ch + 31.
+__device__ __forceinline__ void put_row32(uint8_t *sA, int r, int ch, const float (&v)[32])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[8 * j + 2 * i], v[8 * j + 2 * i + 1]);
+        *reinterpret_cast<uint4 *>(sA + ch * TILE_A + canon_off(r, 8 * j)) = *reinterpret_cast<const uint4 *>(h);
+    }
+}
+
+__device__ __forceinline__ void put_f32x32(float *dst, const float (&v)[32])
+{
+#pragma unroll
+    for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+}
+
+// hacc[j] += sum_i w[i] J_{(d + j) mod F}[i] over the 32 columns that the
+// tangent rows of this row's point left in ex.
+template <int F>
+__device__ __forceinline__ void pair_products(const float *ex, int row0, int d, const float (&w)[32],
+                                              float (&hacc)[FuCfg<F>::NJ])
+{
+#pragma unroll
+    for (int j = 0; j < FuCfg<F>::NJ; ++j) {
+        int k = d + j;
+        k = k >= F ? k - F : k;
+        const float *xr = ex + (row0 + 1 + k) * FU_XS;
+        float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 32; i += 8) {
+            const float4 x4 = *reinterpret_cast<const float4 *>(xr + i);
+            const float4 y4 = *reinterpret_cast<const float4 *>(xr + i + 4);
+            a0 = fmaf(w[i], x4.x, fmaf(w[i + 1], x4.y, fmaf(w[i + 2], x4.z, fmaf(w[i + 3], x4.w, a0))));
+            a1 = fmaf(w[i + 4], y4.x, fmaf(w[i + 5], y4.y, fmaf(w[i + 6], y4.z, fmaf(w[i + 7], y4.w, a1))));
+        }
+        hacc[j] += a0 + a1;
+    }
+}
+
+template <int F>
+__global__ void __launch_bounds__(320, 1)
+    k_mlp_fused(MlpDev m, int64_t n, int n_tiles, const float *__restrict__ q, float *__restrict__ Vout,
+                float *__restrict__ gout, float *__restrict__ Hout)
+{
+    using C = FuCfg<F>;
+    constexpr int R = C::R, NE = C::NE, NJ = C::NJ, SPT = FU_SPT, PS = FU_PS;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    uint8_t *sm = smem_raw;
+    uint8_t *sA = sm + FU_O_A;
+    uint8_t *sB = sm + FU_O_B;
+    float *z1s = reinterpret_cast<float *>(sm + FU_O_Z1);    // z1
+    float *z2s = reinterpret_cast<float *>(sm + FU_O_Z2);    // z2
+    float *pb = reinterpret_cast<float *>(sm + FU_O_P);      // silu'(z1), silu'(z2), abar2, abar1 -> d1
+    float *qb = reinterpret_cast<float *>(sm + FU_O_Q);      // c3, c2, c1
+    float *zb = reinterpret_cast<float *>(sm + FU_O_ZB);     // value-row staging: a1, a2, delta3, delta2
+    float *exb = reinterpret_cast<float *>(sm + FU_O_X);
+    float *w1s = reinterpret_cast<float *>(sm + FU_O_W1);
+    float *b1s = reinterpret_cast<float *>(sm + FU_O_PAR);
+    float *b2s = b1s + HW, *b3s = b2s + HW, *w4s = b3s + HW, *sins = w4s + HW, *one = sins + 16;
+    float *xq = reinterpret_cast<float *>(sm + FU_O_XQ);
+    float *ys = reinterpret_cast<float *>(sm + FU_O_Y);
+    __shared__ uint64_t full_bar[FU_STAGES], empty_bar[FU_STAGES], a_bar, c_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < FU_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        mbar_init(&a_bar, FU_NC);
+        mbar_init(&c_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < HW * F; i += blockDim.x) w1s[i] = m.W1[i];
+    for (int i = threadIdx.x; i < HW; i += blockDim.x) {
+        b1s[i] = m.b1[i];
+        b2s[i] = m.b2[i];
+        b3s[i] = m.b3[i];
+        w4s[i] = m.w4[i];
+    }
+    if (threadIdx.x < 16) sins[threadIdx.x] = threadIdx.x < F ? m.s_in[threadIdx.x] : 0.0f;
+    if (threadIdx.x == 0) one[0] = 1.0f;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                     "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 8) {
+        // ---------------- weight producer: per tile W2, W3 (forward), W3^T, W2^T (reverse)
+        if (lane == 0) {
+            int kc = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x)
+                for (int gm = 0; gm < 4 && ok; ++gm) {
+                    const uint8_t *Bsrc = gm == 0 ? m.W2t : gm == 1 ? m.W3t : gm == 2 ? m.W3Tt : m.W2Tt;
+                    for (int kt = 0; kt < KT_H; ++kt, ++kc) {
+                        const int s = kc % FU_STAGES, use = kc / FU_STAGES;
+                        if ((use > 0 && !mbar_wait(&empty_bar[s], (use - 1) & 1, kWaitLimitCycles)) ||
+                            *(volatile int *)&abort_flag) {
+                            atomicExch(&abort_flag, 1);
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&full_bar[s], TILE_B);
+                        bulk_g2s(sB + s * TILE_B, Bsrc + (size_t)kt * TILE_B, TILE_B, &full_bar[s]);
+                    }
+                }
+            // do not leave with copies still landing in shared memory
+            for (int k = kc - FU_STAGES > 0 ? kc - FU_STAGES : 0; k < kc; ++k)
+                mbar_wait(&full_bar[k % FU_STAGES], (k / FU_STAGES) & 1, kWaitLimitCycles);
+        }
+    } else if (warp == 9) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            const uint32_t a0 = su32(sA), b0 = su32(sB);
+            int kc = 0, ca = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x)
+                for (int gm = 0; gm < 4 && ok; ++gm) {
+                    if (!mbar_wait(&a_bar, ca & 1, kWaitLimitCycles) || *(volatile int *)&abort_flag) {
+                        atomicExch(&abort_flag, 1);
+                        ok = false;
+                        break;
+                    }
+                    ++ca;
+                    tc_fence_after();
+                    const uint32_t d = tmem + (gm == 0 ? 0u : 256u);
+                    for (int kt = 0; kt < KT_H; ++kt, ++kc) {
+                        const int s = kc % FU_STAGES;
+                        if (!mbar_wait(&full_bar[s], (kc / FU_STAGES) & 1, kWaitLimitCycles)) {
+                            atomicExch(&abort_flag, 1);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+#pragma unroll
+                        for (int ks = 0; ks < BK / 16; ++ks)
+                            umma(d, sdesc(a0 + kt * TILE_A + ks * 2 * LBO), sdesc(b0 + s * TILE_B + ks * 2 * LBO),
+                                 idesc, (kt | ks) != 0);
+                        umma_commit(&empty_bar[s]);
+                    }
+                    umma_commit(&c_bar);   // also on abort: the compute warps are waiting on it
+                }
+        }
+    } else {
+        // ---------------- compute warps
+        const int c = threadIdx.x;            // 0..255
+        const int hf = warp >> 2;             // column half
+        const int r = (warp & 3) * 32 + lane; // tile row = TMEM lane
+        const int sr = r / R, kr = r % R;     // point of the row; 0 = value row, k = direction k - 1
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + hf * 128;
+        float *ex = exb + hf * BM * FU_XS;
+        int cc = 0;
+        // wait for the accumulator of the current GEMM; uniform verdict over the compute threads
+        auto wait_acc = [&]() -> bool {
+            if (!mbar_wait(&c_bar, cc & 1, kWaitLimitCycles)) atomicExch(&abort_flag, 1);
+            ++cc;
+            tc_fence_after();
+            named_sync();
+            return *(volatile int *)&abort_flag == 0;
+        };
+        auto release_a = [&]() {
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(&a_bar);
+        };
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            const int64_t p0 = (int64_t)t * SPT;
+            const bool valid = sr < SPT && p0 + sr < n;
+            const bool prim = valid && kr == 0, tang = valid && kr > 0;
+            const int d = tang ? kr - 1 : 0;          // this row's direction
+            const float sv = valid ? 1.0f : 0.0f, pv = prim ? 1.0f : 0.0f;
+            const int rowp = (valid ? sr : 0) * PS;   // this row's point in the per-point buffers
+            const int row0 = (valid ? sr : 0) * R;    // the point's first tile row
+            float hacc[NJ];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) hacc[j] = 0.0f;
+
+            // ---- layer 1 (CUDA cores)
+            if (c < SPT * F) {
+                const int s = c / F, k = c % F;
+                const int64_t b = p0 + s;
+                xq[c] = b < n ? sins[k] * q[b * F + k] : 0.0f;
+            }
+            if (c < SPT) ys[c] = *m.b4;
+            named_sync();
+            for (int idx = c; idx < SPT * HW; idx += FU_NC) {
+                const int s = idx >> 8, o = idx & (HW - 1);
+                float z = b1s[o];
+#pragma unroll
+                for (int k = 0; k < F; ++k) z = fmaf(w1s[o * F + k], xq[s * F + k], z);
+                float f, f1, f2;
+                silu3f(z, f, f1, f2);
+                z1s[s * PS + o] = z;
+                zb[s * PS + o] = f;
+                pb[s * PS + o] = f1;
+            }
+            named_sync();
+            {
+                const float *src = (prim ? zb : pb) + rowp;
+                const float *fac = tang ? w1s + d : one;
+                const int fst = tang ? F : 0;
+#pragma unroll 1
+                for (int j = 0; j < 4; ++j) {
+                    const int ch = hf * 4 + j;
+                    float v[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int o = ch * 32 + i;
+                        v[i] = sv * src[o] * fac[o * fst];
+                    }
+                    put_row32(sA, r, ch, v);
+                }
+            }
+            release_a();
+
+            // ---- layer 2: TMEM[0:256) holds z2 - b2 (value rows) and J2 (tangent rows)
+            if (!wait_acc()) break;
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                float v[32];
+                tmem_ld32(lane_base + j * 32, v);
+                tmem_wait_ld();
+                if (prim) put_f32x32(zb + rowp + (hf * 4 + j) * 32, v);
+            }
+            named_sync();
+            for (int idx = c; idx < SPT * HW; idx += FU_NC) {
+                const int s = idx >> 8, o = idx & (HW - 1);
+                const float z = zb[s * PS + o] + b2s[o];
+                float f, f1, f2;
+                silu3f(z, f, f1, f2);
+                z2s[s * PS + o] = z;
+                zb[s * PS + o] = f;
+                pb[s * PS + o] = f1;
+            }
+            named_sync();
+            {
+                const float *src = (prim ? zb : pb) + rowp;
+#pragma unroll 1
+                for (int j = 0; j < 4; ++j) {
+                    const int ch = hf * 4 + j;
+                    float v[32];
+                    tmem_ld32(lane_base + j * 32, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = sv * src[ch * 32 + i] * fmaf(pv, 1.0f - v[i], v[i]);
+                    put_row32(sA, r, ch, v);
+                }
+            }
+            release_a();
+
+            // ---- layer 3: TMEM[256:512) holds z3 - b3 and J3; V, delta3 and the layer-3 Hessian term
+            if (!wait_acc()) break;
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                float v[32];
+                tmem_ld32(lane_base + 256 + j * 32, v);
+                tmem_wait_ld();
+                if (prim) put_f32x32(zb + rowp + (hf * 4 + j) * 32, v);
+            }
+            named_sync();
+            for (int idx = c; idx < SPT * HW; idx += FU_NC) {   // the 256 entries of one pass share a point
+                const int s = idx >> 8, o = idx & (HW - 1);
+                float f, f1, f2;
+                silu3f(zb[s * PS + o] + b3s[o], f, f1, f2);
+                const float w4 = w4s[o];
+                zb[s * PS + o] = w4 * f1;        // delta3
+                qb[s * PS + o] = w4 * f2;        // c3
+                float y = w4 * f;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
+                if (lane == 0) atomicAdd(&ys[s], y);
+            }
+            named_sync();
+            if (prim && hf == 0) Vout[p0 + sr] = m.s_out * ys[sr];
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                const int ch = hf * 4 + j;
+                float v[32], x[32], w[32];
+                tmem_ld32(lane_base + 256 + j * 32, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 32; ++i) x[i] = pv * zb[rowp + ch * 32 + i];
+                put_row32(sA, r, ch, x);
+                put_f32x32(ex + r * FU_XS, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) w[i] = qb[rowp + ch * 32 + i] * v[i];
+                named_sync();
+                pair_products<F>(ex, row0, d, w, hacc);
+                named_sync();
+            }
+            release_a();
+
+            // ---- reverse through layer 3: TMEM[256:512) = abar2 (value rows); J2 in TMEM[0:256)
+            if (!wait_acc()) break;
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                float v[32];
+                tmem_ld32(lane_base + 256 + j * 32, v);
+                tmem_wait_ld();
+                if (prim) put_f32x32(pb + rowp + (hf * 4 + j) * 32, v);
+            }
+            named_sync();
+            for (int idx = c; idx < SPT * HW; idx += FU_NC) {
+                const int s = idx >> 8, o = idx & (HW - 1);
+                float f, f1, f2;
+                silu3f(z2s[s * PS + o], f, f1, f2);
+                const float ab = pb[s * PS + o];
+                zb[s * PS + o] = ab * f1;        // delta2 = abar2 silu'(z2)
+                qb[s * PS + o] = ab * f2;        // c2 = abar2 silu''(z2)
+            }
+            named_sync();
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                const int ch = hf * 4 + j;
+                float v[32], x[32], w[32];
+                tmem_ld32(lane_base + j * 32, v);          // J2
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 32; ++i) x[i] = pv * zb[rowp + ch * 32 + i];
+                put_row32(sA, r, ch, x);
+                put_f32x32(ex + r * FU_XS, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) w[i] = qb[rowp + ch * 32 + i] * v[i];
+                named_sync();
+                pair_products<F>(ex, row0, d, w, hacc);
+                named_sync();
+            }
+            release_a();
+
+            // ---- reverse through layer 2: TMEM[256:512) = abar1; grad V and the layer-1 term
+            if (!wait_acc()) break;
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                float v[32];
+                tmem_ld32(lane_base + 256 + j * 32, v);
+                tmem_wait_ld();
+                if (prim) put_f32x32(pb + rowp + (hf * 4 + j) * 32, v);
+            }
+            tc_fence_before();
+            named_sync();
+            for (int idx = c; idx < SPT * HW; idx += FU_NC) {
+                const int s = idx >> 8, o = idx & (HW - 1);
+                float f, f1, f2;
+                silu3f(z1s[s * PS + o], f, f1, f2);
+                const float ab = pb[s * PS + o];
+                pb[s * PS + o] = ab * f1;        // d1 = abar1 silu'(z1)
+                qb[s * PS + o] = ab * f2;        // c1 = abar1 silu''(z1)
+            }
+            // the two column halves of each row add their Hessian partial sums
+            if (hf == 1) {
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) exb[r * FU_XS + j] = hacc[j];
+            }
+            named_sync();
+            if (hf == 0) {
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) hacc[j] += exb[r * FU_XS + j];
+            }
+            // grad V and H1 = W1^T diag(c1) W1: thread (point s, slice sl) sums 16 hidden units,
+            // then the 16 slices of a point (adjacent lanes) are added by shuffles
+            if (c < SPT * 16) {
+                const int s = c >> 4, sl = c & 15;
+                float ga[F], ha[NE];
+#pragma unroll
+                for (int k = 0; k < F; ++k) ga[k] = 0.0f;
+#pragma unroll
+                for (int e = 0; e < NE; ++e) ha[e] = 0.0f;
+#pragma unroll 1
+                for (int oo = 0; oo < 16; ++oo) {
+                    const int o = sl * 16 + ((oo + sl) & 15);   // staggered start: fewer bank conflicts
+                    const float d1 = pb[s * PS + o], c1 = qb[s * PS + o];
+                    float wk[F];
+#pragma unroll
+                    for (int k = 0; k < F; ++k) wk[k] = w1s[o * F + k];
+                    int e = 0;
+#pragma unroll
+                    for (int k1 = 0; k1 < F; ++k1) {
+                        ga[k1] = fmaf(d1, wk[k1], ga[k1]);
+                        const float cw = c1 * wk[k1];
+#pragma unroll
+                        for (int k2 = k1; k2 < F; ++k2, ++e) ha[e] = fmaf(cw, wk[k2], ha[e]);
+                    }
+                }
+#pragma unroll
+                for (int off = 1; off < 16; off <<= 1) {
+#pragma unroll
+                    for (int k = 0; k < F; ++k) ga[k] += __shfl_xor_sync(0xffffffffu, ga[k], off);
+#pragma unroll
+                    for (int e = 0; e < NE; ++e) ha[e] += __shfl_xor_sync(0xffffffffu, ha[e], off);
+                }
+                const int64_t b = p0 + s;
+                if (sl == 0 && b < n) {
+#pragma unroll
+                    for (int k = 0; k < F; ++k) gout[b * F + k] = m.s_out * sins[k] * ga[k];
+#pragma unroll
+                    for (int e = 0; e < NE; ++e) zb[s * PS + e] = ha[e];
+                }
+            }
+            named_sync();
+            if (tang && hf == 0) {
+                const int64_t b = p0 + sr;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    int k = d + j;
+                    k = k >= F ? k - F : k;
+                    if ((F % 2 == 0) && j == F / 2 && d >= F / 2) continue;   // pair already taken
+                    const int lo = d < k ? d : k, hi = d < k ? k : d;
+                    const int e = lo * F - lo * (lo - 1) / 2 + (hi - lo);
+                    const float h = m.s_out * sins[d] * sins[k] * (hacc[j] + zb[rowp + e]);
+                    Hout[(b * F + d) * F + k] = h;
+                    Hout[(b * F + k) * F + d] = h;
+                }
+            }
+            named_sync();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
 // ---------------------------------------------------------------- host side
 inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -734,6 +1229,10 @@ cudaError_t set_smem_attributes()
                                  TSMEM + 2 * TR_SPT * kMaxF * 4);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tr_out, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tr_back, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM);
+#define SCIVR_FA(FF) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_fused<FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, FU_SMEM);
+    SCIVR_FA(1) SCIVR_FA(2) SCIVR_FA(3) SCIVR_FA(4) SCIVR_FA(5) SCIVR_FA(6) SCIVR_FA(7) SCIVR_FA(8) SCIVR_FA(9)
+#undef SCIVR_FA
     return e;
 }
 
@@ -765,6 +1264,22 @@ cudaError_t eval_F(const MlpWeightsDev &w, int64_t n, const float *q, float *V, 
     gemm_rows(D2, m.W2Tt, Ab1, L.n_pad, s);
     k_grad_hess<F, HESS><<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(m, n, Z1, C2, C3, Ab2, Ab1, g, H);
     *n_launch = 9;
+    return cudaGetLastError();
+}
+
+template <int F>
+cudaError_t eval_fused_F(const MlpWeightsDev &w, int64_t n, const float *q, float *V, float *g, float *H,
+                         cudaStream_t s, int *n_launch)
+{
+    const MlpDev m = make_dev(w, F, F + 1);
+    const int64_t n_tiles = (n + FU_SPT - 1) / FU_SPT;
+    int dev = 0, n_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)(n_tiles < n_sm ? n_tiles : n_sm);
+    k_mlp_fused<F><<<grid, 320, FU_SMEM, s>>>(m, n, (int)n_tiles, q, V, g, H);
+    *n_launch = 1;
     return cudaGetLastError();
 }
 
@@ -810,7 +1325,10 @@ cudaError_t loss_grad_F(const MlpWeightsDev &w, int64_t n, const float *q, const
 
 }  // namespace mlp
 
-size_t mlp_eval_scratch_bytes(int F, int64_t n, bool hess) { return mlp::eval_layout(F, n, hess).total; }
+size_t mlp_eval_scratch_bytes(int F, int64_t n, bool hess)
+{
+    return hess ? 256 : mlp::eval_layout(F, n, false).total;   // the Hessian path keeps everything on chip
+}
 size_t mlp_train_scratch_bytes(int F, int64_t n) { return mlp::train_layout(F, n).total; }
 
 cudaError_t mlp_prepare() { return mlp::set_smem_attributes(); }
@@ -822,7 +1340,7 @@ cudaError_t mlp_eval(const MlpWeightsDev &w, int F, int64_t n, const float *q, f
     switch (F) {
 #define SCIVR_M(FF)                                                                         \
     case FF:                                                                                \
-        return H ? mlp::eval_F<FF, true>(w, n, q, V, g, H, scr, s, n_launch)                \
+        return H ? mlp::eval_fused_F<FF>(w, n, q, V, g, H, s, n_launch)                     \
                  : mlp::eval_F<FF, false>(w, n, q, V, g, H, scr, s, n_launch);
     SCIVR_M(1) SCIVR_M(2) SCIVR_M(3) SCIVR_M(4) SCIVR_M(5) SCIVR_M(6) SCIVR_M(7) SCIVR_M(8) SCIVR_M(9)
 #undef SCIVR_M

@@ -72,8 +72,12 @@ __device__ __forceinline__ void drift(State &st, int64_t j, int64_t n, double td
     }
 }
 
-template <int F>
-__global__ void __launch_bounds__(128) k_mlp_stage(const PropLaunch L, State st, int stage)
+// KIND 0: set-up and the first drift; 1: a kick and a drift (stage = 1, 2);
+// 3: the last kick and drift of a step, the per-step diagnostics, and the next
+// step's first drift.  COUPLED: the analytic part has coupling terms (else it
+// is the separable diagonal alone and its Hessian is diagonal).
+template <int F, int KIND, bool COUPLED>
+__global__ void __launch_bounds__(KIND == 3 ? 64 : 128) k_mlp_stage(const PropLaunch L, State st, int stage)
 {
     constexpr int N2 = 2 * F;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(128) k_mlp_stage(const PropLaunch L, State st,
     if (stage == 1 && j == 0) *st.step += 1;   // read by stage 3 of this step (later in stream order)
     if (j >= n) return;
     double p[F], q[F], S;
-    if (stage == 0) {
+    if (KIND == 0) {
 #pragma unroll
         for (int a = 0; a < F; ++a) {
             p[a] = L.p0[a * n + j];
@@ -104,18 +108,48 @@ __global__ void __launch_bounds__(128) k_mlp_stage(const PropLaunch L, State st,
         }
         S = st.S[j];
         // kick d_{stage-1}: analytic part (FP64) + network part (FP32)
-        double H[F][F], g[F], V;
-        tpt::pes_fp64<F>(L.pes, q, H, g, V);
         const double tk = A.tkick[stage - 1];
-        V += (double)st.Vm[j];
-        S = fma(-tk, V, S);
-#pragma unroll
-        for (int a = 0; a < F; ++a) p[a] = fma(-tk, g[a] + (double)st.gm[j * F + a], p[a]);
+        const float tkf = A.tkick_f[stage - 1];
         float Hk[F][F];
 #pragma unroll
         for (int a = 0; a < F; ++a)
 #pragma unroll
-            for (int b = 0; b < F; ++b) Hk[a][b] = (float)(tk * H[a][b]) + A.tkick_f[stage - 1] * st.Hm[(j * F + a) * F + b];
+            for (int b = 0; b < F; ++b) Hk[a][b] = tkf * st.Hm[(j * F + a) * F + b];
+        double V = (double)st.Vm[j];
+        if constexpr (COUPLED) {
+            double H[F][F], g[F], Va;
+            tpt::pes_fp64<F>(L.pes, q, H, g, Va);
+            V += Va;
+#pragma unroll
+            for (int a = 0; a < F; ++a) {
+                p[a] = fma(-tk, g[a] + (double)st.gm[j * F + a], p[a]);
+#pragma unroll
+                for (int b = 0; b < F; ++b) Hk[a][b] += (float)(tk * H[a][b]);
+            }
+        } else {
+            // separable diagonal only: V, grad V and the (diagonal) Hessian per mode
+#pragma unroll
+            for (int a = 0; a < F; ++a) {
+                double Va, ga, ha;
+                if (L.pes.diag_kind == SCIVR_DIAG_MORSE) {
+                    const double Dm = __ldg(L.pes.D + a), am = __ldg(L.pes.a + a);
+                    const double u = exp(-am * q[a]);
+                    const double omu = 1.0 - u;
+                    Va = Dm * omu * omu;
+                    ga = 2.0 * Dm * am * u * omu;
+                    ha = 2.0 * Dm * am * am * u * (2.0 * u - 1.0);
+                } else {
+                    const double w2 = __ldg(L.pes.omega + a) * __ldg(L.pes.omega + a);
+                    Va = 0.5 * w2 * q[a] * q[a];
+                    ga = w2 * q[a];
+                    ha = w2;
+                }
+                V += Va;
+                p[a] = fma(-tk, ga + (double)st.gm[j * F + a], p[a]);
+                Hk[a][a] += (float)(tk * ha);
+            }
+        }
+        S = fma(-tk, V, S);
 #pragma unroll 1
         for (int c = 0; c < N2; ++c) {
             float mq[F];
@@ -132,48 +166,85 @@ __global__ void __launch_bounds__(128) k_mlp_stage(const PropLaunch L, State st,
         }
     }
     drift<F>(st, j, n, A.tdrift[stage], A.tdrift_f[stage], p, q, S);
-    if (stage == 3) {
+    if (KIND == 3) {
         const int step = *st.step;
         bool good = L.good[j] != 0;
-        // stability |det(M)^2 - 1| (FP32 LU with partial pivoting)
-        float W[N2][N2];
+        // stability |det(M)^2 - 1| (FP32 LU with partial pivoting).  The work
+        // matrices live in shared memory as [element][thread] (bank-conflict
+        // free); thread-local arrays of this size would spill past L1.
+        extern __shared__ __align__(16) uint8_t fin_smem[];
+        constexpr int NT = 64;   // threads per block of the final stage
+        const int tid = threadIdx.x;
+        float *W = reinterpret_cast<float *>(fin_smem) + tid;
+        auto w = [&](int r, int c) -> float & { return W[(r * N2 + c) * NT]; };
         for (int r = 0; r < N2; ++r)
-            for (int c = 0; c < N2; ++c) W[r][c] = st.M[((int64_t)r * N2 + c) * n + j];
+            for (int c = 0; c < N2; ++c) w(r, c) = st.M[((int64_t)r * N2 + c) * n + j];
         float det = 1.0f;
         for (int k = 0; k < N2; ++k) {
             int piv = k;
-            float best = fabsf(W[k][k]);
+            float best = fabsf(w(k, k));
             for (int i = k + 1; i < N2; ++i)
-                if (fabsf(W[i][k]) > best) { best = fabsf(W[i][k]); piv = i; }
+                if (fabsf(w(i, k)) > best) { best = fabsf(w(i, k)); piv = i; }
             if (piv != k) {
-                for (int c = k; c < N2; ++c) { const float t = W[k][c]; W[k][c] = W[piv][c]; W[piv][c] = t; }
+                for (int c = k; c < N2; ++c) { const float t = w(k, c); w(k, c) = w(piv, c); w(piv, c) = t; }
                 det = -det;
             }
-            const float akk = W[k][k];
+            const float akk = w(k, k);
             det *= akk;
             const float inv = 1.0f / akk;
             for (int i = k + 1; i < N2; ++i) {
-                const float l = W[i][k] * inv;
-                for (int c = k + 1; c < N2; ++c) W[i][c] = fmaf(-l, W[k][c], W[i][c]);
+                const float l = w(i, k) * inv;
+#pragma unroll 6
+                for (int c = k + 1; c < N2; ++c) w(i, c) = fmaf(-l, w(k, c), w(i, c));
             }
         }
         const float dev = isfinite(det) ? fabsf(fmaf(det, det, -1.0f)) : __int_as_float(0x7f800000);
         const double stab = fmax(st.stab[j], (double)dev);
         st.stab[j] = stab;
         if (dev > A.stab_tol_f) good = false;
-        // Herman-Kluk prefactor determinant (FP64) and the continuous phase
-        tpt::cplx Am[F][F];
+        // Herman-Kluk prefactor determinant (FP64, complex LU with partial
+        // pivoting) in the same shared memory, as [element][re/im][thread]
+        double *Z = reinterpret_cast<double *>(fin_smem) + tid;
+        auto zr = [&](int a, int b) -> double & { return Z[((a * F + b) * 2) * NT]; };
+        auto zi = [&](int a, int b) -> double & { return Z[((a * F + b) * 2 + 1) * NT]; };
         for (int a = 0; a < F; ++a)
             for (int b = 0; b < F; ++b) {
                 const double mqq = st.M[((int64_t)(F + a) * N2 + F + b) * n + j];
                 const double mpp = st.M[((int64_t)a * N2 + b) * n + j];
                 const double mqp = st.M[((int64_t)(F + a) * N2 + b) * n + j];
                 const double mpq = st.M[((int64_t)a * N2 + F + b) * n + j];
-                const double re = fma(A.rg[a] * A.irg[b], mqq, A.rg[b] * A.irg[a] * mpp);
-                const double im = fma(-A.rg[a] * A.rg[b], mqp, A.irg[a] * A.irg[b] * mpq);
-                Am[a][b] = {0.5 * re, 0.5 * im};
+                zr(a, b) = 0.5 * fma(A.rg[a] * A.irg[b], mqq, A.rg[b] * A.irg[a] * mpp);
+                zi(a, b) = 0.5 * fma(-A.rg[a] * A.rg[b], mqp, A.irg[a] * A.irg[b] * mpq);
             }
-        const tpt::cplx dA = tpt::det_complex<F>(Am);
+        tpt::cplx dA = {1.0, 0.0};
+        for (int k = 0; k < F; ++k) {
+            int piv = k;
+            double best = zr(k, k) * zr(k, k) + zi(k, k) * zi(k, k);
+            for (int i = k + 1; i < F; ++i) {
+                const double v = zr(i, k) * zr(i, k) + zi(i, k) * zi(i, k);
+                if (v > best) { best = v; piv = i; }
+            }
+            if (piv != k) {
+                for (int c = k; c < F; ++c) {
+                    const double tr = zr(k, c), ti = zi(k, c);
+                    zr(k, c) = zr(piv, c); zi(k, c) = zi(piv, c);
+                    zr(piv, c) = tr; zi(piv, c) = ti;
+                }
+                dA.re = -dA.re; dA.im = -dA.im;
+            }
+            const tpt::cplx akk = {zr(k, k), zi(k, k)};
+            dA = tpt::cmul(dA, akk);
+            const double rr = 1.0 / (akk.re * akk.re + akk.im * akk.im);
+            const tpt::cplx inv = {akk.re * rr, -akk.im * rr};
+            for (int i = k + 1; i < F; ++i) {
+                const tpt::cplx l = tpt::cmul({zr(i, k), zi(i, k)}, inv);
+                for (int c = k + 1; c < F; ++c) {
+                    const tpt::cplx y = tpt::cfnma(l, {zr(k, c), zi(k, c)}, {zr(i, c), zi(i, c)});
+                    zr(i, c) = y.re;
+                    zi(i, c) = y.im;
+                }
+            }
+        }
         const double arg_new = atan2(dA.im, dA.re);
         double d = arg_new - st.arg_old[j] + A.ref_step;
         d = fma(-kTwoPi, rint(d * kInvTwoPi), d);
@@ -253,8 +324,16 @@ cudaError_t run(const PropLaunch &L, cudaStream_t s, int *n_launch)
     e = cudaMemsetAsync(st.step, 0, sizeof(int), s);
     if (e == cudaSuccess) e = mlp_prepare();
     const unsigned blocks = (unsigned)((n + 127) / 128);
+    // final stage: one [element][thread] work array per thread, 16 F^2 bytes (the
+    // FP32 (2F)^2 LU and the FP64 complex F^2 LU need the same size)
+    const size_t fin_smem = (size_t)64 * 16 * F * F;
     if (e == cudaSuccess) {
-        k_mlp_stage<F><<<blocks, 128, 0, s>>>(L, st, 0);
+        e = cudaFuncSetAttribute(k_mlp_stage<F, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fin_smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mlp_stage<F, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fin_smem);
+    }
+    if (e == cudaSuccess) {
+        k_mlp_stage<F, 0, false><<<blocks, 128, 0, s>>>(L, st, 0);
         nl += 1;
         for (int step = 1; step <= L.args.n_steps && e == cudaSuccess; ++step) {
             for (int stage = 1; stage <= 3; ++stage) {
@@ -262,7 +341,15 @@ cudaError_t run(const PropLaunch &L, cudaStream_t s, int *n_launch)
                 e = mlp_eval(L.pes.mlp, F, n, st.qf, Vm, gm, Hm, b + oEval, s, &ne);
                 nl += ne;
                 if (e != cudaSuccess) break;
-                k_mlp_stage<F><<<blocks, 128, 0, s>>>(L, st, stage);
+                const bool cpl = L.pes.has3 || L.pes.has4;
+                if (stage < 3) {
+                    if (cpl) k_mlp_stage<F, 1, true><<<blocks, 128, 0, s>>>(L, st, stage);
+                    else k_mlp_stage<F, 1, false><<<blocks, 128, 0, s>>>(L, st, stage);
+                } else {
+                    const unsigned b64 = (unsigned)((n + 63) / 64);
+                    if (cpl) k_mlp_stage<F, 3, true><<<b64, 64, fin_smem, s>>>(L, st, stage);
+                    else k_mlp_stage<F, 3, false><<<b64, 64, fin_smem, s>>>(L, st, stage);
+                }
                 nl += 1;
             }
             if (e == cudaSuccess) e = cudaGetLastError();
