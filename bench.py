@@ -7,7 +7,7 @@ amplitudes) over n_steps, and the time -> energy transform with the weighted
 Morse + cubic + quartic surface, 16384 trajectories, 4000 steps of 10 au,
 4000 energies, FP64 propagation and FP64 Fourier step.
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload f6|f3|f9]
+  python bench.py [--gpus N --steps K --warmup W] [--workload f6|f3|f9|batch|f9mlp]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
 
 Multi-GPU (torchrun): weak scaling, every rank runs its own batch (seed
@@ -197,8 +197,20 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w8 = sized(workload(args.workload, 0), args)
+    if args.workload == "batch":
+        print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no single oracle "
+                          "configuration; time --workload f3/f6/f9/f9mlp instead"}))
+        return 0
     n_sample = args.cpu_sample
+    if args.workload == "f9mlp":
+        # the oracle on the same surface type: Morse diagonal + a network of the same shape
+        base = sized(wl.config_f9(seed=0), args)
+        w8 = base.with_(pes=wl.PesDesc(base.F, base.pes.diag_kind, base.pes.omega, base.pes.D, base.pes.a,
+                                       np.zeros((0, 3)), np.zeros(0), np.zeros((0, 4)), np.zeros(0),
+                                       wl.init_mlp(base.F, 256, 0, s_in=np.sqrt(base.pes.omega), s_out=3e-6)))
+        n_sample = min(n_sample, 16)
+    else:
+        w8 = sized(workload(args.workload, 0), args)
     times = []
     for i in range(args.warmup + args.steps):
         r = run_cpu_oracle(w8, n_sample, 0)
@@ -328,13 +340,268 @@ def batch_arm(args):
     return 0
 
 
+def mlp_flops_per_point(F: int, H: int = 256) -> float:
+    """Algorithmic flops of one value + gradient + Hessian evaluation of the
+    learned residual (multiply-add = 2 flops): layer 1 for the point and its F
+    tangent directions, the two 256 x 256 forward layers on 1 + F rows, the two
+    reverse layers on the point row, the output layer, and the Hessian terms
+    J_l^T diag(c_l) J_l of the three layers (F(F+1)/2 pairs over H units each)."""
+    R = F + 1
+    fwd = 2 * (F * H + F * H) + 2 * 2 * R * H * H + 2 * H
+    rev = 2 * 2 * H * H + 2 * F * H
+    hess = 3 * 2 * (F * (F + 1) // 2) * H
+    return float(fwd + rev + hess)
+
+
+def surrogate_arm(args):
+    """Learned-residual surface (F = 9 recipe): the network learns the coupling
+    polynomial from 2^21 points of FP64 trajectories of the analytic surface
+    (training untimed, reported), then each step samples, propagates on
+    diagonal + network (one fused tensor-core evaluation per force stage) and
+    takes the spectrum."""
+    import torch
+    import torch.distributed as dist
+    from paper_1312_4698_gb300 import scivr, shards, surrogate as su
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w8 = sized(wl.config_f9(seed=rank), args)
+    n, K = w8.n_traj, w8.n_steps + 1
+    ftm = FT_MODES[args.ft]
+
+    # ---- training set and training (untimed)
+    full = scivr.scivr_create_pes(w8.pes)
+    t0 = time.perf_counter()
+    q = su.trajectory_points(full, w8, n_traj=65536, n_seg=32, seg_steps=20, seed=1000 + rank)
+    V, g = su.coupling_targets(full, q)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = su.initial_network(w8, V, seed=rank)
+    pes = scivr.scivr_create_pes(su.surrogate_pes(w8, net))
+    res = su.train(pes, q, V, g, epochs=args.train_epochs, batch=16384, lr=3e-3)
+    qh = su.trajectory_points(full, w8, n_traj=2048, n_seg=2, seg_steps=50, seed=2000 + rank)
+    Vh, gh = su.coupling_targets(full, qh)
+    Vn = torch.empty(qh.shape[0], device=dev)
+    gn = torch.empty(qh.shape[0], w8.F, device=dev)
+    scivr.scivr_mlp_eval(pes, qh.shape[0], qh.float().contiguous(), Vn, gn, None)
+    held = {"V": float(torch.linalg.norm(Vn.double() - Vh) / torch.linalg.norm(Vh)),
+            "grad": float(torch.linalg.norm(gn.double() - gh) / torch.linalg.norm(gh))}
+
+    # ---- accuracy on a trajectory subset: surrogate vs the FP64 path (parity-tested
+    # against the FP64 oracle) and vs the same run without the network
+    n_chk = min(n, args.check_traj)
+    wc = w8.with_(n_traj=n_chk)
+
+    def spectrum_of(p_, precision, tol):
+        b = scivr.alloc_buffers(wc, device=dev)
+        scivr.scivr_sample_initial(p_, wc.gamma, wc.p_eq[0], wc.q_eq[0], n_chk, 77, b.p0, b.q0, b.w)
+        scivr.scivr_propagate(p_, wc.dt, wc.n_steps, wc.gamma, wc.p_eq, wc.q_eq, n_chk, b.p0, b.q0, b.amp, K,
+                              b.good, precision=precision, stab_tol=tol)
+        scivr.scivr_spectrum(b.amp[0], K, b.w, b.good, n_chk, wc.n_steps, wc.dt, wc.E_min, wc.E_max, wc.n_E,
+                             b.I[0], b.n_good)
+        return b.I[0].cpu().numpy()
+
+    I_ref = spectrum_of(full, PRECISIONS["fp64"], w8.stab_tol)
+    I_sur = spectrum_of(pes, PRECISIONS["mixed"], MIXED_STAB_TOL)
+    I_dia = spectrum_of(scivr.scivr_create_pes(su.diagonal_part(w8.pes)), PRECISIONS["fp64"], w8.stab_tol)
+    E = wc.energies()
+    pk_ref = wl.spectrum_peaks(E, I_ref)
+    accuracy = {
+        "trajectories": n_chk, "reference": "FP64 GPU path on the analytic surface (parity-tested "
+                                            "against the FP64 oracle to 1e-9)",
+        "peaks": int(pk_ref.size),
+        "max_peak_shift_cm1": float(wl.to_cm1(wl.peak_shift(pk_ref, wl.spectrum_peaks(E, I_sur)))),
+        "max_norm_error": float(np.max(np.abs(I_sur - I_ref)) / np.max(np.abs(I_ref))),
+        "without_network_max_norm_error": float(np.max(np.abs(I_dia - I_ref)) / np.max(np.abs(I_ref))),
+        "without_network_max_peak_shift_cm1": float(wl.to_cm1(wl.peak_shift(pk_ref, wl.spectrum_peaks(E, I_dia)))),
+    }
+
+    # ---- timed steps
+    bufs = scivr.alloc_buffers(w8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = {k: [] for k in ("prop0", "prop1", "spec1")}
+
+    def one_step(record):
+        scivr.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], n, w8.seed, bufs.p0, bufs.q0, bufs.w,
+                                   stream)
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True); e0.record(stream); ev["prop0"].append(e0)
+        scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0, bufs.q0, bufs.amp,
+                              K, bufs.good, precision=PRECISIONS["mixed"], stab_tol=MIXED_STAB_TOL, stream=stream)
+        if record:
+            e1 = torch.cuda.Event(enable_timing=True); e1.record(stream); ev["prop1"].append(e1)
+        scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E,
+                             bufs.I[0], bufs.n_good, ft_mode=ftm, stream=stream)
+        if record:
+            e2 = torch.cuda.Event(enable_timing=True); e2.record(stream); ev["spec1"].append(e2)
+        if world > 1:
+            shards.combine_spectra_async(bufs.I[0], bufs.n_good)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    scivr.launch_count(reset=True)
+    ts = torch.cuda.Event(enable_timing=True)
+    te = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_selector(local)) as clk:
+        ts.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            one_step(True)
+        te.record(stream)
+        torch.cuda.synchronize()
+    launches = scivr.launch_count(reset=True)
+    if world > 1:
+        dist.barrier()
+    t = torch.tensor([ts.elapsed_time(te)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    prop_avg = float(np.mean([a.elapsed_time(b) for a, b in zip(ev["prop0"], ev["prop1"])]))
+    spec_avg = float(np.mean([a.elapsed_time(b) for a, b in zip(ev["prop1"], ev["spec1"])]))
+    n_good = int(bufs.n_good.item())
+
+    # ---- the dominant kernel (fused network evaluation), timed by itself at the same batch
+    qe = (torch.randn(n, w8.F, device=dev, dtype=torch.float64) /
+          torch.sqrt(torch.as_tensor(w8.pes.omega, device=dev))).float().contiguous()
+    Ve = torch.empty(n, device=dev)
+    ge = torch.empty(n, w8.F, device=dev)
+    He = torch.empty(n, w8.F, w8.F, device=dev)
+    for _ in range(3):
+        scivr.scivr_mlp_eval(pes, n, qe, Ve, ge, He, stream)
+    reps = 20
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        scivr.scivr_mlp_eval(pes, n, qe, Ve, ge, He, stream)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    eval_ms = k0.elapsed_time(k1) / reps
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hp0 = bufs.p0.cpu().pin_memory()
+        hq0 = bufs.q0.cpu().pin_memory()
+        hw = bufs.w.cpu().pin_memory()
+        hI = torch.empty(w8.n_E, dtype=torch.float64).pin_memory()
+        hng = torch.empty(1, dtype=torch.int64).pin_memory()
+        h2d = (hp0.numel() + hq0.numel() + hw.numel()) * 8
+        d2h = hI.numel() * 8 + 8
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            bufs.p0.copy_(hp0, non_blocking=True)
+            bufs.q0.copy_(hq0, non_blocking=True)
+            bufs.w.copy_(hw, non_blocking=True)
+            scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0, bufs.q0,
+                                  bufs.amp, K, bufs.good, precision=PRECISIONS["mixed"], stab_tol=MIXED_STAB_TOL,
+                                  stream=stream)
+            scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min, w8.E_max,
+                                 w8.n_E, bufs.I[0], bufs.n_good, ft_mode=ftm, stream=stream)
+            hI.copy_(bufs.I[0], non_blocking=True)
+            hng.copy_(bufs.n_good, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        tt = torch.tensor([a0.elapsed_time(a1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item()) / args.steps
+        e2e = {"value": world * n * w8.n_steps / (e2e_ms * 1e-3), "unit": "trajectory-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    peaks = measured_peaks()
+    pk = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+    achieved = mlp_flops_per_point(w8.F) * n / (eval_ms * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        wcpu = w8.with_(pes=su.surrogate_pes(w8, wl.init_mlp(w8.F, 256, 0, s_in=np.sqrt(w8.pes.omega),
+                                                               s_out=net.s_out)))
+        ns = min(args.cpu_sample, 16)   # about 1 s of one core per trajectory-thousand-steps
+        p0, q0, w = oracle.sample_initial(wcpu.gamma, wcpu.p_eq, wcpu.q_eq, ns, wcpu.seed)
+        c0 = time.perf_counter()
+        amp, good = oracle.propagate(wcpu.pes, wcpu.gamma, wcpu.p_eq, wcpu.q_eq, wcpu.dt, wcpu.n_steps, p0, q0,
+                                     wcpu.stab_tol, 0)
+        oracle.spectrum(amp[0], w, good, wcpu.n_steps, wcpu.dt, wcpu.E_min, wcpu.E_max, wcpu.n_E, 0)
+        c1 = time.perf_counter()
+        cpu = {"value": ns * wcpu.n_steps / (c1 - c0), "unit": "trajectory-steps/s",
+               "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"{ns} of {n} trajectories on the same surface type (Morse diagonal + a 9-256-256-256-1 "
+                         f"network of the same shape), all {w8.n_steps} steps and {w8.n_E} energies "
+                         f"({c1 - c0:.1f} s); rate is linear in trajectories"}
+    value = world * n * w8.n_steps / (ms_per_step * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 x bf16 -> f32 network + f32/f64 propagation" + ("" if ftm == 0 else f" + {args.ft} tensor FT"),
+        "data": "synthetic",
+        "config": {"workload": f"{w8.name} with a learned coupling residual: Morse diagonal + 9-256-256-256-1 "
+                               f"SiLU network (BF16 weights, FP32 accumulate), {n} trajectories, {w8.n_steps} "
+                               f"steps of {w8.dt} au, {w8.n_E} energies, Fourier step {args.ft}",
+                   "global_batch": world * n, "seed": "base 0 + rank",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); amplitudes "
+                         f"({n * K * 16 / 1e9:.2f} GB) exceed L2",
+                   "parallelism": f"replicas x{world}",
+                   "training": {"points": int(q.shape[0]), "source": "FP64 trajectories of the analytic "
+                                "surface, every 20 steps, |sqrt(omega) q| <= 6", "data_s": t_data,
+                                "steps": res.steps, "batch": 16384, "train_s": res.seconds,
+                                "loss_first": res.losses[0], "loss_last": res.losses[-1],
+                                "held_out_rel_error": held},
+                   "accuracy": accuracy},
+        "spectra_per_s": world / (ms_per_step * 1e-3),
+        "propagate_ms": prop_avg, "spectrum_ms": spec_avg, "n_good": n_good,
+        "network_eval_ms": eval_ms,
+        "roofline": {"kernel": "k_mlp_fused<9> (scivr_mlp_eval at the propagation batch; 3 launches per step)",
+                     "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                     "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained of measured"
+                                    if "bf16_tflops_sustained" in peaks else "fallback 1700 TFLOP/s sustained",
+                     "note": f"{mlp_flops_per_point(w8.F):.3g} algorithmic flop per point (value, gradient, "
+                             f"Hessian); tile padding and the 128-row reverse GEMMs are not counted"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="f6", choices=["f3", "f6", "f9", "batch"])
+    ap.add_argument("--workload", default="f6", choices=["f3", "f6", "f9", "batch", "f9mlp"])
+    ap.add_argument("--train-epochs", type=int, default=12, help="training epochs of --workload f9mlp")
+    ap.add_argument("--check-traj", type=int, default=2048,
+                    help="trajectories of the --workload f9mlp accuracy check")
     ap.add_argument("--n-mol", type=int, default=48, help="molecules in --workload batch")
     ap.add_argument("--cpu-sample", type=int, default=768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -353,6 +620,8 @@ def main(argv=None):
         return reference_arm(args)
     if args.workload == "batch":
         return batch_arm(args)
+    if args.workload == "f9mlp":
+        return surrogate_arm(args)
 
     import torch
     import torch.distributed as dist

@@ -304,3 +304,29 @@ def batch_molecules(n_mol: int = 48, seed: int = 0, Fs=(3, 6, 9, 12, 15, 24),
 def standard_normals(seed: int, n_traj: int, F: int) -> np.ndarray:
     """Plain numpy standard normals [2F, n_traj] for tests that feed explicit samples."""
     return np.random.default_rng(seed).standard_normal((2 * F, n_traj))
+
+
+def spectrum_peaks(E, I, rel=0.01):
+    """Peak positions of a spectrum on a grid: local maxima of at least rel * max(I),
+    each refined by the parabola through it and its two neighbours."""
+    E = np.asarray(E, dtype=np.float64)
+    I = np.asarray(I, dtype=np.float64)
+    if I.size < 3 or not np.isfinite(I).all():
+        return np.zeros(0)
+    thr = rel * I.max()
+    k = np.flatnonzero((I[1:-1] >= thr) & (I[1:-1] > I[:-2]) & (I[1:-1] >= I[2:])) + 1
+    y0, y1, y2 = I[k - 1], I[k], I[k + 1]
+    den = y0 - 2.0 * y1 + y2
+    off = np.where(den != 0.0, 0.5 * (y0 - y2) / np.where(den != 0.0, den, 1.0), 0.0)
+    return E[k] + off * (E[1] - E[0])
+
+
+def peak_shift(ref, got):
+    """Largest distance from a reference peak to the nearest peak of the other spectrum."""
+    ref = np.asarray(ref)
+    got = np.asarray(got)
+    if ref.size == 0:
+        return 0.0
+    if got.size == 0:
+        return float("inf")
+    return float(np.max(np.min(np.abs(got[None, :] - ref[:, None]), axis=1)))
