@@ -76,14 +76,16 @@ int scivr_pes_set_mlp(scivr_pes pes, const scivr_mlp_desc *m);
 
 /* V_mlp, its gradient and Hessian (with respect to q) for n points.
  * q: device [n][F] FP32.  V: device [n]; g: device [n][F]; H: device
- * [n][F][F] (symmetric) -- all FP32.  Layer 1 runs on the CUDA cores; the
- * 256 x 256 layers run as tcgen05 GEMMs with BF16 operands and FP32
- * accumulation, carrying the F input-Jacobian directions as extra rows next
- * to each point (forward mode); one reverse pass over the point rows gives
- * the gradient, and the Hessian is sum_l J_l^T diag(abar_l silu''(z_l)) J_l.
- * Allocates scratch with cudaMallocAsync on `stream` (about
- * 3 (F + 1) n kB).  Errors: SCIVR_EINVAL (no residual attached, n < 1, NULL
- * pointers), SCIVR_EUNSUPPORTED (F > 9), SCIVR_ENOMEM, SCIVR_ECUDA. */
+ * [n][F][F] (symmetric), or NULL for value and gradient only -- all FP32.
+ * Layer 1 runs on the CUDA cores; the 256 x 256 layers run as tcgen05 GEMMs
+ * with BF16 operands and FP32 accumulation.  With H, one persistent kernel
+ * carries the F input-Jacobian directions as extra rows next to each point
+ * (forward mode), runs the reverse pass on the point rows, and forms the
+ * Hessian sum_l J_l^T diag(abar_l silu''(z_l)) J_l, all on chip.  Without H the
+ * unfused kernels stage their operands in scratch allocated with
+ * cudaMallocAsync on `stream` (about 3.5 n kB).  Errors: SCIVR_EINVAL (no
+ * residual attached, n < 1, NULL q/V/g), SCIVR_EUNSUPPORTED (F > 9),
+ * SCIVR_ENOMEM, SCIVR_ECUDA. */
 int scivr_mlp_eval(scivr_pes pes, int64_t n, const float *q, float *V, float *g, float *H, void *stream);
 
 /* Copy the current parameter vector out to / in from device memory

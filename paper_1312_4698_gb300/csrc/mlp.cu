@@ -12,9 +12,10 @@
 // pass (point rows only) gives abar_l = dy/da_l; then
 //   grad V = s_out s_in * W1^T (abar_1 silu'(z1)),
 //   Hess V = s_out diag(s_in) [sum_l J_l^T diag(abar_l silu''(z_l)) J_l] diag(s_in).
-// A point's 1 + F rows sit in one 128-row tile (floor(128 / (F+1)) points per
-// tile), so per-point elementwise steps never cross tiles.  Without the
-// Hessian a point has a single row.
+// With the Hessian, k_mlp_fused keeps a tile of 12 points x (1 + F) rows on
+// chip from input to outputs.  Without it (the training pass and value +
+// gradient requests) a point has a single row and the unfused kernels below
+// stage their operands in HBM.
 //
 // Training objective L = (1/n) sum_j alpha (V_j - Vref_j)^2 + beta |g_j - gref_j|^2.
 // With e_j = 2 alpha (V_j - Vref_j) / n and u_j = 2 beta (g_j - gref_j) / n held
@@ -340,82 +341,32 @@ __global__ void k_backward_act(MlpDev m, int64_t n, const float *__restrict__ Ab
     put8<BM>(Dn, KT_H, b, ch * 8, v);
 }
 
-// Gradient (and with HESS the Hessian) of one point per warp.
-template <int F, bool HESS>
-__global__ void k_grad_hess(MlpDev m, int64_t n, const float *__restrict__ Z1, const float *__restrict__ C2,
-                            const float *__restrict__ C3, const float *__restrict__ Abar2,
-                            const float *__restrict__ Abar1, float *__restrict__ g, float *__restrict__ Hout)
+// Gradient of one point per warp (value-only rows: grad V = s_out s_in W1^T (abar1 silu'(z1))).
+template <int F>
+__global__ void k_grad(MlpDev m, int64_t n, const float *__restrict__ Z1, const float *__restrict__ Abar1,
+                       float *__restrict__ g)
 {
     const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= n) return;
-    const int64_t prow = point_row(m, b);
-    constexpr int NE = HESS ? F * (F + 1) / 2 : 1;
     float gacc[F];
-    float hacc[NE];
 #pragma unroll
     for (int k = 0; k < F; ++k) gacc[k] = 0.0f;
-#pragma unroll
-    for (int e = 0; e < NE; ++e) hacc[e] = 0.0f;
     for (int j = 0; j < HW / 32; ++j) {
         const int i = lane + 32 * j;
         float f, f1, f2;
         silu3(Z1[b * HW + i], f, f1, f2);
-        const float ab1 = Abar1[b * HW + i];
-        const float d1 = ab1 * f1;
-        float J1[F];
+        const float d1 = Abar1[b * HW + i] * f1;
 #pragma unroll
-        for (int k = 0; k < F; ++k) {
-            J1[k] = m.W1[i * F + k];
-            gacc[k] = fmaf(J1[k], d1, gacc[k]);
-        }
-        if constexpr (HESS) {
-            const float c1 = ab1 * f2;
-            float s2f, s21, s22;
-            silu3(C2[prow * HW + i] + m.b2[i], s2f, s21, s22);
-            const float c2 = Abar2[b * HW + i] * s22;
-            float s3f, s31, s32;
-            silu3(C3[prow * HW + i] + m.b3[i], s3f, s31, s32);
-            const float c3 = m.w4[i] * s32;
-            float J2[F], J3[F];
-#pragma unroll
-            for (int k = 0; k < F; ++k) {
-                J2[k] = C2[(prow + 1 + k) * HW + i];
-                J3[k] = C3[(prow + 1 + k) * HW + i];
-            }
-            int e = 0;
-#pragma unroll
-            for (int k = 0; k < F; ++k)
-#pragma unroll
-                for (int kk = k; kk < F; ++kk, ++e)
-                    hacc[e] = fmaf(c1 * J1[k], J1[kk], fmaf(c2 * J2[k], J2[kk], fmaf(c3 * J3[k], J3[kk], hacc[e])));
-        }
+        for (int k = 0; k < F; ++k) gacc[k] = fmaf(m.W1[i * F + k], d1, gacc[k]);
     }
 #pragma unroll
     for (int k = 0; k < F; ++k)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) gacc[k] += __shfl_xor_sync(0xffffffffu, gacc[k], off);
-    if constexpr (HESS) {
-#pragma unroll
-        for (int e = 0; e < NE; ++e)
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) hacc[e] += __shfl_xor_sync(0xffffffffu, hacc[e], off);
-    }
-    if (lane == 0) {
-        if constexpr (HESS) {
-            int e = 0;
-#pragma unroll
-            for (int k = 0; k < F; ++k)
-#pragma unroll
-                for (int kk = k; kk < F; ++kk, ++e) {
-                    const float h = m.s_out * m.s_in[k] * m.s_in[kk] * hacc[e];
-                    Hout[(b * F + k) * F + kk] = h;
-                    Hout[(b * F + kk) * F + k] = h;
-                }
-        }
+    if (lane == 0)
 #pragma unroll
         for (int k = 0; k < F; ++k) g[b * F + k] = m.s_out * m.s_in[k] * gacc[k];
-    }
 }
 
 // ---------------------------------------------------------------- training
@@ -890,6 +841,7 @@ __global__ void __launch_bounds__(320, 1)
             }
             if (c < SPT) ys[c] = *m.b4;
             named_sync();
+#pragma unroll 3
             for (int idx = c; idx < SPT * HW; idx += FU_NC) {
                 const int s = idx >> 8, o = idx & (HW - 1);
                 float z = b1s[o];
@@ -923,13 +875,18 @@ __global__ void __launch_bounds__(320, 1)
             // ---- layer 2: TMEM[0:256) holds z2 - b2 (value rows) and J2 (tangent rows)
             if (!wait_acc()) break;
 #pragma unroll 1
-            for (int j = 0; j < 4; ++j) {
-                float v[32];
+            for (int j = 0; j < 4; j += 2) {
+                float v[32], u[32];
                 tmem_ld32(lane_base + j * 32, v);
+                tmem_ld32(lane_base + (j + 1) * 32, u);
                 tmem_wait_ld();
-                if (prim) put_f32x32(zb + rowp + (hf * 4 + j) * 32, v);
+                if (prim) {
+                    put_f32x32(zb + rowp + (hf * 4 + j) * 32, v);
+                    put_f32x32(zb + rowp + (hf * 4 + j + 1) * 32, u);
+                }
             }
             named_sync();
+#pragma unroll 3
             for (int idx = c; idx < SPT * HW; idx += FU_NC) {
                 const int s = idx >> 8, o = idx & (HW - 1);
                 const float z = zb[s * PS + o] + b2s[o];
@@ -943,14 +900,18 @@ __global__ void __launch_bounds__(320, 1)
             {
                 const float *src = (prim ? zb : pb) + rowp;
 #pragma unroll 1
-                for (int j = 0; j < 4; ++j) {
-                    const int ch = hf * 4 + j;
-                    float v[32];
+                for (int j = 0; j < 4; j += 2) {
+                    float v[32], u[32];
                     tmem_ld32(lane_base + j * 32, v);
+                    tmem_ld32(lane_base + (j + 1) * 32, u);
                     tmem_wait_ld();
+                    const int ch = hf * 4 + j;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = sv * src[ch * 32 + i] * fmaf(pv, 1.0f - v[i], v[i]);
                     put_row32(sA, r, ch, v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) u[i] = sv * src[ch * 32 + 32 + i] * fmaf(pv, 1.0f - u[i], u[i]);
+                    put_row32(sA, r, ch + 1, u);
                 }
             }
             release_a();
@@ -958,13 +919,18 @@ __global__ void __launch_bounds__(320, 1)
             // ---- layer 3: TMEM[256:512) holds z3 - b3 and J3; V, delta3 and the layer-3 Hessian term
             if (!wait_acc()) break;
 #pragma unroll 1
-            for (int j = 0; j < 4; ++j) {
-                float v[32];
+            for (int j = 0; j < 4; j += 2) {
+                float v[32], u[32];
                 tmem_ld32(lane_base + 256 + j * 32, v);
+                tmem_ld32(lane_base + 256 + (j + 1) * 32, u);
                 tmem_wait_ld();
-                if (prim) put_f32x32(zb + rowp + (hf * 4 + j) * 32, v);
+                if (prim) {
+                    put_f32x32(zb + rowp + (hf * 4 + j) * 32, v);
+                    put_f32x32(zb + rowp + (hf * 4 + j + 1) * 32, u);
+                }
             }
             named_sync();
+#pragma unroll 3
             for (int idx = c; idx < SPT * HW; idx += FU_NC) {   // the 256 entries of one pass share a point
                 const int s = idx >> 8, o = idx & (HW - 1);
                 float f, f1, f2;
@@ -1000,13 +966,18 @@ __global__ void __launch_bounds__(320, 1)
             // ---- reverse through layer 3: TMEM[256:512) = abar2 (value rows); J2 in TMEM[0:256)
             if (!wait_acc()) break;
 #pragma unroll 1
-            for (int j = 0; j < 4; ++j) {
-                float v[32];
+            for (int j = 0; j < 4; j += 2) {
+                float v[32], u[32];
                 tmem_ld32(lane_base + 256 + j * 32, v);
+                tmem_ld32(lane_base + 256 + (j + 1) * 32, u);
                 tmem_wait_ld();
-                if (prim) put_f32x32(pb + rowp + (hf * 4 + j) * 32, v);
+                if (prim) {
+                    put_f32x32(pb + rowp + (hf * 4 + j) * 32, v);
+                    put_f32x32(pb + rowp + (hf * 4 + j + 1) * 32, u);
+                }
             }
             named_sync();
+#pragma unroll 3
             for (int idx = c; idx < SPT * HW; idx += FU_NC) {
                 const int s = idx >> 8, o = idx & (HW - 1);
                 float f, f1, f2;
@@ -1037,14 +1008,19 @@ __global__ void __launch_bounds__(320, 1)
             // ---- reverse through layer 2: TMEM[256:512) = abar1; grad V and the layer-1 term
             if (!wait_acc()) break;
 #pragma unroll 1
-            for (int j = 0; j < 4; ++j) {
-                float v[32];
+            for (int j = 0; j < 4; j += 2) {
+                float v[32], u[32];
                 tmem_ld32(lane_base + 256 + j * 32, v);
+                tmem_ld32(lane_base + 256 + (j + 1) * 32, u);
                 tmem_wait_ld();
-                if (prim) put_f32x32(pb + rowp + (hf * 4 + j) * 32, v);
+                if (prim) {
+                    put_f32x32(pb + rowp + (hf * 4 + j) * 32, v);
+                    put_f32x32(pb + rowp + (hf * 4 + j + 1) * 32, u);
+                }
             }
             tc_fence_before();
             named_sync();
+#pragma unroll 3
             for (int idx = c; idx < SPT * HW; idx += FU_NC) {
                 const int s = idx >> 8, o = idx & (HW - 1);
                 float f, f1, f2;
@@ -1242,11 +1218,13 @@ inline void gemm_rows(const uint8_t *A, const uint8_t *B, float *C, int64_t rows
     k_gemm<<<dim3(1, (unsigned)(rows / BM), 1), 128, GEMM_SMEM, s>>>(A, B, KT_H, KT_H, C, HW, rows, 0);
 }
 
-template <int F, bool HESS>
-cudaError_t eval_F(const MlpWeightsDev &w, int64_t n, const float *q, float *V, float *g, float *H, uint8_t *scr,
+// V and grad V (no Hessian): one row per point through the unfused kernels
+// (layer 1, two GEMMs with activation, output, two reverse GEMMs, gradient).
+template <int F>
+cudaError_t eval_F(const MlpWeightsDev &w, int64_t n, const float *q, float *V, float *g, uint8_t *scr,
                    cudaStream_t s, int *n_launch)
 {
-    const EvalLayout L = eval_layout(F, n, HESS);
+    const EvalLayout L = eval_layout(F, n, false);
     const MlpDev m = make_dev(w, F, L.R);
     uint8_t *X2 = scr + L.X2, *X3 = scr + L.X3, *D3 = scr + L.D3, *D2 = scr + L.D2;
     float *Z1 = reinterpret_cast<float *>(scr + L.Z1), *C2 = reinterpret_cast<float *>(scr + L.C2);
@@ -1262,7 +1240,7 @@ cudaError_t eval_F(const MlpWeightsDev &w, int64_t n, const float *q, float *V, 
     const int64_t nbk = L.n_pad * (HW / 8);
     k_backward_act<<<(unsigned)((nbk + 255) / 256), 256, 0, s>>>(m, n, Ab2, C2, m.b2, D2);
     gemm_rows(D2, m.W2Tt, Ab1, L.n_pad, s);
-    k_grad_hess<F, HESS><<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(m, n, Z1, C2, C3, Ab2, Ab1, g, H);
+    k_grad<F><<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(m, n, Z1, Ab1, g);
     *n_launch = 9;
     return cudaGetLastError();
 }
@@ -1292,7 +1270,7 @@ cudaError_t loss_grad_F(const MlpWeightsDev &w, int64_t n, const float *q, const
     auto fp = [&](size_t off) { return reinterpret_cast<float *>(scr + off); };
     float *V1 = fp(L.V1), *g1 = fp(L.g1);
     int nl = 0;
-    cudaError_t e = eval_F<F, false>(w, n, q, V1, g1, nullptr, scr + L.eval, s, &nl);
+    cudaError_t e = eval_F<F>(w, n, q, V1, g1, scr + L.eval, s, &nl);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(loss, 0, sizeof(float), s);
     if (e != cudaSuccess) return e;
@@ -1341,7 +1319,7 @@ cudaError_t mlp_eval(const MlpWeightsDev &w, int F, int64_t n, const float *q, f
 #define SCIVR_M(FF)                                                                         \
     case FF:                                                                                \
         return H ? mlp::eval_fused_F<FF>(w, n, q, V, g, H, s, n_launch)                     \
-                 : mlp::eval_F<FF, false>(w, n, q, V, g, H, scr, s, n_launch);
+                 : mlp::eval_F<FF>(w, n, q, V, g, scr, s, n_launch);
     SCIVR_M(1) SCIVR_M(2) SCIVR_M(3) SCIVR_M(4) SCIVR_M(5) SCIVR_M(6) SCIVR_M(7) SCIVR_M(8) SCIVR_M(9)
 #undef SCIVR_M
     default: *n_launch = 0; return cudaErrorInvalidValue;

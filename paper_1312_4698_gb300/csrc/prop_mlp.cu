@@ -50,41 +50,37 @@ __device__ __forceinline__ void record(const PropLaunch &L, int64_t j, int step,
     }
 }
 
-// Drift of length td for (q, S) and M_q += td M_p, all columns.
+// Drift of (q, S) by td (FP64).
 template <int F>
-__device__ __forceinline__ void drift(State &st, int64_t j, int64_t n, double td, float tdf, double (&p)[F],
-                                      double (&q)[F], double &S)
+__device__ __forceinline__ void drift_qs(double td, const double (&p)[F], double (&q)[F], double &S)
 {
-    constexpr int N2 = 2 * F;
     double kin = 0.0;
 #pragma unroll
     for (int a = 0; a < F; ++a) kin = fma(0.5 * p[a], p[a], kin);
     S = fma(td, kin, S);
 #pragma unroll
     for (int a = 0; a < F; ++a) q[a] = fma(td, p[a], q[a]);
-#pragma unroll 1
-    for (int c = 0; c < N2; ++c) {
-#pragma unroll
-        for (int a = 0; a < F; ++a) {
-            float *mq = st.M + ((int64_t)(F + a) * N2 + c) * n + j;
-            *mq = fmaf(tdf, st.M[((int64_t)a * N2 + c) * n + j], *mq);
-        }
-    }
 }
 
 // KIND 0: set-up and the first drift; 1: a kick and a drift (stage = 1, 2);
 // 3: the last kick and drift of a step, the per-step diagnostics, and the next
 // step's first drift.  COUPLED: the analytic part has coupling terms (else it
-// is the separable diagonal alone and its Hessian is diagonal).
+// is the separable diagonal alone and its Hessian is diagonal).  The kick and
+// the drift update M in one pass over its columns (M_p -= tk H M_q, then
+// M_q += td M_p); the final stage also copies M into the work array of its LU.
 template <int F, int KIND, bool COUPLED>
-__global__ void __launch_bounds__(KIND == 3 ? 64 : 128) k_mlp_stage(const PropLaunch L, State st, int stage)
+__global__ void __launch_bounds__(KIND == 3 ? 64 : 128, KIND == 3 ? 2 : 3) k_mlp_stage(const PropLaunch L, State st, int stage)
 {
     constexpr int N2 = 2 * F;
+    constexpr int NT = 64;                    // threads per block of the final stage
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n = L.n_traj;
     const PropArgs &A = L.args;
-    if (stage == 1 && j == 0) *st.step += 1;   // read by stage 3 of this step (later in stream order)
+    if (KIND == 1 && stage == 1 && j == 0) *st.step += 1;   // read by stage 3 of this step (later in stream order)
     if (j >= n) return;
+    float *Mj = st.M + j;                     // element (r, c) at Mj[(r 2F + c) n]
+    extern __shared__ __align__(16) uint8_t fin_smem[];
+    float *W = reinterpret_cast<float *>(fin_smem) + threadIdx.x;   // final stage: (r, c) at W[(r 2F + c) NT]
     double p[F], q[F], S;
     if (KIND == 0) {
 #pragma unroll
@@ -93,13 +89,21 @@ __global__ void __launch_bounds__(KIND == 3 ? 64 : 128) k_mlp_stage(const PropLa
             q[a] = L.q0[a * n + j];
         }
         S = 0.0;
-        for (int r = 0; r < N2; ++r)
-            for (int c = 0; c < N2; ++c) st.M[((int64_t)r * N2 + c) * n + j] = r == c ? 1.0f : 0.0f;
         st.theta[j] = 0.0;
         st.arg_old[j] = 0.0;
         st.stab[j] = 0.0;
         L.good[j] = 1;
         record<F>(L, j, 0, p, q, 0.0, 0.0);
+        const float td = A.tdrift_f[0];
+        for (int c = 0; c < N2; ++c)
+#pragma unroll
+            for (int a = 0; a < F; ++a) {
+                const float mp = a == c ? 1.0f : 0.0f;
+                const float mq = (F + a == c ? 1.0f : 0.0f) + td * mp;
+                Mj[((int64_t)a * N2 + c) * n] = mp;
+                Mj[((int64_t)(F + a) * N2 + c) * n] = mq;
+            }
+        drift_qs<F>(A.tdrift[0], p, q, S);
     } else {
 #pragma unroll
         for (int a = 0; a < F; ++a) {
@@ -150,52 +154,69 @@ __global__ void __launch_bounds__(KIND == 3 ? 64 : 128) k_mlp_stage(const PropLa
             }
         }
         S = fma(-tk, V, S);
+        const float td = A.tdrift_f[stage];
 #pragma unroll 1
         for (int c = 0; c < N2; ++c) {
-            float mq[F];
+            float mp[F], mq[F];
 #pragma unroll
-            for (int b = 0; b < F; ++b) mq[b] = st.M[((int64_t)(F + b) * N2 + c) * n + j];
+            for (int a = 0; a < F; ++a) {
+                mp[a] = Mj[((int64_t)a * N2 + c) * n];
+                mq[a] = Mj[((int64_t)(F + a) * N2 + c) * n];
+            }
 #pragma unroll
             for (int a = 0; a < F; ++a) {
                 float hm = 0.0f;
 #pragma unroll
                 for (int b = 0; b < F; ++b) hm = fmaf(Hk[a][b], mq[b], hm);
-                float *mp = st.M + ((int64_t)a * N2 + c) * n + j;
-                *mp -= hm;
+                mp[a] -= hm;
+            }
+#pragma unroll
+            for (int a = 0; a < F; ++a) {
+                mq[a] = fmaf(td, mp[a], mq[a]);
+                Mj[((int64_t)a * N2 + c) * n] = mp[a];
+                Mj[((int64_t)(F + a) * N2 + c) * n] = mq[a];
+                if (KIND == 3) {
+                    W[(a * N2 + c) * NT] = mp[a];
+                    W[((F + a) * N2 + c) * NT] = mq[a];
+                }
             }
         }
+        drift_qs<F>(A.tdrift[stage], p, q, S);
     }
-    drift<F>(st, j, n, A.tdrift[stage], A.tdrift_f[stage], p, q, S);
     if (KIND == 3) {
         const int step = *st.step;
         bool good = L.good[j] != 0;
-        // stability |det(M)^2 - 1| (FP32 LU with partial pivoting).  The work
-        // matrices live in shared memory as [element][thread] (bank-conflict
-        // free); thread-local arrays of this size would spill past L1.
-        extern __shared__ __align__(16) uint8_t fin_smem[];
-        constexpr int NT = 64;   // threads per block of the final stage
-        const int tid = threadIdx.x;
-        float *W = reinterpret_cast<float *>(fin_smem) + tid;
-        auto w = [&](int r, int c) -> float & { return W[(r * N2 + c) * NT]; };
-        for (int r = 0; r < N2; ++r)
-            for (int c = 0; c < N2; ++c) w(r, c) = st.M[((int64_t)r * N2 + c) * n + j];
+        // stability |det(M)^2 - 1| (FP32 LU with partial pivoting) on the copy
+        // in shared memory, laid out [element][thread] (bank-conflict free)
+        // fully unrolled: every shared-memory offset is a compile-time constant
+        // relative to the row pointers, and the pivot row sits in registers
         float det = 1.0f;
+#pragma unroll
         for (int k = 0; k < N2; ++k) {
             int piv = k;
-            float best = fabsf(w(k, k));
-            for (int i = k + 1; i < N2; ++i)
-                if (fabsf(w(i, k)) > best) { best = fabsf(w(i, k)); piv = i; }
+            float best = fabsf(W[(k * N2 + k) * NT]);
+#pragma unroll 1
+            for (int i = k + 1; i < N2; ++i) {
+                const float v = fabsf(W[(i * N2 + k) * NT]);
+                if (v > best) { best = v; piv = i; }
+            }
+            float rkv[N2];
+            float *rp = W + piv * N2 * NT;
+#pragma unroll
+            for (int c = k; c < N2; ++c) rkv[c] = rp[c * NT];
             if (piv != k) {
-                for (int c = k; c < N2; ++c) { const float t = w(k, c); w(k, c) = w(piv, c); w(piv, c) = t; }
+#pragma unroll
+                for (int c = k; c < N2; ++c) rp[c * NT] = W[(k * N2 + c) * NT];
                 det = -det;
             }
-            const float akk = w(k, k);
-            det *= akk;
-            const float inv = 1.0f / akk;
+            det *= rkv[k];
+            const float inv = 1.0f / rkv[k];
+#pragma unroll 1
             for (int i = k + 1; i < N2; ++i) {
-                const float l = w(i, k) * inv;
-#pragma unroll 6
-                for (int c = k + 1; c < N2; ++c) w(i, c) = fmaf(-l, w(k, c), w(i, c));
+                float *ri = W + i * N2 * NT;
+                const float l = ri[k * NT] * inv;
+#pragma unroll
+                for (int c = k + 1; c < N2; ++c) ri[c * NT] = fmaf(-l, rkv[c], ri[c * NT]);
             }
         }
         const float dev = isfinite(det) ? fabsf(fmaf(det, det, -1.0f)) : __int_as_float(0x7f800000);
@@ -203,45 +224,53 @@ __global__ void __launch_bounds__(KIND == 3 ? 64 : 128) k_mlp_stage(const PropLa
         st.stab[j] = stab;
         if (dev > A.stab_tol_f) good = false;
         // Herman-Kluk prefactor determinant (FP64, complex LU with partial
-        // pivoting) in the same shared memory, as [element][re/im][thread]
-        double *Z = reinterpret_cast<double *>(fin_smem) + tid;
-        auto zr = [&](int a, int b) -> double & { return Z[((a * F + b) * 2) * NT]; };
-        auto zi = [&](int a, int b) -> double & { return Z[((a * F + b) * 2 + 1) * NT]; };
+        // pivoting) in the same shared memory: (a, b) re at Z[(2 (a F + b)) NT], im at + NT
+        double *Z = reinterpret_cast<double *>(fin_smem) + threadIdx.x;
         for (int a = 0; a < F; ++a)
             for (int b = 0; b < F; ++b) {
-                const double mqq = st.M[((int64_t)(F + a) * N2 + F + b) * n + j];
-                const double mpp = st.M[((int64_t)a * N2 + b) * n + j];
-                const double mqp = st.M[((int64_t)(F + a) * N2 + b) * n + j];
-                const double mpq = st.M[((int64_t)a * N2 + F + b) * n + j];
-                zr(a, b) = 0.5 * fma(A.rg[a] * A.irg[b], mqq, A.rg[b] * A.irg[a] * mpp);
-                zi(a, b) = 0.5 * fma(-A.rg[a] * A.rg[b], mqp, A.irg[a] * A.irg[b] * mpq);
+                const float mqq = Mj[((int64_t)(F + a) * N2 + F + b) * n];
+                const float mpp = Mj[((int64_t)a * N2 + b) * n];
+                const float mqp = Mj[((int64_t)(F + a) * N2 + b) * n];
+                const float mpq = Mj[((int64_t)a * N2 + F + b) * n];
+                Z[(2 * (a * F + b)) * NT] = 0.5 * fma(A.rg[a] * A.irg[b], (double)mqq, A.rg[b] * A.irg[a] * (double)mpp);
+                Z[(2 * (a * F + b) + 1) * NT] = 0.5 * fma(-A.rg[a] * A.rg[b], (double)mqp, A.irg[a] * A.irg[b] * (double)mpq);
             }
         tpt::cplx dA = {1.0, 0.0};
+#pragma unroll
         for (int k = 0; k < F; ++k) {
             int piv = k;
-            double best = zr(k, k) * zr(k, k) + zi(k, k) * zi(k, k);
+            double best = Z[(2 * (k * F + k)) * NT] * Z[(2 * (k * F + k)) * NT] +
+                          Z[(2 * (k * F + k) + 1) * NT] * Z[(2 * (k * F + k) + 1) * NT];
+#pragma unroll 1
             for (int i = k + 1; i < F; ++i) {
-                const double v = zr(i, k) * zr(i, k) + zi(i, k) * zi(i, k);
+                const double vr = Z[(2 * (i * F + k)) * NT], vi = Z[(2 * (i * F + k) + 1) * NT];
+                const double v = vr * vr + vi * vi;
                 if (v > best) { best = v; piv = i; }
             }
+            tpt::cplx rkv[F];
+            double *rp = Z + 2 * piv * F * NT;
+#pragma unroll
+            for (int c = k; c < F; ++c) rkv[c] = {rp[2 * c * NT], rp[(2 * c + 1) * NT]};
             if (piv != k) {
+#pragma unroll
                 for (int c = k; c < F; ++c) {
-                    const double tr = zr(k, c), ti = zi(k, c);
-                    zr(k, c) = zr(piv, c); zi(k, c) = zi(piv, c);
-                    zr(piv, c) = tr; zi(piv, c) = ti;
+                    rp[2 * c * NT] = Z[(2 * (k * F + c)) * NT];
+                    rp[(2 * c + 1) * NT] = Z[(2 * (k * F + c) + 1) * NT];
                 }
                 dA.re = -dA.re; dA.im = -dA.im;
             }
-            const tpt::cplx akk = {zr(k, k), zi(k, k)};
-            dA = tpt::cmul(dA, akk);
-            const double rr = 1.0 / (akk.re * akk.re + akk.im * akk.im);
-            const tpt::cplx inv = {akk.re * rr, -akk.im * rr};
+            dA = tpt::cmul(dA, rkv[k]);
+            const double rr = 1.0 / (rkv[k].re * rkv[k].re + rkv[k].im * rkv[k].im);
+            const tpt::cplx inv = {rkv[k].re * rr, -rkv[k].im * rr};
+#pragma unroll 1
             for (int i = k + 1; i < F; ++i) {
-                const tpt::cplx l = tpt::cmul({zr(i, k), zi(i, k)}, inv);
+                double *ri = Z + 2 * i * F * NT;
+                const tpt::cplx l = tpt::cmul({ri[2 * k * NT], ri[(2 * k + 1) * NT]}, inv);
+#pragma unroll
                 for (int c = k + 1; c < F; ++c) {
-                    const tpt::cplx y = tpt::cfnma(l, {zr(k, c), zi(k, c)}, {zr(i, c), zi(i, c)});
-                    zr(i, c) = y.re;
-                    zi(i, c) = y.im;
+                    const tpt::cplx y = tpt::cfnma(l, rkv[c], {ri[2 * c * NT], ri[(2 * c + 1) * NT]});
+                    ri[2 * c * NT] = y.re;
+                    ri[(2 * c + 1) * NT] = y.im;
                 }
             }
         }
@@ -268,10 +297,19 @@ __global__ void __launch_bounds__(KIND == 3 ? 64 : 128) k_mlp_stage(const PropLa
             if (fo.detA) { fo.detA[2 * j] = dA.re; fo.detA[2 * j + 1] = dA.im; }
             if (fo.M)
                 for (int r = 0; r < N2; ++r)
-                    for (int c = 0; c < N2; ++c) fo.M[j * N2 * N2 + r * N2 + c] = st.M[((int64_t)r * N2 + c) * n + j];
+                    for (int c = 0; c < N2; ++c) fo.M[j * N2 * N2 + r * N2 + c] = Mj[((int64_t)r * N2 + c) * n];
             return;
         }
-        drift<F>(st, j, n, A.tdrift[0], A.tdrift_f[0], p, q, S);
+        // first drift of the next step
+        const float td0 = A.tdrift_f[0];
+#pragma unroll 1
+        for (int c = 0; c < N2; ++c)
+#pragma unroll
+            for (int a = 0; a < F; ++a) {
+                float *mq = Mj + ((int64_t)(F + a) * N2 + c) * n;
+                *mq = fmaf(td0, Mj[((int64_t)a * N2 + c) * n], *mq);
+            }
+        drift_qs<F>(A.tdrift[0], p, q, S);
     }
 #pragma unroll
     for (int a = 0; a < F; ++a) {
