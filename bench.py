@@ -43,7 +43,8 @@ FP64_PEAK_NOTE = ("GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table
                   "probe on this pool measured 1.252 TFLOP/s")
 # dram read+write bytes per launch from ncu captures (profiles/), keyed by (kernel, workload);
 # scaled to the full launch where the capture used fewer trajectories
-TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9, ("k_ft_tc2", "f6"): 7.98e9}
+TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9, ("k_ft_tc2", "f6"): 7.98e9,
+           ("k_mlp_fused", "f9mlp"): 0.914e6 * 8}
 
 
 def workload(name: str, seed: int):
@@ -576,7 +577,8 @@ def surrogate_arm(args):
         "network_eval_ms": eval_ms,
         "roofline": {"kernel": "k_mlp_fused<9> (scivr_mlp_eval at the propagation batch; 3 launches per step)",
                      "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                     "traffic": None,
+                     "traffic": TRAFFIC[("k_mlp_fused", "f9mlp")] if n == 65536 else None,
+                     "traffic_note": "ncu capture at 8192 points scaled by 8; outputs stay in L2",
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained of measured"
                                     if "bf16_tflops_sustained" in peaks else "fallback 1700 TFLOP/s sustained",
                      "note": f"{mlp_flops_per_point(w8.F):.3g} algorithmic flop per point (value, gradient, "

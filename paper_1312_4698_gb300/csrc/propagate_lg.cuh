@@ -81,6 +81,12 @@ template <typename Real, int F> __device__ __forceinline__ Real c_D(const CtaCon
 template <typename Real, int F> __device__ __forceinline__ Real c_a(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.af[i]; else return c.ad[i]; }
 template <typename Real, int F> __device__ __forceinline__ Real c_w2(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.w2f[i]; else return c.w2d[i]; }
 
+// Column of job j in row r of the per-job arrays: the F mode lanes of a group
+// store one job into F different rows, which a plain [row][job] layout puts
+// into a single shared-memory bank; XOR-ing the job with the row spreads them
+// over banks, and every row is still a permutation of the 32 jobs.
+__device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & 15); }
+
 template <int F, int G, typename Real>
 struct WarpShared {
     static constexpr int P = F * (F + 1) / 2;
@@ -90,8 +96,8 @@ struct WarpShared {
     Real qq[T][P];
     Real gc[T][P];
     Real H[T][F][F];
-    typename Vec2<Real>::T A[F * F][32];   // prefactor matrix per job, entry-major
-    double pj[F][32], qj[F][32];           // state per job (for the overlap)
+    typename Vec2<Real>::T A[F * F][32];   // prefactor matrix per job, entry-major (job column swizzled)
+    double pj[F][32], qj[F][32];           // state per job (for the overlap; job column swizzled)
     double Sj[32];                          // action per job
 };
 
@@ -366,12 +372,12 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         R2 v;
                         v.x = Real(0.5) * re;
                         v.y = Real(0.5) * im;
-                        sh.A[a * F + g][job] = v;
+                        sh.A[a * F + g][jswz(a * F + g, job)] = v;
                     }
                 }
                 if (g < F) {
-                    sh.pj[g][job] = p;
-                    sh.qj[g][job] = q;
+                    sh.pj[g][jswz(g, job)] = p;
+                    sh.qj[g][jswz(g, job)] = q;
                 }
                 // the step's action increment, summed over the group, joins the FP64 action
 #pragma unroll
@@ -399,7 +405,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             for (int a = 0; a < F; ++a)
 #pragma unroll
                 for (int b = 0; b < F; ++b) {
-                    const R2 v = sh.A[a * F + b][ln];
+                    const R2 v = sh.A[a * F + b][jswz(a * F + b, ln)];
                     Ar[a][b] = (double)v.x;
                     Ai[a][b] = (double)v.y;
                 }
@@ -468,7 +474,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 double re = 0.0, im = 0.0;
 #pragma unroll
                 for (int a = 0; a < F; ++a) {
-                    const double pa = sh.pj[a][ln], qa = sh.qj[a][ln];
+                    const double pa = sh.pj[a][jswz(a, ln)], qa = sh.qj[a][jswz(a, ln)];
                     const double dq = cc.q_eq[x][a] - qa, dp = cc.p_eq[x][a] - pa;
                     re = fma(-cc.qw[a] * dq, dq, re);
                     re = fma(-cc.pw[a] * dp, dp, re);
