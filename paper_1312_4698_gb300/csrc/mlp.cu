@@ -29,6 +29,7 @@
 // 2 n rows, so the activation kernels also write their output transposed
 // (hidden index as the tile row, the point row as k).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 
@@ -588,48 +589,58 @@ __global__ void k_adamw(float *__restrict__ theta, const float *__restrict__ gra
 // ---------------------------------------------------------------- fused evaluation
 // V, grad V and the Hessian with every intermediate on chip.  A persistent CTA
 // (one per SM: 512 TMEM columns, ~225 KB of shared memory) walks 128-row tiles
-// of 12 points x (1 + F) rows.  Per tile:
-//   layer 1 (CUDA cores) -> A tile X2 in shared memory
-//   GEMM X2 W2^T -> TMEM[0:256)     epilogue: X3 = [silu(z2); silu'(z2) J2] -> A tile
-//   GEMM X3 W3^T -> TMEM[256:512)   epilogue: V, delta3 -> A tile, Hessian term of layer 3
-//   GEMM D3 W3   -> TMEM[256:512)   epilogue: delta2 -> A tile, Hessian term of layer 2 (J2 still in TMEM[0:256))
-//   GEMM D2 W2   -> TMEM[256:512)   epilogue: grad V and the layer-1 Hessian term, outputs
-// Warp roles: warps 0-7 compute (tile row r = TMEM lane r is shared by warps
-// r/32 and r/32 + 4, which take the column halves [0,128) and [128,256)),
-// warp 8 streams the BF16 weight tiles (16 KB k-blocks through a 3-stage ring,
-// cp.async.bulk), warp 9 issues tcgen05.mma.  Elementwise work on the point
-// rows is spread over all 256 compute threads through shared memory; the row
-// loops are branch-free (each row picks its source and factor pointers once).
-// The J^T diag(c) J products pair the tangent rows of a point through a shared
-// exchange buffer, 32 columns at a time; direction d takes the partners
-// d, d+1, ..., d + floor(F/2) (mod F), which covers every unordered pair once.
+// of 12 points x (1 + F) rows.  Per tile, six tensor-core products:
+//   layer 1 (CUDA cores)            -> A tile X2
+//   X2 W2^T -> TMEM[0:256)             epilogue: X3 = [silu(z2); silu'(z2) J2] -> A tile
+//   X3 W3^T -> TMEM[256:512)           epilogue: V, c3 = w4 silu''(z3); Gram operands
+//   (c3 J3) J3^T -> TMEM[256:368)      block-diagonal Gram product: the layer-3 Hessian
+//                                      term of every point at once; epilogue: delta3 -> A tile
+//   D3 W3 -> TMEM[256:512)             epilogue: c2 = abar2 silu''(z2); Gram operands (J2 is
+//                                      still in TMEM[0:256) next to z2 - b2 of the value rows)
+//   (c2 J2) J2^T -> TMEM[256:368)      layer-2 Hessian term; epilogue: delta2 -> A tile
+//   D2 W2 -> TMEM[256:512)             epilogue: grad V and the layer-1 term W1^T diag(c1) W1
+// The four weight products stream BF16 weight tiles (16 KB k-blocks, 3-stage
+// ring, cp.async.bulk); the two Gram products take FP16 operands written by
+// the compute warps (c J rows into the A tile, the F tangent rows of every
+// point packed as the 12 F x 256 B operand).  Warp roles: warps 0-7 compute
+// (tile row r = TMEM lane r is shared by warps r/32 and r/32 + 4, which take
+// the column halves), warp 8 streams weights, warp 9 issues tcgen05.mma.
 constexpr int FU_STAGES = 3;
 constexpr int FU_NC = 256;                        // compute threads
 constexpr int FU_SPT = 12;                        // points per tile (F <= 9: 12 (F+1) <= 120 rows)
 constexpr int FU_PS = HW + 4;                     // padded row stride of the per-point buffers
-constexpr int FU_XS = 36;                         // row stride (floats) of the exchange buffer
 constexpr int FU_BUF = FU_SPT * FU_PS * 4;
-constexpr int FU_O_A = 0;                         // A tile: 8 k-blocks of 128 x 32 BF16
+constexpr int FU_NG = 112;                        // Gram B rows at most: 12 x 9 tangent rows, padded
+constexpr int FU_GBLK = FU_NG * BK * 2;           // one 32-k block of the Gram B operand
+constexpr int FU_SCS = 68;                        // row stride (floats) of the Gram read-out scratch
+constexpr int FU_O_A = 0;                         // A tile: 8 k-blocks of 128 x 32 (BF16 or FP16)
 constexpr int FU_O_B = FU_O_A + BM * HW * 2;      // weight ring
-constexpr int FU_O_Z1 = FU_O_B + FU_STAGES * TILE_B;
-constexpr int FU_O_Z2 = FU_O_Z1 + FU_BUF;
-constexpr int FU_O_P = FU_O_Z2 + FU_BUF;
+constexpr int FU_O_G = FU_O_B + FU_STAGES * TILE_B;   // Gram B operand, then the read-out scratch
+constexpr int FU_O_P = FU_O_G + KT_H * FU_GBLK;
 constexpr int FU_O_Q = FU_O_P + FU_BUF;
 constexpr int FU_O_ZB = FU_O_Q + FU_BUF;
-constexpr int FU_O_X = FU_O_ZB + FU_BUF;          // exchange rows [2][128][FU_XS]
-constexpr int FU_O_W1 = FU_O_X + 2 * BM * FU_XS * 4;  // W1 [256][F]
+constexpr int FU_O_W1 = FU_O_ZB + FU_BUF;             // W1 [256][F]
 constexpr int FU_O_PAR = FU_O_W1 + HW * kMaxF * 4;    // b1, b2, b3, w4 [256] each; s_in [16]; one
 constexpr int FU_O_XQ = FU_O_PAR + (4 * HW + 32) * 4; // x = s_in q [12][F]
 constexpr int FU_O_Y = FU_O_XQ + FU_SPT * kMaxF * 4;  // y per point
 constexpr int FU_SMEM = FU_O_Y + FU_SPT * 4;
-static_assert(FU_SMEM + 256 <= 227 * 1024, "fused evaluation exceeds shared memory");
+static_assert(FU_SMEM + 1024 <= 227 * 1024, "fused evaluation exceeds shared memory");
+static_assert(BM * FU_SCS * 4 <= KT_H * FU_GBLK, "Gram read-out scratch exceeds its region");
 
 template <int F> struct FuCfg {
     static constexpr int R = F + 1;
     static constexpr int NE = F * (F + 1) / 2;
-    static constexpr int NJ = F / 2 + 1;          // partners per direction
+    static constexpr int NJ = F / 2 + 1;                      // partners per direction
+    static constexpr int NG = (FU_SPT * F + 15) / 16 * 16;    // Gram N (multiple of 16)
     static_assert(FU_SPT * R <= BM, "points of a tile exceed 128 rows");
+    static_assert(NG <= FU_NG, "Gram operand exceeds its region");
 };
+
+// Instruction descriptor, kind::f16: FP16 x FP16 -> FP32, both operands K-major.
+constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 __device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -639,7 +650,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // silu and its first two derivatives (fast exponential and division: the
-// results feed BF16 operands)
+// results feed BF16/FP16 operands)
 __device__ __forceinline__ void silu3f(float z, float &f, float &f1, float &f2)
 {
     const float s = __fdividef(1.0f, 1.0f + __expf(-fmaxf(z, -80.0f)));
@@ -648,15 +659,25 @@ __device__ __forceinline__ void silu3f(float z, float &f, float &f1, float &f2)
     f2 = s * (1.0f - s) * (2.0f + z * (1.0f - 2.0f * s));
 }
 
-// Row r of the shared A tile, k = 32 ch .. 32 ch + 31.
-__device__ __forceinline__ void put_row32(uint8_t *sA, int r, int ch, const float (&v)[32])
+// Row r (of a canonical K-major operand whose 32-k blocks are blk bytes apart),
+// k = 32 ch .. 32 ch + 31, as BF16 or FP16.
+template <bool HALF>
+__device__ __forceinline__ void put_row32(uint8_t *base, int blk, int r, int ch, const float (&v)[32])
 {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        __nv_bfloat162 h[4];
+        uint32_t h[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[8 * j + 2 * i], v[8 * j + 2 * i + 1]);
-        *reinterpret_cast<uint4 *>(sA + ch * TILE_A + canon_off(r, 8 * j)) = *reinterpret_cast<const uint4 *>(h);
+        for (int i = 0; i < 4; ++i) {
+            if constexpr (HALF) {
+                const __half2 x = __floats2half2_rn(v[8 * j + 2 * i], v[8 * j + 2 * i + 1]);
+                h[i] = *reinterpret_cast<const uint32_t *>(&x);
+            } else {
+                const __nv_bfloat162 x = __floats2bfloat162_rn(v[8 * j + 2 * i], v[8 * j + 2 * i + 1]);
+                h[i] = *reinterpret_cast<const uint32_t *>(&x);
+            }
+        }
+        *reinterpret_cast<uint4 *>(base + ch * blk + canon_off(r, 8 * j)) = make_uint4(h[0], h[1], h[2], h[3]);
     }
 }
 
@@ -666,46 +687,22 @@ __device__ __forceinline__ void put_f32x32(float *dst, const float (&v)[32])
     for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
 }
 
-// hacc[j] += sum_i w[i] J_{(d + j) mod F}[i] over the 32 columns that the
-// tangent rows of this row's point left in ex.
-template <int F>
-__device__ __forceinline__ void pair_products(const float *ex, int row0, int d, const float (&w)[32],
-                                              float (&hacc)[FuCfg<F>::NJ])
-{
-#pragma unroll
-    for (int j = 0; j < FuCfg<F>::NJ; ++j) {
-        int k = d + j;
-        k = k >= F ? k - F : k;
-        const float *xr = ex + (row0 + 1 + k) * FU_XS;
-        float a0 = 0.0f, a1 = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 32; i += 8) {
-            const float4 x4 = *reinterpret_cast<const float4 *>(xr + i);
-            const float4 y4 = *reinterpret_cast<const float4 *>(xr + i + 4);
-            a0 = fmaf(w[i], x4.x, fmaf(w[i + 1], x4.y, fmaf(w[i + 2], x4.z, fmaf(w[i + 3], x4.w, a0))));
-            a1 = fmaf(w[i + 4], y4.x, fmaf(w[i + 5], y4.y, fmaf(w[i + 6], y4.z, fmaf(w[i + 7], y4.w, a1))));
-        }
-        hacc[j] += a0 + a1;
-    }
-}
-
 template <int F>
 __global__ void __launch_bounds__(320, 1)
     k_mlp_fused(MlpDev m, int64_t n, int n_tiles, const float *__restrict__ q, float *__restrict__ Vout,
                 float *__restrict__ gout, float *__restrict__ Hout)
 {
     using C = FuCfg<F>;
-    constexpr int R = C::R, NE = C::NE, NJ = C::NJ, SPT = FU_SPT, PS = FU_PS;
+    constexpr int R = C::R, NE = C::NE, NJ = C::NJ, NG = C::NG, SPT = FU_SPT, PS = FU_PS;
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *sm = smem_raw;
     uint8_t *sA = sm + FU_O_A;
     uint8_t *sB = sm + FU_O_B;
-    float *z1s = reinterpret_cast<float *>(sm + FU_O_Z1);    // z1
-    float *z2s = reinterpret_cast<float *>(sm + FU_O_Z2);    // z2
+    uint8_t *sG = sm + FU_O_G;
+    float *sc = reinterpret_cast<float *>(sm + FU_O_G);      // Gram read-out scratch [128][FU_SCS]
     float *pb = reinterpret_cast<float *>(sm + FU_O_P);      // silu'(z1), silu'(z2), abar2, abar1 -> d1
-    float *qb = reinterpret_cast<float *>(sm + FU_O_Q);      // c3, c2, c1
+    float *qb = reinterpret_cast<float *>(sm + FU_O_Q);      // c3, c2, c1, then the layer-1 Hessian terms
     float *zb = reinterpret_cast<float *>(sm + FU_O_ZB);     // value-row staging: a1, a2, delta3, delta2
-    float *exb = reinterpret_cast<float *>(sm + FU_O_X);
     float *w1s = reinterpret_cast<float *>(sm + FU_O_W1);
     float *b1s = reinterpret_cast<float *>(sm + FU_O_PAR);
     float *b2s = b1s + HW, *b3s = b2s + HW, *w4s = b3s + HW, *sins = w4s + HW, *one = sins + 16;
@@ -766,14 +763,15 @@ __global__ void __launch_bounds__(320, 1)
                 mbar_wait(&full_bar[k % FU_STAGES], (k / FU_STAGES) & 1, kWaitLimitCycles);
         }
     } else if (warp == 9) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer: per tile weight, weight, Gram, weight, Gram, weight
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, BN);
-            const uint32_t a0 = su32(sA), b0 = su32(sB);
+            constexpr uint32_t idesc_w = idesc_bf16(BM, BN);
+            constexpr uint32_t idesc_g = idesc_f16(BM, NG);
+            const uint32_t a0 = su32(sA), b0 = su32(sB), g0 = su32(sG);
             int kc = 0, ca = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x)
-                for (int gm = 0; gm < 4 && ok; ++gm) {
+                for (int op = 0; op < 6 && ok; ++op) {
                     if (!mbar_wait(&a_bar, ca & 1, kWaitLimitCycles) || *(volatile int *)&abort_flag) {
                         atomicExch(&abort_flag, 1);
                         ok = false;
@@ -781,20 +779,30 @@ __global__ void __launch_bounds__(320, 1)
                     }
                     ++ca;
                     tc_fence_after();
-                    const uint32_t d = tmem + (gm == 0 ? 0u : 256u);
-                    for (int kt = 0; kt < KT_H; ++kt, ++kc) {
-                        const int s = kc % FU_STAGES;
-                        if (!mbar_wait(&full_bar[s], (kc / FU_STAGES) & 1, kWaitLimitCycles)) {
-                            atomicExch(&abort_flag, 1);
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
+                    const uint32_t d = tmem + (op == 0 ? 0u : 256u);
+                    if (op == 2 || op == 4) {
+                        // Gram product: operands written by the compute warps
+#pragma unroll 1
+                        for (int kt = 0; kt < KT_H; ++kt)
 #pragma unroll
-                        for (int ks = 0; ks < BK / 16; ++ks)
-                            umma(d, sdesc(a0 + kt * TILE_A + ks * 2 * LBO), sdesc(b0 + s * TILE_B + ks * 2 * LBO),
-                                 idesc, (kt | ks) != 0);
-                        umma_commit(&empty_bar[s]);
+                            for (int ks = 0; ks < BK / 16; ++ks)
+                                umma(d, sdesc(a0 + kt * TILE_A + ks * 2 * LBO), sdesc(g0 + kt * FU_GBLK + ks * 2 * LBO),
+                                     idesc_g, (kt | ks) != 0);
+                    } else {
+                        for (int kt = 0; kt < KT_H; ++kt, ++kc) {
+                            const int s = kc % FU_STAGES;
+                            if (!mbar_wait(&full_bar[s], (kc / FU_STAGES) & 1, kWaitLimitCycles)) {
+                                atomicExch(&abort_flag, 1);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+#pragma unroll
+                            for (int ks = 0; ks < BK / 16; ++ks)
+                                umma(d, sdesc(a0 + kt * TILE_A + ks * 2 * LBO), sdesc(b0 + s * TILE_B + ks * 2 * LBO),
+                                     idesc_w, (kt | ks) != 0);
+                            umma_commit(&empty_bar[s]);
+                        }
                     }
                     umma_commit(&c_bar);   // also on abort: the compute warps are waiting on it
                 }
@@ -803,12 +811,17 @@ __global__ void __launch_bounds__(320, 1)
         // ---------------- compute warps
         const int c = threadIdx.x;            // 0..255
         const int hf = warp >> 2;             // column half
-        const int r = (warp & 3) * 32 + lane; // tile row = TMEM lane
+        const int qd = warp & 3;              // TMEM lane quadrant
+        const int r = qd * 32 + lane;         // tile row = TMEM lane
         const int sr = r / R, kr = r % R;     // point of the row; 0 = value row, k = direction k - 1
-        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + hf * 128;
-        float *ex = exb + hf * BM * FU_XS;
+        const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16);
+        const uint32_t col_half = hf * 128;
+        // Gram read-out window of quadrant qq: 64 columns from gwin(qq) cover the blocks of
+        // every point with a row in it (checked for F = 1..9)
+        auto gwin = [](int qq) { return ((qq * 32) / R * F) / 32 * 32; };
+        const int gbase = gwin(qd);
         int cc = 0;
-        // wait for the accumulator of the current GEMM; uniform verdict over the compute threads
+        // wait for the accumulator of the current product; uniform verdict over the compute threads
         auto wait_acc = [&]() -> bool {
             if (!mbar_wait(&c_bar, cc & 1, kWaitLimitCycles)) atomicExch(&abort_flag, 1);
             ++cc;
@@ -826,12 +839,39 @@ __global__ void __launch_bounds__(320, 1)
             const bool valid = sr < SPT && p0 + sr < n;
             const bool prim = valid && kr == 0, tang = valid && kr > 0;
             const int d = tang ? kr - 1 : 0;          // this row's direction
-            const float sv = valid ? 1.0f : 0.0f, pv = prim ? 1.0f : 0.0f;
+            const float sv = valid ? 1.0f : 0.0f, pv = prim ? 1.0f : 0.0f, tv = tang ? 1.0f : 0.0f;
             const int rowp = (valid ? sr : 0) * PS;   // this row's point in the per-point buffers
-            const int row0 = (valid ? sr : 0) * R;    // the point's first tile row
+            const int gb = (valid ? sr : 0) * F + d;  // this tangent row in the Gram B operand
             float hacc[NJ];
 #pragma unroll
             for (int j = 0; j < NJ; ++j) hacc[j] = 0.0f;
+
+            // the read-out of a Gram product (TMEM[256:256+NG)) into hacc, symmetrised
+            auto gram_readout = [&]() {
+                if (hf == 0) {   // warp-uniform: the first column half reads, the second waits
+                    float va[32], vb[32];
+                    tmem_ld32(lane_base + 256 + gbase, va);
+                    tmem_ld32(lane_base + 256 + gbase + 32, vb);
+                    tmem_wait_ld();
+                    put_f32x32(sc + r * FU_SCS, va);
+                    put_f32x32(sc + r * FU_SCS + 32, vb);
+                }
+                tc_fence_before();
+                named_sync();
+                if (tang && hf == 0) {
+                    const int c0 = sr * F - gbase;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) {
+                        int k = d + j;
+                        k = k >= F ? k - F : k;
+                        const int rk = sr * R + 1 + k;                 // the partner's row (maybe another quadrant)
+                        const float gdk = sc[r * FU_SCS + c0 + k];
+                        const float gkd = sc[rk * FU_SCS + sr * F - gwin(rk >> 5) + d];
+                        hacc[j] += 0.5f * (gdk + gkd);
+                    }
+                }
+                named_sync();
+            };
 
             // ---- layer 1 (CUDA cores)
             if (c < SPT * F) {
@@ -849,7 +889,6 @@ __global__ void __launch_bounds__(320, 1)
                 for (int k = 0; k < F; ++k) z = fmaf(w1s[o * F + k], xq[s * F + k], z);
                 float f, f1, f2;
                 silu3f(z, f, f1, f2);
-                z1s[s * PS + o] = z;
                 zb[s * PS + o] = f;
                 pb[s * PS + o] = f1;
             }
@@ -867,7 +906,7 @@ __global__ void __launch_bounds__(320, 1)
                         const int o = ch * 32 + i;
                         v[i] = sv * src[o] * fac[o * fst];
                     }
-                    put_row32(sA, r, ch, v);
+                    put_row32<false>(sA, TILE_A, r, ch, v);
                 }
             }
             release_a();
@@ -877,8 +916,8 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll 1
             for (int j = 0; j < 4; j += 2) {
                 float v[32], u[32];
-                tmem_ld32(lane_base + j * 32, v);
-                tmem_ld32(lane_base + (j + 1) * 32, u);
+                tmem_ld32(lane_base + col_half + j * 32, v);
+                tmem_ld32(lane_base + col_half + (j + 1) * 32, u);
                 tmem_wait_ld();
                 if (prim) {
                     put_f32x32(zb + rowp + (hf * 4 + j) * 32, v);
@@ -889,10 +928,8 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll 3
             for (int idx = c; idx < SPT * HW; idx += FU_NC) {
                 const int s = idx >> 8, o = idx & (HW - 1);
-                const float z = zb[s * PS + o] + b2s[o];
                 float f, f1, f2;
-                silu3f(z, f, f1, f2);
-                z2s[s * PS + o] = z;
+                silu3f(zb[s * PS + o] + b2s[o], f, f1, f2);
                 zb[s * PS + o] = f;
                 pb[s * PS + o] = f1;
             }
@@ -902,27 +939,27 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll 1
                 for (int j = 0; j < 4; j += 2) {
                     float v[32], u[32];
-                    tmem_ld32(lane_base + j * 32, v);
-                    tmem_ld32(lane_base + (j + 1) * 32, u);
+                    tmem_ld32(lane_base + col_half + j * 32, v);
+                    tmem_ld32(lane_base + col_half + (j + 1) * 32, u);
                     tmem_wait_ld();
                     const int ch = hf * 4 + j;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = sv * src[ch * 32 + i] * fmaf(pv, 1.0f - v[i], v[i]);
-                    put_row32(sA, r, ch, v);
+                    put_row32<false>(sA, TILE_A, r, ch, v);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) u[i] = sv * src[ch * 32 + 32 + i] * fmaf(pv, 1.0f - u[i], u[i]);
-                    put_row32(sA, r, ch + 1, u);
+                    put_row32<false>(sA, TILE_A, r, ch + 1, u);
                 }
             }
             release_a();
 
-            // ---- layer 3: TMEM[256:512) holds z3 - b3 and J3; V, delta3 and the layer-3 Hessian term
+            // ---- layer 3: TMEM[256:512) holds z3 - b3 and J3; V, delta3, c3 and the Gram operands
             if (!wait_acc()) break;
 #pragma unroll 1
             for (int j = 0; j < 4; j += 2) {
                 float v[32], u[32];
-                tmem_ld32(lane_base + 256 + j * 32, v);
-                tmem_ld32(lane_base + 256 + (j + 1) * 32, u);
+                tmem_ld32(lane_base + 256 + col_half + j * 32, v);
+                tmem_ld32(lane_base + 256 + col_half + (j + 1) * 32, u);
                 tmem_wait_ld();
                 if (prim) {
                     put_f32x32(zb + rowp + (hf * 4 + j) * 32, v);
@@ -946,34 +983,40 @@ __global__ void __launch_bounds__(320, 1)
             named_sync();
             if (prim && hf == 0) Vout[p0 + sr] = m.s_out * ys[sr];
 #pragma unroll 1
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 4; ++j) {                     // Gram operands: c3 J3 (A), J3 (B, tangent rows)
                 const int ch = hf * 4 + j;
-                float v[32], x[32], w[32];
-                tmem_ld32(lane_base + 256 + j * 32, v);
+                float v[32], w[32];
+                tmem_ld32(lane_base + 256 + col_half + j * 32, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) x[i] = pv * zb[rowp + ch * 32 + i];
-                put_row32(sA, r, ch, x);
-                put_f32x32(ex + r * FU_XS, v);
+                for (int i = 0; i < 32; ++i) w[i] = tv * qb[rowp + ch * 32 + i] * v[i];
+                put_row32<true>(sA, TILE_A, r, ch, w);
+                if (tang) put_row32<true>(sG, FU_GBLK, gb, ch, v);
+            }
+            release_a();
+            if (!wait_acc()) break;                           // Gram product of layer 3 done
+            gram_readout();
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {                     // delta3 rows
+                const int ch = hf * 4 + j;
+                float x[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) w[i] = qb[rowp + ch * 32 + i] * v[i];
-                named_sync();
-                pair_products<F>(ex, row0, d, w, hacc);
-                named_sync();
+                for (int i = 0; i < 32; ++i) x[i] = pv * zb[rowp + ch * 32 + i];
+                put_row32<false>(sA, TILE_A, r, ch, x);
             }
             release_a();
 
-            // ---- reverse through layer 3: TMEM[256:512) = abar2 (value rows); J2 in TMEM[0:256)
+            // ---- reverse through layer 3: TMEM[256:512) = abar2 (value rows); TMEM[0:256) = z2 - b2, J2
             if (!wait_acc()) break;
 #pragma unroll 1
-            for (int j = 0; j < 4; j += 2) {
+            for (int j = 0; j < 4; ++j) {
                 float v[32], u[32];
-                tmem_ld32(lane_base + 256 + j * 32, v);
-                tmem_ld32(lane_base + 256 + (j + 1) * 32, u);
+                tmem_ld32(lane_base + 256 + col_half + j * 32, v);
+                tmem_ld32(lane_base + col_half + j * 32, u);
                 tmem_wait_ld();
                 if (prim) {
                     put_f32x32(pb + rowp + (hf * 4 + j) * 32, v);
-                    put_f32x32(pb + rowp + (hf * 4 + j + 1) * 32, u);
+                    put_f32x32(zb + rowp + (hf * 4 + j) * 32, u);
                 }
             }
             named_sync();
@@ -981,27 +1024,33 @@ __global__ void __launch_bounds__(320, 1)
             for (int idx = c; idx < SPT * HW; idx += FU_NC) {
                 const int s = idx >> 8, o = idx & (HW - 1);
                 float f, f1, f2;
-                silu3f(z2s[s * PS + o], f, f1, f2);
+                silu3f(zb[s * PS + o] + b2s[o], f, f1, f2);
                 const float ab = pb[s * PS + o];
                 zb[s * PS + o] = ab * f1;        // delta2 = abar2 silu'(z2)
                 qb[s * PS + o] = ab * f2;        // c2 = abar2 silu''(z2)
             }
             named_sync();
 #pragma unroll 1
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 4; ++j) {                     // Gram operands: c2 J2 (A), J2 (B)
                 const int ch = hf * 4 + j;
-                float v[32], x[32], w[32];
-                tmem_ld32(lane_base + j * 32, v);          // J2
+                float v[32], w[32];
+                tmem_ld32(lane_base + col_half + j * 32, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) x[i] = pv * zb[rowp + ch * 32 + i];
-                put_row32(sA, r, ch, x);
-                put_f32x32(ex + r * FU_XS, v);
+                for (int i = 0; i < 32; ++i) w[i] = tv * qb[rowp + ch * 32 + i] * v[i];
+                put_row32<true>(sA, TILE_A, r, ch, w);
+                if (tang) put_row32<true>(sG, FU_GBLK, gb, ch, v);
+            }
+            release_a();
+            if (!wait_acc()) break;                           // Gram product of layer 2 done
+            gram_readout();
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {                     // delta2 rows
+                const int ch = hf * 4 + j;
+                float x[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) w[i] = qb[rowp + ch * 32 + i] * v[i];
-                named_sync();
-                pair_products<F>(ex, row0, d, w, hacc);
-                named_sync();
+                for (int i = 0; i < 32; ++i) x[i] = pv * zb[rowp + ch * 32 + i];
+                put_row32<false>(sA, TILE_A, r, ch, x);
             }
             release_a();
 
@@ -1010,8 +1059,8 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll 1
             for (int j = 0; j < 4; j += 2) {
                 float v[32], u[32];
-                tmem_ld32(lane_base + 256 + j * 32, v);
-                tmem_ld32(lane_base + 256 + (j + 1) * 32, u);
+                tmem_ld32(lane_base + 256 + col_half + j * 32, v);
+                tmem_ld32(lane_base + 256 + col_half + (j + 1) * 32, u);
                 tmem_wait_ld();
                 if (prim) {
                     put_f32x32(pb + rowp + (hf * 4 + j) * 32, v);
@@ -1023,22 +1072,16 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll 3
             for (int idx = c; idx < SPT * HW; idx += FU_NC) {
                 const int s = idx >> 8, o = idx & (HW - 1);
+                float z = b1s[o];
+#pragma unroll
+                for (int k = 0; k < F; ++k) z = fmaf(w1s[o * F + k], xq[s * F + k], z);
                 float f, f1, f2;
-                silu3f(z1s[s * PS + o], f, f1, f2);
+                silu3f(z, f, f1, f2);
                 const float ab = pb[s * PS + o];
                 pb[s * PS + o] = ab * f1;        // d1 = abar1 silu'(z1)
                 qb[s * PS + o] = ab * f2;        // c1 = abar1 silu''(z1)
             }
-            // the two column halves of each row add their Hessian partial sums
-            if (hf == 1) {
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) exb[r * FU_XS + j] = hacc[j];
-            }
             named_sync();
-            if (hf == 0) {
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) hacc[j] += exb[r * FU_XS + j];
-            }
             // grad V and H1 = W1^T diag(c1) W1: thread (point s, slice sl) sums 16 hidden units,
             // then the 16 slices of a point (adjacent lanes) are added by shuffles
             if (c < SPT * 16) {
@@ -1075,6 +1118,8 @@ __global__ void __launch_bounds__(320, 1)
                 if (sl == 0 && b < n) {
 #pragma unroll
                     for (int k = 0; k < F; ++k) gout[b * F + k] = m.s_out * sins[k] * ga[k];
+                }
+                if (sl == 0) {
 #pragma unroll
                     for (int e = 0; e < NE; ++e) zb[s * PS + e] = ha[e];
                 }
