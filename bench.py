@@ -7,7 +7,7 @@ amplitudes) over n_steps, and the time -> energy transform with the weighted
 Morse + cubic + quartic surface, 16384 trajectories, 4000 steps of 10 au,
 4000 energies, FP64 propagation and FP64 Fourier step.
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload f6|f3|f9|batch|f9mlp]
+  python bench.py [--gpus N --steps K --warmup W] [--workload f6|f3|f9|batch|f9mlp|speedup]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
 
 Multi-GPU (torchrun): weak scaling, every rank runs its own batch (seed
@@ -198,9 +198,10 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    if args.workload == "batch":
-        print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no single oracle "
-                          "configuration; time --workload f3/f6/f9/f9mlp instead"}))
+    if args.workload in ("batch", "speedup"):
+        print(json.dumps({"impl": "reference", "unavailable": f"the {args.workload} workload has no single oracle "
+                          "configuration (its line carries the oracle's own rates); time --workload "
+                          "f3/f6/f9/f9mlp instead"}))
         return 0
     n_sample = args.cpu_sample
     if args.workload == "f9mlp":
@@ -594,14 +595,91 @@ def surrogate_arm(args):
     return 0
 
 
+def speedup_arm(args):
+    """F uncoupled Morse oscillators, F = 1..9 (the speed-up-versus-F comparison of
+    Sec. IV): GPU trajectory-steps/s of the FP64 and the mixed propagation (each with
+    its Fourier step) against the oracle on one host core and on all host cores."""
+    import torch
+    from paper_1312_4698_gb300 import scivr
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    oracle.build()
+    all_threads = oracle.max_threads()     # read before any single-thread run changes it
+    n = args.n_traj or 16384
+    steps = args.n_steps or 300
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    scivr.launch_count(reset=True)
+    with ClockSampler(gpu_selector(0)) as clk:
+        for F in range(1, 10):
+            w8 = wl.uncoupled_morse(F, n_traj=n, n_steps=steps, n_E=2000)
+            pes = scivr.scivr_create_pes(w8.pes)
+            bufs = scivr.alloc_buffers(w8)
+            scivr.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], n, 0, bufs.p0, bufs.q0, bufs.w)
+            K = steps + 1
+            row = {"F": F}
+            for name, prec, ftm, tol in (("gpu_fp64", 0, 0, w8.stab_tol), ("gpu_mixed", 1, 2, MIXED_STAB_TOL)):
+                def run():
+                    scivr.scivr_propagate(pes, w8.dt, steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0, bufs.q0,
+                                          bufs.amp, K, bufs.good, precision=prec, stab_tol=tol, stream=stream)
+                    scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, steps, w8.dt, w8.E_min, w8.E_max,
+                                         w8.n_E, bufs.I[0], bufs.n_good, ft_mode=ftm, stream=stream)
+                for _ in range(args.warmup):
+                    flush.zero_()
+                    run()
+                torch.cuda.synchronize()
+                ms = 0.0
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    run()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                row[name] = n * steps / (ms / args.steps * 1e-3)
+            # the oracle on a bounded sample (about a second per F and thread setting)
+            for name, threads in (("cpu_1core", 1), ("cpu_all", all_threads)):
+                ns = max(16, int(2e6 / (steps * (F + 1) ** 2))) * threads
+                p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, ns, 0)
+                c0 = time.perf_counter()
+                amp, good = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, steps, p0, q0,
+                                             w8.stab_tol, threads)
+                oracle.spectrum(amp[0], w, good, steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, threads)
+                row[name] = ns * steps / (time.perf_counter() - c0)
+            row["speedup_fp64_vs_1core"] = row["gpu_fp64"] / row["cpu_1core"]
+            row["speedup_mixed_vs_1core"] = row["gpu_mixed"] / row["cpu_1core"]
+            row["speedup_fp64_vs_all_cores"] = row["gpu_fp64"] / row["cpu_all"]
+            rows.append(row)
+    line = {
+        "metric": METRIC, "value": rows[-1]["gpu_mixed"], "unit": "trajectory-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": n * steps / rows[-1]["gpu_mixed"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 and f32+f64", "data": "synthetic",
+        "config": {"workload": f"uncoupled Morse oscillators F = 1..9 (omega ~ U[1100, 3000] cm^-1, D ~ U[0.15, "
+                               f"0.25]), {n} trajectories, {steps} steps, 2000 energies; value = mixed path at F = 9",
+                   "l2": f"flushed between runs ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "cpu_cores": all_threads},
+        "sweep": rows,
+        "gpu_launches": scivr.launch_count(reset=True),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="f6", choices=["f3", "f6", "f9", "batch", "f9mlp"])
-    ap.add_argument("--train-epochs", type=int, default=12, help="training epochs of --workload f9mlp")
+    ap.add_argument("--workload", default="f6", choices=["f3", "f6", "f9", "batch", "f9mlp", "speedup"])
+    ap.add_argument("--train-epochs", type=int, default=40, help="training epochs of --workload f9mlp")
     ap.add_argument("--check-traj", type=int, default=2048,
                     help="trajectories of the --workload f9mlp accuracy check")
     ap.add_argument("--n-mol", type=int, default=48, help="molecules in --workload batch")
@@ -624,6 +702,8 @@ def main(argv=None):
         return batch_arm(args)
     if args.workload == "f9mlp":
         return surrogate_arm(args)
+    if args.workload == "speedup":
+        return speedup_arm(args)
 
     import torch
     import torch.distributed as dist
