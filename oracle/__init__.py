@@ -62,7 +62,7 @@ class _Pes(C.Structure):
 class _Prop(C.Structure):
     _fields_ = [("F", C.c_int32), ("n_steps", C.c_int32), ("dt", C.c_double),
                 ("stab_tol", C.c_double), ("gamma", C.c_void_p), ("p_eq", C.c_void_p),
-                ("q_eq", C.c_void_p), ("n_chi", C.c_int32)]
+                ("q_eq", C.c_void_p), ("n_chi", C.c_int32), ("amplitude", C.c_int32)]
 
 
 class _Cplx(C.Structure):
@@ -96,6 +96,8 @@ def _load():
                                          vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
             lib.or_spectrum.restype = C.c_int
             lib.or_spectrum.argtypes = [vp, i64, vp, vp, i64, i32, d, d, d, i32, vp, vp, C.c_int]
+            lib.or_spectrum_hk.restype = C.c_int
+            lib.or_spectrum_hk.argtypes = [vp, i64, vp, i64, i32, d, d, d, i32, vp, vp, vp]
             lib.or_philox4x32_10.restype = None
             lib.or_philox4x32_10.argtypes = [vp, vp, vp]
             lib.or_sample_initial.restype = C.c_int
@@ -178,16 +180,20 @@ def log_overlap(gamma, p1, q1, p2, q2):
     return complex(r.re, r.im)
 
 
-def _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol):
+AMP_TA = 0   # time-averaged amplitude: <chi|p q> e^{i (S + theta/2)}
+AMP_HK = 1   # Herman-Kluk summand of Eq. I(E)_SCIVR, weight included
+
+
+def _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol, amplitude=AMP_TA):
     gamma = _f64(gamma)
     p_eq = _f64(np.atleast_2d(p_eq))
     q_eq = _f64(np.atleast_2d(q_eq))
     s = _Prop(F, int(n_steps), float(dt), float(stab_tol), _p(gamma), _p(p_eq), _p(q_eq),
-              p_eq.shape[0])
+              p_eq.shape[0], int(amplitude))
     return s, (gamma, p_eq, q_eq)
 
 
-def propagate_one(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6):
+def propagate_one(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6, amplitude=AMP_TA):
     """One trajectory with full diagnostics.
 
     Returns a dict with amp [n_chi, K], good, the series S, theta, detA, detM
@@ -195,7 +201,7 @@ def propagate_one(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6):
     lib = _load()
     P = Pes(desc)
     F = P.F
-    s, keep = _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol)
+    s, keep = _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol, amplitude)
     K = n_steps + 1
     n_chi = keep[1].shape[0]
     amp = np.zeros((n_chi, K), dtype=np.complex128)
@@ -211,7 +217,7 @@ def propagate_one(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6):
 
 
 def propagate(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6, n_threads=0,
-              final=False):
+              final=False, amplitude=AMP_TA):
     """Batch propagation; p0, q0 are [F, n_traj] (variable-major).
 
     Returns amp [n_chi, n_traj, n_steps+1] complex128 and good [n_traj] uint8,
@@ -221,7 +227,7 @@ def propagate(desc, gamma, p_eq, q_eq, dt, n_steps, p0, q0, stab_tol=1e-6, n_thr
     F = P.F
     p0 = _f64(p0); q0 = _f64(q0)
     n = p0.shape[1]
-    s, keep = _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol)
+    s, keep = _prop_struct(F, gamma, p_eq, q_eq, dt, n_steps, stab_tol, amplitude)
     n_chi = keep[1].shape[0]
     K = n_steps + 1
     amp = np.zeros((n_chi, n, K), dtype=np.complex128)
@@ -250,6 +256,20 @@ def spectrum(amp, w, good, n_steps, dt, E_min, E_max, n_E, n_threads=0):
                     float(dt), float(E_min), float(E_max), int(n_E), _p(I), _p(ng),
                     int(n_threads))
     return I, int(ng[0])
+
+
+def spectrum_hk(amp, good, n_steps, dt, E_min, E_max, n_E):
+    """Eq. I(E)_SCIVR on Herman-Kluk amplitudes amp [n_traj, K] (propagated with
+    amplitude=AMP_HK); returns (I [n_E], n_good, survival amplitude C [K])."""
+    lib = _load()
+    amp = np.ascontiguousarray(amp, dtype=np.complex128)
+    good = np.ascontiguousarray(good, dtype=np.uint8)
+    I = np.zeros(int(n_E))
+    ng = np.zeros(1, dtype=np.int64)
+    Cs = np.zeros(amp.shape[1], dtype=np.complex128)
+    lib.or_spectrum_hk(_p(amp), amp.shape[1], _p(good), amp.shape[0], int(n_steps), float(dt), float(E_min),
+                       float(E_max), int(n_E), _p(I), _p(ng), _p(Cs))
+    return I, int(ng[0]), Cs
 
 
 def philox4x32_10(ctr, key):

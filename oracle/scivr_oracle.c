@@ -27,6 +27,9 @@
  *      amplitude a(c) = <chi|p_c q_c> exp(i (S_c + phi_c)) (Eq. I(E)_discreto).
  *   7. The discrete time-averaged spectrum, Eq. I(E)_discreto, as a direct
  *      O(K * N_E) Fourier sum per good trajectory.
+ *   8. The plain Herman-Kluk SC-IVR spectrum, Eq. I(E)_SCIVR: each trajectory's
+ *      summand C_t e^{iS_t} <chi|p_t q_t> <p0 q0|chi> (times its weight), their
+ *      mean over trajectories, and the one-sided Fourier transform.
  *
  * Every number is IEEE double; transcendental functions come from libm.
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.
@@ -41,6 +44,7 @@
 #endif
 
 #define OR_TWO_PI 6.283185307179586476925286766559
+#define OR_PI 3.141592653589793238462643383280
 
 /* ------------------------------------------------------------------------ */
 /* Potential: V(q) = sum_i diag_i(q_i) + sum_m c3_m q_i q_j q_k + sum_m c4_m q_i q_j q_k q_l */
@@ -292,6 +296,7 @@ typedef struct {
     const double *p_eq;    /* [n_chi * F] */
     const double *q_eq;    /* [n_chi * F] */
     int32_t n_chi;
+    int32_t amplitude;     /* 0: time-averaged (prefactor phase only), 1: Herman-Kluk (Eq. I(E)_SCIVR) */
 } or_prop;
 
 typedef struct {
@@ -437,8 +442,21 @@ int or_propagate_one(const or_pes *pes, const or_prop *prm, const double *p0, co
             for (int x = 0; x < prm->n_chi; ++x) {
                 double complex lo = or_log_overlap(F, prm->gamma, prm->p_eq + x * F,
                                                    prm->q_eq + x * F, p, q);
-                double phase = cimag(lo) + S + 0.5 * theta;
-                amp[x * amp_chi_stride + step] = exp(creal(lo)) * (cos(phase) + I * sin(phase));
+                if (prm->amplitude == 1) {
+                    /* Herman-Kluk summand of Eq. I(E)_SCIVR times the sampling weight
+                     * w = 1 / |<p0 q0|chi>|^2:  C_t e^{i S_t} <chi|p_t q_t> <p0 q0|chi> w,
+                     * with C_t = |det A|^{1/2} e^{i theta/2} (Eq. prefactor on the branch
+                     * that theta follows) */
+                    double complex lo0 = or_log_overlap(F, prm->gamma, prm->p_eq + x * F,
+                                                        prm->q_eq + x * F, p0, q0);
+                    double complex Ct = sqrt(cabs(detA)) * cexp(0.5 * I * theta);
+                    double complex ov0 = cexp(lo0);
+                    double w0 = 1.0 / (creal(ov0) * creal(ov0) + cimag(ov0) * cimag(ov0));
+                    amp[x * amp_chi_stride + step] = Ct * cexp(I * S) * cexp(lo) * conj(ov0) * w0;
+                } else {
+                    double phase = cimag(lo) + S + 0.5 * theta;
+                    amp[x * amp_chi_stride + step] = exp(creal(lo)) * (cos(phase) + I * sin(phase));
+                }
             }
         }
     }
@@ -530,6 +548,46 @@ int or_spectrum(const double complex *amp, int64_t amp_ld, const double *w, cons
         }
         free(tw);
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plain Herman-Kluk SC-IVR spectrum, Eq. I(E)_SCIVR                         */
+/* ------------------------------------------------------------------------ */
+
+/* The survival amplitude <chi|e^{-iHt}|chi> at t = c dt is the Monte Carlo mean
+ * of the Herman-Kluk summands (propagation with amplitude = 1, which carries
+ * the weights) over the good trajectories,
+ *   C(c dt) = (1/n_good) sum_{j good} amp_j(c),
+ * and I(E) = (Re / pi) int_0^T C(t) e^{i E t} dt by the trapezoid rule,
+ *   I(E_k) = (dt/pi) Re[ C(0)/2 + sum_{c=1}^{n_steps} C(c dt) e^{i E_k c dt} ]
+ * (the full-line rectangle rule with C(-t) = conj C(t)). */
+int or_spectrum_hk(const double complex *amp, int64_t amp_ld, const uint8_t *good, int64_t n_traj,
+                   int32_t n_steps, double dt, double E_min, double E_max, int32_t n_E, double *I_out,
+                   int64_t *n_good_out, double complex *C_out)
+{
+    int64_t n_good = 0;
+    for (int64_t j = 0; j < n_traj; ++j) n_good += good[j] ? 1 : 0;
+    if (n_good_out) *n_good_out = n_good;
+    const int K = n_steps + 1;
+    double complex *C = malloc(sizeof(double complex) * K);
+    for (int c = 0; c < K; ++c) {
+        double complex acc = 0.0;
+        for (int64_t j = 0; j < n_traj; ++j)
+            if (good[j]) acc += amp[j * amp_ld + c];
+        C[c] = n_good > 0 ? acc / (double)n_good : 0.0;
+        if (C_out) C_out[c] = C[c];
+    }
+    for (int k = 0; k < n_E; ++k) {
+        double E = n_E > 1 ? E_min + k * ((E_max - E_min) / (n_E - 1)) : E_min;
+        double complex acc = 0.5 * C[0];
+        for (int c = 1; c < K; ++c) {
+            double ang = E * (c * dt);
+            acc += C[c] * (cos(ang) + I * sin(ang));
+        }
+        I_out[k] = dt / OR_PI * creal(acc);
+    }
+    free(C);
     return 0;
 }
 
