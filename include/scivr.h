@@ -67,6 +67,10 @@ enum { SCIVR_FT_FP64 = 0,         /* FP64 fused-multiply-add contraction (CUDA c
        SCIVR_FT_TC_BF16X3 = 2,    /* tensor cores: two BF16 digits, three digit products */
        SCIVR_FT_TC_BF16X6 = 3 };  /* tensor cores: three BF16 digits, six products (FP32-level) */
 
+/* What scivr_propagate records per step. */
+enum { SCIVR_AMP_TA = 0,          /* time-averaged SC-IVR summand (Eq. I(E)_discreto) */
+       SCIVR_AMP_HK = 1 };        /* Herman-Kluk SC-IVR summand with its sampling weight (Eq. I(E)_SCIVR) */
+
 #define SCIVR_MAX_F 24            /* largest number of modes */
 #define SCIVR_MAX_CHI 8           /* largest number of reference states per call */
 
@@ -104,6 +108,7 @@ typedef struct {
     const double *q_eq;     /* [n_chi * F] reference-state positions */
     int32_t n_chi;          /* number of reference states, 1..SCIVR_MAX_CHI */
     int32_t kernel;         /* SCIVR_KERNEL_AUTO / _THREAD / _GROUP */
+    int32_t amplitude;      /* SCIVR_AMP_TA (0) or SCIVR_AMP_HK */
 } scivr_prop_params;
 
 /* Optional final-state outputs of scivr_propagate (device pointers, each may be NULL). */
@@ -149,7 +154,12 @@ int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
 /* Propagate n_traj trajectories from (p0, q0) to T = n_steps dt and record, for
  * every reference state x and step c = 0..n_steps, the amplitude
  *   amp[x][j][c] = <chi_x|p_j(c dt), q_j(c dt)> exp(i (S_j(c dt) + phi_j(c dt)))
- * (the summand of Eq. I(E)_discreto without the energy factor).  Integrator:
+ * (the summand of Eq. I(E)_discreto without the energy factor).  With
+ * prm->amplitude = SCIVR_AMP_HK it records instead the Herman-Kluk summand of
+ * Eq. I(E)_SCIVR times the sampling weight w_j = 1/|<p_j(0) q_j(0)|chi_x>|^2,
+ *   amp[x][j][c] = C_j(c dt) e^{i S_j(c dt)} <chi_x|p_j(c dt), q_j(c dt)> / <chi_x|p_j(0), q_j(0)>,
+ * C = |det A|^{1/2} e^{i theta/2} (Eq. prefactor on the branch theta follows),
+ * whose mean over trajectories is <chi_x|e^{-iHt}|chi_x> (scivr_spectrum_hk).  Integrator:
  * Yoshida's fourth-order triple jump of exact drift/kick sub-flows for (p, q),
  * the action S and the monodromy M (Sec. III.A).  phi = theta/2 with theta the
  * continuous arg det A of the Herman-Kluk matrix (Eq. prefactor), unwrapped
@@ -192,6 +202,21 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
                    const uint8_t *good, int64_t n_traj, int32_t n_steps, double dt,
                    double E_min, double E_max, int32_t n_E, int32_t ft_mode,
                    double *I_out, int64_t *n_good_out, void *stream);
+
+/* Plain Herman-Kluk SC-IVR spectrum of one reference state, Eq. I(E)_SCIVR,
+ * from amplitudes recorded with SCIVR_AMP_HK:
+ *   C(c dt) = (1/n_good) sum_{j: good[j] != 0} amp[j][c]   (the survival amplitude),
+ *   I(E_k) = (dt/pi) Re[ C(0)/2 + sum_{c=1}^{n_steps} C(c dt) e^{i E_k c dt} ]
+ * (Eq. I(E)_timedependent's one-sided integral by the trapezoid rule), E_k as
+ * for scivr_spectrum.  amp: device complex double [n_traj][amp_ld].  good:
+ * device [n_traj].  I_out: device [n_E].  C_out: device complex double
+ * [n_steps+1] (may be NULL).  n_good_out: device int64 (may be NULL).  The
+ * column sums over trajectories run in a fixed order (bitwise reproducible).
+ * Allocates stream-ordered scratch of about 16 (n_steps+1) ceil(n_traj/4096)
+ * bytes.  Errors: as scivr_spectrum. */
+int scivr_spectrum_hk(const void *amp, int64_t amp_ld, const uint8_t *good, int64_t n_traj, int32_t n_steps,
+                      double dt, double E_min, double E_max, int32_t n_E, double *I_out, void *C_out,
+                      int64_t *n_good_out, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched runs: many molecules (different F, n_traj, n_steps) in one call    */

@@ -98,6 +98,8 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
         return fail(SCIVR_EINVAL, "scivr_propagate: precision %d invalid", prm->precision);
     if (prm->kernel < SCIVR_KERNEL_AUTO || prm->kernel > SCIVR_KERNEL_GROUP)
         return fail(SCIVR_EINVAL, "scivr_propagate: kernel %d invalid", prm->kernel);
+    if (prm->amplitude != SCIVR_AMP_TA && prm->amplitude != SCIVR_AMP_HK)
+        return fail(SCIVR_EINVAL, "scivr_propagate: amplitude %d invalid", prm->amplitude);
     if (!propagate_supported(F, prm->precision, prm->kernel))
         return fail(SCIVR_EUNSUPPORTED, "scivr_propagate: precision %d / kernel %d not built for F=%d",
                     prm->precision, prm->kernel, F);
@@ -110,6 +112,7 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
     A.n_chi = prm->n_chi;
     A.precision = prm->precision;
     A.kernel = prm->kernel;
+    A.amplitude = prm->amplitude;
     A.dt = prm->dt;
     A.stab_tol = prm->stab_tol;
     triple_jump(A.cdrift, A.dkick);
@@ -403,6 +406,32 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
     cudaError_t e2 = cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "scivr_spectrum: cudaFreeAsync");
+    ok();
+    return SCIVR_OK;
+}
+
+int scivr_spectrum_hk(const void *amp, int64_t amp_ld, const uint8_t *good, int64_t n_traj, int32_t n_steps,
+                      double dt, double E_min, double E_max, int32_t n_E, double *I_out, void *C_out,
+                      int64_t *n_good_out, void *stream)
+{
+    // same argument rules as scivr_spectrum (weights are not used: the summands carry them)
+    const double one = 1.0;
+    int rc = check_spectrum_args(amp, amp_ld, SCIVR_FP64, &one, good, n_traj, n_steps, dt, E_min, E_max, n_E,
+                                 SCIVR_FT_FP64, I_out);
+    if (rc != SCIVR_OK) return rc;
+    if (C_out && reinterpret_cast<uintptr_t>(C_out) % 16 != 0)
+        return fail(SCIVR_EINVAL, "scivr_spectrum_hk: C_out not 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, spectrum_hk_scratch_bytes(n_traj, n_steps), s);
+    if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum_hk: cudaMallocAsync");
+    int nl = 0;
+    e = launch_spectrum_hk(static_cast<const double2 *>(amp), amp_ld, good, n_traj, n_steps, dt, E_min, E_max, n_E,
+                           I_out, static_cast<double2 *>(C_out), n_good_out, scratch, s, &nl);
+    g_launches += nl;
+    cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum_hk: launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "scivr_spectrum_hk: cudaFreeAsync");
     ok();
     return SCIVR_OK;
 }

@@ -189,6 +189,10 @@ int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t f
                                      it.prm.dt, it.E_min, it.E_max, it.n_E, ft_mode, it.I_out);
         if (rc == SCIVR_OK && it.prm.precision == SCIVR_MIXED && it.pes->dev.F > 9)
             rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: mixed precision is built for F <= 9");
+        if (rc == SCIVR_OK && it.prm.amplitude != SCIVR_AMP_TA)
+            rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: batch spectra are time-averaged (SCIVR_AMP_TA)");
+        if (rc == SCIVR_OK && it.pes->dev.mlp.H != 0)
+            rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: potentials with a learned residual run through scivr_propagate");
         if (rc != SCIVR_OK) {
             char msg[600];
             std::snprintf(msg, sizeof msg, "scivr_batch_create: item %d: %s", i, scivr_last_error());

@@ -28,9 +28,12 @@ struct State {
     int *step;            // device step counter (column of the amplitude)
 };
 
+// Amplitude of step `step` for every reference state: the time-averaged summand,
+// or with SCIVR_AMP_HK the Herman-Kluk summand (|det A|^{1/2} = sqrt(absA), divided
+// by the initial overlap).
 template <int F>
 __device__ __forceinline__ void record(const PropLaunch &L, int64_t j, int step, const double (&p)[F],
-                                       const double (&q)[F], double S, double theta)
+                                       const double (&q)[F], double S, double theta, double absA)
 {
     const PropArgs &A = L.args;
     for (int x = 0; x < A.n_chi; ++x) {
@@ -43,8 +46,15 @@ __device__ __forceinline__ void record(const PropLaunch &L, int64_t j, int step,
             re = fma(-A.pw[a] * dp, dp, re);
             im = fma(0.5 * (A.p_eq[x * F + a] + p[a]), dq, im);
         }
+        double ph = im + S + 0.5 * theta;
+        if (A.amplitude == SCIVR_AMP_HK) {
+            double re0, im0;
+            chi_log_overlap0<F>(A, L.p0, L.q0, L.n_traj, j, x, re0, im0);
+            re = re - re0 + 0.5 * log(absA);
+            ph -= im0;
+        }
         double sn, cs;
-        sincos(im + S + 0.5 * theta, &sn, &cs);
+        sincos(ph, &sn, &cs);
         const double mag = exp(re);
         L.amp[x * L.chi_stride + j * L.amp_ld + step] = make_double2(mag * cs, mag * sn);
     }
@@ -93,7 +103,7 @@ __global__ void __launch_bounds__(KIND == 3 ? 64 : 128, KIND == 3 ? 2 : 3) k_mlp
         st.arg_old[j] = 0.0;
         st.stab[j] = 0.0;
         L.good[j] = 1;
-        record<F>(L, j, 0, p, q, 0.0, 0.0);
+        record<F>(L, j, 0, p, q, 0.0, 0.0, 1.0);
         const float td = A.tdrift_f[0];
         for (int c = 0; c < N2; ++c)
 #pragma unroll
@@ -285,7 +295,7 @@ __global__ void __launch_bounds__(KIND == 3 ? 64 : 128, KIND == 3 ? 2 : 3) k_mlp
         for (int a = 0; a < F; ++a) finite = finite && isfinite(p[a]) && isfinite(q[a]);
         if (!finite) good = false;
         L.good[j] = good ? 1 : 0;
-        record<F>(L, j, step, p, q, S, theta);
+        record<F>(L, j, step, p, q, S, theta, hypot(dA.re, dA.im));
         if (step == A.n_steps) {
             const FinalDev &fo = L.fin;
             if (fo.p) for (int a = 0; a < F; ++a) fo.p[a * n + j] = p[a];

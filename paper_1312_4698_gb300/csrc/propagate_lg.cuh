@@ -99,6 +99,8 @@ struct WarpShared {
     typename Vec2<Real>::T A[F * F][32];   // prefactor matrix per job, entry-major (job column swizzled)
     double pj[F][32], qj[F][32];           // state per job (for the overlap; job column swizzled)
     double Sj[32];                          // action per job
+    double lnA[32];                         // log |det A|^{1/2} per job (Herman-Kluk summand only)
+    double2 ov0[SCIVR_MAX_CHI][T];          // log <chi|p0 q0> per trajectory (Herman-Kluk summand only)
 };
 
 // One CTA's share of a propagation: trajectories (cta * WARPS + warp) * T + t.
@@ -209,10 +211,13 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 re = fma(-cc.pw[a] * dp, dp, re);
                 im = fma(0.5 * (cc.p_eq[x][a] + pa), dq, im);
             }
+            sh.ov0[x][t] = make_double2(re, im);
             double sn, cs;
             sincos(im, &sn, &cs);
             const double mag = exp(re);
-            L.amp[x * L.chi_stride + jl * L.amp_ld] = make_double2(mag * cs, mag * sn);
+            // the Herman-Kluk summand is exactly 1 at t = 0 (C = 1, S = 0, the overlaps cancel)
+            L.amp[x * L.chi_stride + jl * L.amp_ld] =
+                A.amplitude == SCIVR_AMP_HK ? make_double2(1.0, 0.0) : make_double2(mag * cs, mag * sn);
         }
     }
 
@@ -220,7 +225,6 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         const int cnt = min(C, A.n_steps - step0);
         // ---------------- phase 1: cnt steps, group-parallel ----------------
         for (int c = 0; c < cnt; ++c) {
-#pragma unroll
             Real dS = Real(0);   // this lane's share of the step's action increment
             for (int sub = 0; sub < 4; ++sub) {
                 // drift: q += tau p, S += tau p.p/2, M_q += tau M_p
@@ -448,6 +452,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             }
             detA = make_double2(dr, di);
         }
+        // Herman-Kluk summand: log |det A|^{1/2}, the only part of det A phase 4 needs
+        if (A.amplitude == SCIVR_AMP_HK) sh.lnA[ln] = 0.5 * log(hypot(detA.x, detA.y));
         // ---------------- phase 3: continuous phase (segmented scan) ----------------
         const double arg = atan2(detA.y, detA.x);
         double arg_prev = __shfl_up_sync(FULL, arg, 1, G);
@@ -480,7 +486,13 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     re = fma(-cc.pw[a] * dp, dp, re);
                     im = fma(0.5 * (cc.p_eq[x][a] + pa), dq, im);
                 }
-                const double ph = im + S + 0.5 * theta;
+                double ph = im + S + 0.5 * theta;
+                if (A.amplitude == SCIVR_AMP_HK) {
+                    // Herman-Kluk summand: |det A|^{1/2} and the division by <chi|p0 q0>
+                    const double2 o = sh.ov0[x][t];
+                    re = re - o.x + sh.lnA[ln];
+                    ph -= o.y;
+                }
                 double sn, cs, mag;
                 if constexpr (sizeof(Real) == 4) {
                     const double red = fma(-kTwoPi, rint(ph * kInvTwoPi), ph);   // FP64 reduction to [-pi, pi]

@@ -303,7 +303,14 @@ __global__ void __launch_bounds__(64) k_propagate_tpt_fp64(const PropLaunch L)
                 re = fma(-A.pw[a] * dp, dp, re);
                 im = fma(0.5 * (A.p_eq[x * F + a] + p[a]), dq, im);
             }
-            const double ph = im + S + 0.5 * theta;
+            double ph = im + S + 0.5 * theta;
+            if (A.amplitude == SCIVR_AMP_HK) {
+                // Herman-Kluk summand: |det A|^{1/2} and the division by <chi|p0 q0>
+                double re0, im0;
+                chi_log_overlap0<F>(A, L.p0, L.q0, n, j, x, re0, im0);
+                re = re - re0 + 0.5 * log(hypot(detA.re, detA.im));
+                ph -= im0;
+            }
             double sn, cs;
             sincos(ph, &sn, &cs);
             const double mag = exp(re);

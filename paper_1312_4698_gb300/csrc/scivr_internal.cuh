@@ -45,6 +45,7 @@ struct PesDev {
 // Kernel-side propagation parameters, passed by value.
 struct PropArgs {
     int F, n_steps, n_chi, precision, kernel;
+    int amplitude;                   // SCIVR_AMP_TA or SCIVR_AMP_HK
     double dt, stab_tol, ref_step;   // ref_step = sum_i gamma_i dt
     double cdrift[4], dkick[3];      // triple-jump fractions of dt
     double tdrift[4], tkick[3];      // the sub-step lengths themselves (fraction x dt)
@@ -90,6 +91,10 @@ cudaError_t launch_spectrum_noalloc(const double2 *amp, int64_t amp_ld, const do
                                     double E_min, double E_max, int n_E, double *I_out,
                                     int64_t *n_good_out, cudaStream_t s, int *n_launch);
 int spectrum_noalloc_max_energies();
+size_t spectrum_hk_scratch_bytes(int64_t n_traj, int n_steps);
+cudaError_t launch_spectrum_hk(const double2 *amp, int64_t amp_ld, const uint8_t *good, int64_t n_traj, int n_steps,
+                               double dt, double E_min, double E_max, int n_E, double *I_out, double2 *C_out,
+                               int64_t *n_good_out, void *scratch, cudaStream_t s, int *n_launch);
 int ft_tc_digits(int ft_mode);
 size_t spectrum_tc_scratch_bytes(int ft_mode, int64_t n_traj, int n_steps, int n_E);
 cudaError_t launch_spectrum_tc(int ft_mode, const double2 *amp, int64_t amp_ld, const double *w,
@@ -131,6 +136,24 @@ int cuda_error(cudaError_t e, const char *where);
 cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, const int2 *work, int n_work,
                                      int *counter, int n_sm, cudaStream_t s);
 int batch_warp_candidates(int F, int *out);   // returns the count (<= 2)
+
+// log <chi_x|p0_j, q0_j> = re0 + i im0 (Eq. coherent_state with unit-norm
+// states): the initial overlap that the Herman-Kluk summand divides by.
+template <int F>
+__device__ __forceinline__ void chi_log_overlap0(const PropArgs &A, const double *p0, const double *q0,
+                                                 int64_t n, int64_t j, int x, double &re0, double &im0)
+{
+    re0 = 0.0;
+    im0 = 0.0;
+#pragma unroll
+    for (int a = 0; a < F; ++a) {
+        const double pa = p0[a * n + j], qa = q0[a * n + j];
+        const double dq = A.q_eq[x * F + a] - qa, dp = A.p_eq[x * F + a] - pa;
+        re0 = fma(-A.qw[a] * dq, dq, re0);
+        re0 = fma(-A.pw[a] * dp, dp, re0);
+        im0 = fma(0.5 * (A.p_eq[x * F + a] + pa), dq, im0);
+    }
+}
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kInvTwoPi = 0.15915494309189533576888376337251;

@@ -36,6 +36,8 @@ SCIVR_FT_TC_BF16X6 = 3
 SCIVR_KERNEL_AUTO = 0
 SCIVR_KERNEL_THREAD = 1
 SCIVR_KERNEL_GROUP = 2
+SCIVR_AMP_TA = 0
+SCIVR_AMP_HK = 1
 SCIVR_MAX_F = 24
 SCIVR_MAX_CHI = 8
 
@@ -63,7 +65,8 @@ class scivr_pes_desc(C.Structure):
 class scivr_prop_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_steps", C.c_int32), ("precision", C.c_int32),
                 ("stab_tol", C.c_double), ("gamma", C.c_void_p), ("p_eq", C.c_void_p),
-                ("q_eq", C.c_void_p), ("n_chi", C.c_int32), ("kernel", C.c_int32)]
+                ("q_eq", C.c_void_p), ("n_chi", C.c_int32), ("kernel", C.c_int32),
+                ("amplitude", C.c_int32)]
 
 
 class scivr_final_state(C.Structure):
@@ -97,6 +100,8 @@ _lib.scivr_spectrum.argtypes = [_vp, _i64, _i32, _vp, _vp, _i64, _i32, _d, _d, _
 _lib.scivr_spectrum.restype = C.c_int
 _lib.scivr_spectrum_noalloc.argtypes = list(_lib.scivr_spectrum.argtypes)
 _lib.scivr_spectrum_noalloc.restype = C.c_int
+_lib.scivr_spectrum_hk.argtypes = [_vp, _i64, _vp, _i64, _i32, _d, _d, _d, _i32, _vp, _vp, _vp, _vp]
+_lib.scivr_spectrum_hk.restype = C.c_int
 _lib.scivr_batch_create.argtypes = [C.POINTER(scivr_batch_item), _i32, _i32, C.POINTER(_vp)]
 _lib.scivr_batch_create.restype = C.c_int
 _lib.scivr_batch_launch.argtypes = [_vp, _vp]
@@ -115,7 +120,7 @@ _lib.scivr_launch_count.argtypes = [C.c_int]
 _lib.scivr_launch_count.restype = _i64
 
 EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_sample_initial",
-            "scivr_propagate", "scivr_spectrum", "scivr_spectrum_noalloc", "scivr_check_status",
+            "scivr_propagate", "scivr_spectrum", "scivr_spectrum_noalloc", "scivr_spectrum_hk", "scivr_check_status",
             "scivr_selftest_wait_timeout", "scivr_last_error", "scivr_launch_count",
             "scivr_batch_create", "scivr_batch_launch", "scivr_batch_info", "scivr_batch_destroy",
             "scivr_mlp_param_count", "scivr_pes_set_mlp", "scivr_mlp_eval", "scivr_mlp_get_params",
@@ -220,13 +225,16 @@ sample_initial = scivr_sample_initial
 
 def scivr_propagate(pes: Pes, dt, n_steps, gamma, p_eq, q_eq, n_traj, p0, q0, amp, amp_ld, good,
                     precision=SCIVR_FP64, stab_tol=1e-6, fin: Optional[dict] = None, stream=None,
-                    kernel=SCIVR_KERNEL_AUTO):
-    """p_eq, q_eq: [n_chi, F] host arrays.  fin: optional dict of device tensors."""
+                    kernel=SCIVR_KERNEL_AUTO, amplitude=SCIVR_AMP_TA):
+    """p_eq, q_eq: [n_chi, F] host arrays.  fin: optional dict of device tensors.
+    amplitude: SCIVR_AMP_TA (time-averaging integrand) or SCIVR_AMP_HK (plain
+    Herman-Kluk summand)."""
     g = _f64(gamma)
     pe = _f64(np.atleast_2d(p_eq))
     qe = _f64(np.atleast_2d(q_eq))
     prm = scivr_prop_params(float(dt), int(n_steps), int(precision), float(stab_tol),
-                            g.ctypes.data, pe.ctypes.data, qe.ctypes.data, pe.shape[0], int(kernel))
+                            g.ctypes.data, pe.ctypes.data, qe.ctypes.data, pe.shape[0], int(kernel),
+                            int(amplitude))
     fs = None
     if fin:
         fs = scivr_final_state(*[_ptr(fin.get(k)) for k in ("p", "q", "S", "theta", "detM", "detA", "M",
@@ -248,6 +256,14 @@ def scivr_spectrum(amp, amp_ld, w, good, n_traj, n_steps, dt, E_min, E_max, n_E,
 
 
 spectrum = scivr_spectrum
+
+
+def scivr_spectrum_hk(amp, amp_ld, good, n_traj, n_steps, dt, E_min, E_max, n_E, I_out, C_out=None,
+                      n_good_out=None, stream=None):
+    """Plain HK SC-IVR spectrum from the summands written with amplitude=SCIVR_AMP_HK."""
+    _check(_lib.scivr_spectrum_hk(_ptr(amp), int(amp_ld), _ptr(good), int(n_traj), int(n_steps), float(dt),
+                                  float(E_min), float(E_max), int(n_E), _ptr(I_out), _ptr(C_out),
+                                  _ptr(n_good_out), _stream(stream)), "scivr_spectrum_hk")
 
 
 def scivr_spectrum_noalloc(amp, amp_ld, w, good, n_traj, n_steps, dt, E_min, E_max, n_E, I_out,

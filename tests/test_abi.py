@@ -109,3 +109,17 @@ def test_learned_residual_entry_points_validate_before_any_launch(lib):
     assert scivr._lib.scivr_mlp_loss_grad(None, 4, 1, 1, 1, 1.0, 1.0, 1, 1, None) == scivr.SCIVR_EINVAL
     assert scivr._lib.scivr_mlp_adamw(None, 1, 1, 1, 1, 1e-3, 0.9, 0.999, 1e-8, 0.0, None) == scivr.SCIVR_EINVAL
     assert scivr._lib.scivr_pes_eval(None, 4, 1, 0, 1, None, None, None) == scivr.SCIVR_EINVAL
+
+
+def test_plain_scivr_spectrum_arguments_validated(lib):
+    from paper_1312_4698_gb300 import scivr
+    fake = 0x1000
+    cases = [dict(n_E=1), dict(E_min=1.0, E_max=0.5), dict(amp_ld=5), dict(n_steps=0), dict(n_traj=0),
+             dict(dt=-1.0), dict(amp=fake + 8), dict(good=None), dict(I_out=None), dict(C_out=fake + 8)]
+    for over in cases:
+        a = dict(amp=fake, amp_ld=11, good=fake, n_traj=4, n_steps=10, dt=10.0, E_min=0.0, E_max=0.1, n_E=16,
+                 I_out=fake, C_out=None)
+        a.update(over)
+        rc = scivr._lib.scivr_spectrum_hk(a["amp"], a["amp_ld"], a["good"], a["n_traj"], a["n_steps"], a["dt"],
+                                          a["E_min"], a["E_max"], a["n_E"], a["I_out"], a["C_out"], None, None)
+        assert rc == scivr.SCIVR_EINVAL, over
