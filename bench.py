@@ -89,12 +89,13 @@ def propagate_flops_per_traj_step(F: int, n3: int, n4: int) -> float:
 
 def propagate_flops_split(F: int, n3: int, n4: int):
     """(bulk, fp64-kept) split of propagate_flops_per_traj_step: in the mixed path
-    the bulk (potential, monodromy, det M, building A) runs in FP32 and the rest
-    (p, q, S updates, det A, phase, amplitude) in FP64."""
+    the bulk (potential, monodromy, det M, building A, det A) runs in FP32 and the
+    rest (p, q, S updates, continuous phase, amplitude) in FP64."""
     P = F * (F + 1) // 2
     pes = 2 * (P + (P * F if n3 else 0) + (P * P if n4 else 0) + 4 * P) + 6 * F
-    bulk = 3 * (pes + 2 * (2 * F * F * F)) + 4 * (2 * 2 * F * F) + (2.0 / 3.0) * (2 * F) ** 3 + 6 * F * F
-    kept = 3 * (2 * F + 2) + 4 * (2 * F + 2 * F) + (8.0 / 3.0) * F ** 3 + 30 + 10 * F + 30
+    bulk = (3 * (pes + 2 * (2 * F * F * F)) + 4 * (2 * 2 * F * F) + (2.0 / 3.0) * (2 * F) ** 3 + 6 * F * F
+            + (8.0 / 3.0) * F ** 3)
+    kept = 3 * (2 * F + 2) + 4 * (2 * F + 2 * F) + 30 + 10 * F + 30
     return bulk, kept
 
 

@@ -10,16 +10,18 @@
 //     over the group; the tensors T3/T4 live in shared memory.  det M is an
 //     LU over the group's columns (pivot and multipliers by warp shuffle).
 //     The Herman-Kluk matrix A of the step is written to shared memory.
-//   phase 2 (once per G steps, job-parallel, FP64): lane j takes job j =
-//     (trajectory j / G, step j % G) and computes det A and its argument.
+//   phase 2 (once per G steps, job-parallel): lane j takes job j =
+//     (trajectory j / G, step j % G) and computes det A and its argument
+//     (FP64 path: FP64 LU in registers; mixed path: FP32 LU in place in
+//     shared memory, the entries being FP32 already).
 //   phase 3: the continuous phase, a segmented prefix sum over each group.
 //   phase 4 (job-parallel, FP64): overlap <chi|p q>, action, phase and the
 //     amplitude; each group writes G consecutive samples of its row.
 //
-// Real = float is the mixed-precision path: monodromy, potential, det M, A
-// and each step's action increment in FP32; positions, momenta, the
-// accumulated action, det A and the continuous phase in FP64; the amplitude's
-// phase is reduced modulo 2 pi in FP64 and its sine, cosine and magnitude are
+// Real = float is the mixed-precision path: monodromy, potential, det M, A,
+// det A and each step's action increment in FP32; positions, momenta, the
+// accumulated action and the continuous phase in FP64; the amplitude's phase
+// is reduced modulo 2 pi in FP64 and its sine, cosine and magnitude are
 // evaluated in FP32.  Real = double is the same schedule in FP64 throughout.
 //
 // On GB300 a warp-wide FP64 instruction holds a sub-partition's FP64 pipe for
@@ -198,7 +200,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     Real stab = Real(0);
     double detM_last = 1.0;
     double theta_last = 0.0, arg_last = 0.0;
-    double2 detA_last = make_double2(1.0, 0.0);
+    double2 detA_last = make_double2(1.0, 0.0);   // FP64 path
+    double lnAbs_last = 0.0;                      // mixed path: ln |det A| of the last step
 
     // amplitude at c = 0 (M = I, S = 0, theta = 0): lane 0 of each group
     if (g == 0 && active) {
@@ -399,11 +402,70 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             if (bad_bits & gmask) good = false;
         }
         __syncwarp();
-        // ---------------- phase 2: det A per job (FP64) ----------------
+        // ---------------- phase 2: det A per job ----------------
         const int jc = g;                 // this lane's job: trajectory t, step step0 + jc + 1
         const bool jvalid = jc < cnt;
-        double2 detA = make_double2(1.0, 0.0);
-        {
+        double argA;                      // arg det A of this lane's job (principal value)
+        double lnAbsA = 0.0;              // ln |det A| (mixed path always; FP64 path for the HK summand)
+        double2 detA = make_double2(1.0, 0.0);   // FP64 path: det A itself
+        if constexpr (sizeof(Real) == 4) {
+            // Mixed path: the entries of A are FP32 (formed from the FP32 monodromy), so the
+            // complex LU with partial pivoting runs in FP32, in place on this job's column of
+            // the shared array (no per-lane matrix in registers).  ln|det A| = sum ln|pivot|
+            // and the unit phasor prod pivot/|pivot| (sign flipped per row exchange) keep the
+            // result free of FP32 overflow whatever the size of the entries.
+            auto at = [&](int e) -> R2 & { return sh.A[e][jswz(e, ln)]; };
+            float ur = 1.0f, ui = 0.0f, lsum = 0.0f;
+#pragma unroll
+            for (int k = 0; k < F; ++k) {
+                int piv = k;
+                float best;
+                {
+                    const R2 v = at(k * F + k);
+                    best = fmaf(v.x, v.x, v.y * v.y);
+                }
+#pragma unroll
+                for (int i = k + 1; i < F; ++i) {
+                    const R2 v = at(i * F + k);
+                    const float m = fmaf(v.x, v.x, v.y * v.y);
+                    if (m > best) { best = m; piv = i; }
+                }
+                R2 prow[F];
+#pragma unroll
+                for (int cc = k; cc < F; ++cc) prow[cc] = at(piv * F + cc);
+                if (piv != k) {
+#pragma unroll
+                    for (int cc = k; cc < F; ++cc) at(piv * F + cc) = at(k * F + cc);
+                    ur = -ur;
+                    ui = -ui;
+                }
+                const R2 pk = prow[k];
+                const float m = fmaf(pk.x, pk.x, pk.y * pk.y);
+                lsum += __logf(m);
+                const float rn = rsqrtf(m);
+                const float nr = fmaf(ur, pk.x * rn, -ui * (pk.y * rn));
+                const float ni = fmaf(ur, pk.y * rn, ui * (pk.x * rn));
+                ur = nr;
+                ui = ni;
+                const float rm = __frcp_rn(m);
+                const float ir = pk.x * rm, ii = -pk.y * rm;   // 1 / pivot
+#pragma unroll
+                for (int i = k + 1; i < F; ++i) {
+                    const R2 aik = at(i * F + k);
+                    const float lr = fmaf(aik.x, ir, -aik.y * ii);
+                    const float li = fmaf(aik.x, ii, aik.y * ir);
+#pragma unroll
+                    for (int cc = k + 1; cc < F; ++cc) {
+                        R2 a = at(i * F + cc);
+                        a.x = fmaf(-lr, prow[cc].x, fmaf(li, prow[cc].y, a.x));
+                        a.y = fmaf(-lr, prow[cc].y, fmaf(-li, prow[cc].x, a.y));
+                        at(i * F + cc) = a;
+                    }
+                }
+            }
+            argA = (double)atan2f(ui, ur);
+            lnAbsA = 0.5 * (double)lsum;
+        } else {
             double Ar[F][F], Ai[F][F];
 #pragma unroll
             for (int a = 0; a < F; ++a)
@@ -451,11 +513,13 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 }
             }
             detA = make_double2(dr, di);
+            argA = atan2(di, dr);
+            if (A.amplitude == SCIVR_AMP_HK) lnAbsA = log(hypot(dr, di));
         }
         // Herman-Kluk summand: log |det A|^{1/2}, the only part of det A phase 4 needs
-        if (A.amplitude == SCIVR_AMP_HK) sh.lnA[ln] = 0.5 * log(hypot(detA.x, detA.y));
+        if (A.amplitude == SCIVR_AMP_HK) sh.lnA[ln] = 0.5 * lnAbsA;
         // ---------------- phase 3: continuous phase (segmented scan) ----------------
-        const double arg = atan2(detA.y, detA.x);
+        const double arg = argA;
         double arg_prev = __shfl_up_sync(FULL, arg, 1, G);
         if (g == 0) arg_prev = arg_last;
         double d = arg - arg_prev + A.ref_step;
@@ -470,8 +534,12 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         const int lastlane = base + cnt - 1;
         theta_last = __shfl_sync(FULL, theta, lastlane);
         arg_last = __shfl_sync(FULL, arg, lastlane);
-        detA_last.x = __shfl_sync(FULL, detA.x, lastlane);
-        detA_last.y = __shfl_sync(FULL, detA.y, lastlane);
+        if constexpr (sizeof(Real) == 4) {
+            lnAbs_last = __shfl_sync(FULL, lnAbsA, lastlane);
+        } else {
+            detA_last.x = __shfl_sync(FULL, detA.x, lastlane);
+            detA_last.y = __shfl_sync(FULL, detA.y, lastlane);
+        }
         if (!isfinite(theta_last)) good = false;
         // ---------------- phase 4: amplitudes (FP64, job-parallel) ----------------
         if (jvalid && active) {
@@ -524,7 +592,15 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         if (fo.theta) fo.theta[jl] = theta_last;
         if (fo.detM) fo.detM[jl] = detM_last;
         if (fo.stab) fo.stab[jl] = (double)stab;
-        if (fo.detA) { fo.detA[2 * jl] = detA_last.x; fo.detA[2 * jl + 1] = detA_last.y; }
+        if constexpr (sizeof(Real) == 4) {
+            if (fo.detA) {
+                const double r = exp(lnAbs_last);
+                fo.detA[2 * jl] = r * cos(arg_last);
+                fo.detA[2 * jl + 1] = r * sin(arg_last);
+            }
+        } else {
+            if (fo.detA) { fo.detA[2 * jl] = detA_last.x; fo.detA[2 * jl + 1] = detA_last.y; }
+        }
     }
     if (fo.M && g < N2) {
 #pragma unroll
