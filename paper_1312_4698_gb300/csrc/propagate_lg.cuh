@@ -30,6 +30,7 @@
 #pragma once
 
 #include <math_constants.h>
+#include <cstddef>
 
 #include "scivr_internal.cuh"
 
@@ -74,6 +75,8 @@ struct CtaConst {
     float rgf[F], irgf[F];                 // FP32 copies: conversions occupy the FP64 pipe
     float Df[F], af[F], w2f[F];            // diagonal parameters in FP32
     double Dd[F], ad[F], w2d[F];           // and in FP64
+    float qwf[F], pwf[F];                  // overlap constants in FP32 (mixed path's overlap)
+    float p_eqf[SCIVR_MAX_CHI][F], q_eqf[SCIVR_MAX_CHI][F];
 };
 
 // Real-typed views of the staged constants.
@@ -89,17 +92,83 @@ template <typename Real, int F> __device__ __forceinline__ Real c_w2(const CtaCo
 // over banks, and every row is still a permutation of the 32 jobs.
 __device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & 15); }
 
+// 16-byte vectors of Real for shared-memory loads.
+template <typename Real> struct V16;
+template <> struct V16<float> { using T = float4; static constexpr int N = 4; };
+template <> struct V16<double> { using T = double2; static constexpr int N = 2; };
+
+template <typename Real>
+__device__ __forceinline__ Real vcomp(const typename V16<Real>::T &v, int j)
+{
+    if constexpr (V16<Real>::N == 4) return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+    else return j == 0 ? v.x : v.y;
+}
+
+// Length of a row padded to whole 16-byte vectors.
+template <typename Real>
+__host__ __device__ constexpr int vec_len(int n)
+{
+    return (n + V16<Real>::N - 1) / V16<Real>::N * V16<Real>::N;
+}
+
+// Row stride for rows that different lanes read with 16-byte loads at the same
+// time: whole vectors, an odd number of them, so that the 8 lanes served by one
+// shared-memory wavefront start in 8 different groups of 4 banks.
+template <typename Real>
+__host__ __device__ constexpr int row_stride(int n)
+{
+    return (vec_len<Real>(n) / V16<Real>::N) % 2 == 0 ? vec_len<Real>(n) + V16<Real>::N : vec_len<Real>(n);
+}
+
+// sum_{i < S} a[i] b[i] over 16-byte aligned shared rows (S a multiple of the
+// vector length) with one partial sum per vector lane.
+template <typename Real, int S>
+__device__ __forceinline__ Real dot16(const Real *a, const Real *b)
+{
+    using VT = typename V16<Real>::T;
+    constexpr int N = V16<Real>::N;
+    static_assert(S % N == 0, "padded length");
+    Real acc[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j] = Real(0);
+#pragma unroll
+    for (int i = 0; i < S; i += N) {
+        const VT x = *reinterpret_cast<const VT *>(a + i);
+        const VT y = *reinterpret_cast<const VT *>(b + i);
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = fma(vcomp<Real>(x, j), vcomp<Real>(y, j), acc[j]);
+    }
+    Real r = acc[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) r += acc[j];
+    return r;
+}
+
+// Coupling tensors staged per CTA, transposed so that one potential entry e
+// reads one contiguous row: sT3[e][k] (k < F, stride S3), sT4[e][kl] (kl < P,
+// stride S4), zero-padded.
+template <int F, typename Real>
+struct TensorLayout {
+    static constexpr int P = F * (F + 1) / 2;
+    static constexpr int S3 = row_stride<Real>(F);
+    static constexpr int S4 = row_stride<Real>(P);
+    static constexpr size_t bytes = ((sizeof(Real) * (size_t)(P * S3 + P * S4)) + 15) & ~(size_t)15;
+};
+
 template <int F, int G, typename Real>
 struct WarpShared {
     static constexpr int P = F * (F + 1) / 2;
     static constexpr int T = 32 / G;
-    double qd[T][F];
-    Real qr[T][F];
-    Real qq[T][P];
-    Real gc[T][P];
-    Real H[T][F][F];
+    static constexpr int S3 = TensorLayout<F, Real>::S3;   // q, zero-padded (also the Gc row stride)
+    static constexpr int S4 = TensorLayout<F, Real>::S4;   // pair products q_k q_l, zero-padded
+    static constexpr int SH = vec_len<Real>(F);            // row stride of H (rows read by the whole group)
+    alignas(16) Real qr[T][S3];
+    alignas(16) Real qq[T][S4];
+    alignas(16) Real Gc[T][F][S3];          // gradient coefficients, full symmetric matrix (row a read by mode lane a)
+    alignas(16) Real H[T][F][SH];
     typename Vec2<Real>::T A[F * F][32];   // prefactor matrix per job, entry-major (job column swizzled)
-    double pj[F][32], qj[F][32];           // state per job (for the overlap; job column swizzled)
+    Real pj[F][32], qj[F][32];             // state per job, for the overlap (job column swizzled); FP32
+                                           // in the mixed path, where the overlap is evaluated in FP32
     double Sj[32];                          // action per job
     double lnA[32];                         // log |det A|^{1/2} per job (Herman-Kluk summand only)
     double2 ov0[SCIVR_MAX_CHI][T];          // log <chi|p0 q0> per trajectory (Herman-Kluk summand only)
@@ -121,9 +190,11 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     using Sh = WarpShared<F, G, Real>;
     using R2 = typename Vec2<Real>::T;
 
+    using TL = TensorLayout<F, Real>;
+    constexpr int S3 = TL::S3, S4 = TL::S4;
     Real *sT3 = reinterpret_cast<Real *>(smem_raw);
-    Real *sT4 = sT3 + F * P;
-    size_t off = ((sizeof(Real) * (F * P + P * P)) + 15) & ~(size_t)15;
+    Real *sT4 = sT3 + P * S3;
+    size_t off = TL::bytes;
     CtaConst<F> &cc = *reinterpret_cast<CtaConst<F> *>(smem_raw + off);
     off += (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
     Sh *wsh_all = reinterpret_cast<Sh *>(smem_raw + off);
@@ -136,8 +207,14 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         const Real *g3 = nullptr, *g4 = nullptr;
         if constexpr (sizeof(Real) == 4) { g3 = reinterpret_cast<const Real *>(pes.T3f); g4 = reinterpret_cast<const Real *>(pes.T4f); }
         else { g3 = reinterpret_cast<const Real *>(pes.T3); g4 = reinterpret_cast<const Real *>(pes.T4); }
-        for (int i = threadIdx.x; i < F * P; i += blockDim.x) sT3[i] = use3 ? g3[i] : Real(0);
-        for (int i = threadIdx.x; i < P * P; i += blockDim.x) sT4[i] = use4 ? g4[i] : Real(0);
+        for (int i = threadIdx.x; i < P * S3; i += blockDim.x) {
+            const int e = i / S3, k = i % S3;
+            sT3[i] = (use3 && k < F) ? g3[k * P + e] : Real(0);
+        }
+        for (int i = threadIdx.x; i < P * S4; i += blockDim.x) {
+            const int e = i / S4, kl = i % S4;
+            sT4[i] = (use4 && kl < P) ? g4[kl * P + e] : Real(0);
+        }
     }
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -146,6 +223,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             cc.irg[a] = A.irg[a];
             cc.qw[a] = A.qw[a];
             cc.pw[a] = A.pw[a];
+            cc.qwf[a] = (float)A.qw[a];
+            cc.pwf[a] = (float)A.pw[a];
             cc.rgf[a] = (float)A.rg[a];
             cc.irgf[a] = (float)A.irg[a];
             cc.Dd[a] = pes.D[a];
@@ -161,6 +240,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             for (int a = 0; a < F; ++a) {
                 cc.p_eq[x][a] = x < A.n_chi ? A.p_eq[x * F + a] : 0.0;
                 cc.q_eq[x][a] = x < A.n_chi ? A.q_eq[x * F + a] : 0.0;
+                cc.p_eqf[x][a] = (float)cc.p_eq[x][a];
+                cc.q_eqf[x][a] = (float)cc.q_eq[x][a];
             }
     }
     __syncthreads();
@@ -168,6 +249,14 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
     const int t = ln / G, g = ln % G, base = t * G;
     Sh &sh = wsh_all[warp];
+    {
+        // padding entries of the vector rows are read (multiplied by zero or skipped) but never
+        // written by the step loop: clear the warp's rows once
+        Real *z = &sh.qr[0][0];
+        constexpr int nz = (int)((offsetof(Sh, H) + sizeof(Sh::H) - offsetof(Sh, qr)) / sizeof(Real));
+        for (int i = ln; i < nz; i += 32) z[i] = Real(0);
+        __syncwarp();
+    }
     const int64_t n = L.n_traj;
     const int64_t j_traj = (cta * WARPS + warp) * T + t;
     const bool active = j_traj < n;
@@ -247,10 +336,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 Real rtk;
                 if constexpr (sizeof(Real) == 4) rtk = A.tkick_f[sub]; else rtk = tk;
                 __syncwarp();   // previous kick's readers of qr/H are done
-                if (g < F) {
-                    sh.qd[t][g] = q;
-                    sh.qr[t][g] = (Real)q;
-                }
+                if (g < F) sh.qr[t][g] = (Real)q;
                 __syncwarp();
 #pragma unroll
                 for (int i = 0; i < EPL; ++i) {
@@ -263,15 +349,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 for (int i = 0; i < EPL; ++i) {
                     const int e = g + i * G;
                     if (e < P) {
-                        Real h3 = Real(0), h4 = Real(0);
-                        if (use3) {
-#pragma unroll
-                            for (int k = 0; k < F; ++k) h3 = fma(sT3[k * P + e], sh.qr[t][k], h3);
-                        }
-                        if (use4) {
-#pragma unroll 8
-                            for (int kl = 0; kl < P; ++kl) h4 = fma(sT4[kl * P + e], sh.qq[t][kl], h4);
-                        }
+                        const Real h3 = use3 ? dot16<Real, S3>(sT3 + e * S3, sh.qr[t]) : Real(0);
+                        const Real h4 = use4 ? dot16<Real, S4>(sT4 + e * S4, sh.qq[t]) : Real(0);
                         const int a = ea[i], b = eb[i];
                         Real hd = Real(0);
                         if (a == b) {
@@ -286,7 +365,9 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         const Real h = h3 + h4;
                         sh.H[t][a][b] = h + hd;
                         sh.H[t][b][a] = h + hd;
-                        sh.gc[t][e] = fma(Real(0.5), h3, h4 * Real(1.0 / 3.0));
+                        const Real gce = fma(Real(0.5), h3, h4 * Real(1.0 / 3.0));
+                        sh.Gc[t][a][b] = gce;
+                        sh.Gc[t][b][a] = gce;
                         const Real vc = fma(Real(1.0 / 6.0), h3, h4 * Real(1.0 / 12.0));
                         vpart = fma(a == b ? vc : Real(2) * vc, sh.qq[t][e], vpart);
                     }
@@ -295,12 +376,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 // gradient, p and action (mode lanes)
                 Real vlane = vpart;
                 if (g < F) {
-                    Real gr = Real(0);
-#pragma unroll
-                    for (int b = 0; b < F; ++b) {
-                        const int e = g <= b ? g * F - g * (g - 1) / 2 + (b - g) : b * F - b * (b - 1) / 2 + (g - b);
-                        gr = fma(sh.gc[t][e], sh.qr[t][b], gr);
-                    }
+                    const Real gr = dot16<Real, S3>(sh.Gc[t][g], sh.qr[t]);
                     Real Vd, gd;
                     if (pes.diag_kind == SCIVR_DIAG_MORSE) {
                         const Real Dm = c_D<Real>(cc, g), am = c_a<Real>(cc, g);
@@ -318,13 +394,22 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     vlane += Vd;
                 }
                 dS = fma(-rtk, vlane, dS);
-                // monodromy kick: M_p -= tau H M_q (column lanes)
+                // monodromy kick: M_p -= tau H M_q (column lanes; rows of H by 16-byte broadcast loads)
+                {
+                    using VT = typename V16<Real>::T;
+                    constexpr int NV = V16<Real>::N, SH = Sh::SH;
 #pragma unroll
-                for (int a = 0; a < F; ++a) {
-                    Real acc = Real(0);
+                    for (int a = 0; a < F; ++a) {
+                        Real acc = Real(0);
 #pragma unroll
-                    for (int b = 0; b < F; ++b) acc = fma(sh.H[t][a][b], Mq[b], acc);
-                    Mp[a] = fma(-rtk, acc, Mp[a]);
+                        for (int b0 = 0; b0 < SH; b0 += NV) {
+                            const VT v = *reinterpret_cast<const VT *>(&sh.H[t][a][b0]);
+#pragma unroll
+                            for (int j = 0; j < NV; ++j)
+                                if (b0 + j < F) acc = fma(vcomp<Real>(v, j), Mq[b0 + j], acc);
+                        }
+                        Mp[a] = fma(-rtk, acc, Mp[a]);
+                    }
                 }
             }
             // ---- stability: det M by LU over the group's columns ----
@@ -349,7 +434,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     W[k] = wp;
                     const Real pk = __shfl_sync(FULL, W[k], base + k);
                     det *= (piv != k) ? -pk : pk;
-                    const Real inv = Real(1) / pk;
+                    Real inv;   // correctly rounded 1/pk either way
+                    if constexpr (sizeof(Real) == 4) inv = __frcp_rn(pk); else inv = Real(1) / pk;
 #pragma unroll
                     for (int i = k + 1; i < N2; ++i) {
                         const Real li = __shfl_sync(FULL, W[i], base + k) * inv;
@@ -383,8 +469,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     }
                 }
                 if (g < F) {
-                    sh.pj[g][jswz(g, job)] = p;
-                    sh.qj[g][jswz(g, job)] = q;
+                    sh.pj[g][jswz(g, job)] = pr;   // p did not change since the last kick set pr
+                    sh.qj[g][jswz(g, job)] = (Real)q;
                 }
                 // the step's action increment, summed over the group, joins the FP64 action
 #pragma unroll
@@ -541,39 +627,57 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             detA_last.y = __shfl_sync(FULL, detA.y, lastlane);
         }
         if (!isfinite(theta_last)) good = false;
-        // ---------------- phase 4: amplitudes (FP64, job-parallel) ----------------
+        // ---------------- phase 4: amplitudes (job-parallel) ----------------
         if (jvalid && active) {
             const double S = sh.Sj[ln];
             for (int x = 0; x < A.n_chi; ++x) {
-                double re = 0.0, im = 0.0;
-#pragma unroll
-                for (int a = 0; a < F; ++a) {
-                    const double pa = sh.pj[a][jswz(a, ln)], qa = sh.qj[a][jswz(a, ln)];
-                    const double dq = cc.q_eq[x][a] - qa, dp = cc.p_eq[x][a] - pa;
-                    re = fma(-cc.qw[a] * dq, dq, re);
-                    re = fma(-cc.pw[a] * dp, dp, re);
-                    im = fma(0.5 * (cc.p_eq[x][a] + pa), dq, im);
-                }
-                double ph = im + S + 0.5 * theta;
-                if (A.amplitude == SCIVR_AMP_HK) {
-                    // Herman-Kluk summand: |det A|^{1/2} and the division by <chi|p0 q0>
-                    const double2 o = sh.ov0[x][t];
-                    re = re - o.x + sh.lnA[ln];
-                    ph -= o.y;
-                }
-                double sn, cs, mag;
                 if constexpr (sizeof(Real) == 4) {
+                    // the overlap's exponent and phase are O(1)-O(10) in size: FP32 from the FP32
+                    // state copies; the action and the continuous phase join in FP64, and the
+                    // total phase is reduced modulo 2 pi in FP64 before FP32 sine and cosine
+                    float rf = 0.0f, imf = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < F; ++a) {
+                        const float pa = sh.pj[a][jswz(a, ln)], qa = sh.qj[a][jswz(a, ln)];
+                        const float dq = cc.q_eqf[x][a] - qa, dp = cc.p_eqf[x][a] - pa;
+                        rf = fmaf(-cc.qwf[a] * dq, dq, rf);
+                        rf = fmaf(-cc.pwf[a] * dp, dp, rf);
+                        imf = fmaf(0.5f * (cc.p_eqf[x][a] + pa), dq, imf);
+                    }
+                    double ph = fma(0.5, theta, (double)imf + S);
+                    if (A.amplitude == SCIVR_AMP_HK) {
+                        // Herman-Kluk summand: |det A|^{1/2} and the division by <chi|p0 q0>
+                        const double2 o = sh.ov0[x][t];
+                        rf = (float)((double)rf - o.x + sh.lnA[ln]);
+                        ph -= o.y;
+                    }
                     const double red = fma(-kTwoPi, rint(ph * kInvTwoPi), ph);   // FP64 reduction to [-pi, pi]
                     float sf, cf;
                     sincosf((float)red, &sf, &cf);
-                    sn = sf;
-                    cs = cf;
-                    mag = (double)expf((float)re);
+                    const float mag = expf(rf);
+                    L.amp[x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1] =
+                        make_double2((double)(mag * cf), (double)(mag * sf));
                 } else {
+                    double re = 0.0, im = 0.0;
+#pragma unroll
+                    for (int a = 0; a < F; ++a) {
+                        const double pa = sh.pj[a][jswz(a, ln)], qa = sh.qj[a][jswz(a, ln)];
+                        const double dq = cc.q_eq[x][a] - qa, dp = cc.p_eq[x][a] - pa;
+                        re = fma(-cc.qw[a] * dq, dq, re);
+                        re = fma(-cc.pw[a] * dp, dp, re);
+                        im = fma(0.5 * (cc.p_eq[x][a] + pa), dq, im);
+                    }
+                    double ph = im + S + 0.5 * theta;
+                    if (A.amplitude == SCIVR_AMP_HK) {
+                        const double2 o = sh.ov0[x][t];
+                        re = re - o.x + sh.lnA[ln];
+                        ph -= o.y;
+                    }
+                    double sn, cs;
                     sincos(ph, &sn, &cs);
-                    mag = exp(re);
+                    const double mag = exp(re);
+                    L.amp[x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1] = make_double2(mag * cs, mag * sn);
                 }
-                L.amp[x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1] = make_double2(mag * cs, mag * sn);
             }
         }
         if (!isfinite(sh.Sj[base + cnt - 1])) good = false;
@@ -647,8 +751,7 @@ template <int F, int G, typename Real, int WARPS>
 size_t lg_smem_bytes()
 {
     using namespace lg;
-    constexpr int P = F * (F + 1) / 2;
-    const size_t tensors = ((sizeof(Real) * (F * P + P * P)) + 15) & ~(size_t)15;
+    const size_t tensors = TensorLayout<F, Real>::bytes;
     const size_t consts = (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
     return tensors + consts + WARPS * sizeof(WarpShared<F, G, Real>);
 }
@@ -661,6 +764,9 @@ cudaError_t launch_lg_batch(const PropLaunch *items, const int2 *work, int n_wor
     const size_t bytes = lg_smem_bytes<F, G, Real, WARPS>();
     auto kern = k_propagate_lg_batch<F, G, Real, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    // the largest shared-memory carveout, so that as many CTAs fit as the registers allow
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WARPS, bytes);
@@ -681,6 +787,9 @@ cudaError_t launch_lg(const PropLaunch &L, cudaStream_t s)
     const size_t bytes = lg_smem_bytes<F, G, Real, WARPS>();
     auto kern = k_propagate_lg<F, G, Real, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    // the largest shared-memory carveout, so that as many CTAs fit as the registers allow
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     const int64_t per_cta = (int64_t)WARPS * T;
     const int64_t blocks = (L.n_traj + per_cta - 1) / per_cta;
