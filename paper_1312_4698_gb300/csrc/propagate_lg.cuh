@@ -412,36 +412,45 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     }
                 }
             }
-            // ---- stability: det M by LU over the group's columns ----
+            // ---- stability: det M = det M^T by Gaussian elimination of M^T with partial pivoting ----
+            // Lane c holds column c of M, i.e. row c of M^T.  Stage k picks, among the lanes not
+            // used yet, the one with the largest |M[k][c]| (a butterfly arg-max over the group,
+            // ties to the higher lane), and every other unused lane subtracts its multiple of
+            // the pivot lane's entries below row k.  Lanes are marked used instead of being moved;
+            // the sign of det is the parity of the order in which the lanes were picked, counted
+            // as inversions on the bitmask of unused lanes.
             {
                 Real W[N2];
 #pragma unroll
                 for (int a = 0; a < F; ++a) { W[a] = Mp[a]; W[F + a] = Mq[a]; }
                 Real det = Real(1);
+                unsigned unused = (1u << N2) - 1u;
+                unsigned parity = 0u;
 #pragma unroll
                 for (int k = 0; k < N2; ++k) {
-                    int piv = k;
-                    Real best = fabs(W[k]);
+                    const bool mine = (unused >> g) & 1u;   // false for the idle lanes g >= 2F
+                    float mag;
+                    if constexpr (sizeof(Real) == 4) mag = fabsf(W[k]); else mag = (float)fabs(W[k]);
+                    // non-negative floats order like their bit patterns; the low 5 bits carry the lane
+                    unsigned key = mine ? ((((__float_as_uint(mag) >> 5) + 1u) << 5) | (unsigned)g) : 0u;
 #pragma unroll
-                    for (int i = k + 1; i < N2; ++i)
-                        if (fabs(W[i]) > best) { best = fabs(W[i]); piv = i; }
-                    piv = __shfl_sync(FULL, piv, base + k);
-                    Real wp = W[k];
-#pragma unroll
-                    for (int i = k + 1; i < N2; ++i) wp = (i == piv) ? W[i] : wp;
-#pragma unroll
-                    for (int i = k + 1; i < N2; ++i) W[i] = (i == piv) ? W[k] : W[i];
-                    W[k] = wp;
-                    const Real pk = __shfl_sync(FULL, W[k], base + k);
-                    det *= (piv != k) ? -pk : pk;
+                    for (int o = G / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(FULL, key, o, G));
+                    const int pl = (int)(key & 31u);
+                    const Real pk = __shfl_sync(FULL, W[k], base + pl);
+                    parity ^= (unsigned)__popc(unused & ((1u << pl) - 1u)) & 1u;
+                    unused &= ~(1u << pl);
+                    det *= pk;
                     Real inv;   // correctly rounded 1/pk either way
                     if constexpr (sizeof(Real) == 4) inv = __frcp_rn(pk); else inv = Real(1) / pk;
+                    const Real l = W[k] * inv;
+                    const bool elim = mine && g != pl;
 #pragma unroll
                     for (int i = k + 1; i < N2; ++i) {
-                        const Real li = __shfl_sync(FULL, W[i], base + k) * inv;
-                        if (g > k) W[i] = fma(-li, W[k], W[i]);
+                        const Real wp = __shfl_sync(FULL, W[i], base + pl);
+                        if (elim) W[i] = fma(-l, wp, W[i]);
                     }
                 }
+                if (parity) det = -det;
                 const Real dev = isfinite(det) ? fabs(fma(det, det, Real(-1))) : Real(CUDART_INF);
                 stab = dev > stab ? dev : stab;
                 Real tolr;
