@@ -37,12 +37,17 @@ constexpr int kMaxGroupF = 9;    // lane-group kernels (2F <= 32 lanes)
 // Schedule choice when the caller leaves it to the library: the lane-group
 // kernel keeps every SM busy with few trajectories (it launches G lanes per
 // trajectory); the thread kernel wins in FP64 once there are enough
-// trajectories to fill the GPU with one warp per SM sub-partition.
+// trajectories to fill the GPU with one warp per SM sub-partition.  The FP64
+// crossover was measured on GB300 (400 steps of the F = 3, 6, 9 workloads): the
+// thread kernel's time is flat up to ~16k trajectories while the lane-group
+// time grows linearly, and they meet near 6k (F <= 3), 8.5k (F = 4..6) and 5k
+// (F >= 7) trajectories.
 int choose(int F, int precision, int64_t n_traj)
 {
     if (precision == SCIVR_MIXED) return SCIVR_KERNEL_GROUP;
     if (F > kMaxGroupF) return SCIVR_KERNEL_THREAD;
-    return n_traj >= 16384 ? SCIVR_KERNEL_THREAD : SCIVR_KERNEL_GROUP;
+    const int64_t crossover = F <= 3 ? 6144 : F <= 6 ? 8192 : 5120;
+    return n_traj >= crossover ? SCIVR_KERNEL_THREAD : SCIVR_KERNEL_GROUP;
 }
 
 }  // namespace

@@ -12,8 +12,8 @@
 //     The Herman-Kluk matrix A of the step is written to shared memory.
 //   phase 2 (once per G steps, job-parallel): lane j takes job j =
 //     (trajectory j / G, step j % G) and computes det A and its argument
-//     (FP64 path: FP64 LU in registers; mixed path: FP32 LU in place in
-//     shared memory, the entries being FP32 already).
+//     by an LU in place in shared memory (FP64 path in FP64; mixed path in
+//     FP32, the entries being FP32 already).
 //   phase 3: the continuous phase, a segmented prefix sum over each group.
 //   phase 4 (job-parallel, FP64): overlap <chi|p q>, action, phase and the
 //     amplitude; each group writes G consecutive samples of its row.
@@ -414,8 +414,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             }
             // ---- stability: det M = det M^T by Gaussian elimination of M^T with partial pivoting ----
             // Lane c holds column c of M, i.e. row c of M^T.  Stage k picks, among the lanes not
-            // used yet, the one with the largest |M[k][c]| (a butterfly arg-max over the group,
-            // ties to the higher lane), and every other unused lane subtracts its multiple of
+            // used yet, the one with the largest |M[k][c]| (an arg-max over the group by warp
+            // reduction, ties to the higher lane), and every other unused lane subtracts its multiple of
             // the pivot lane's entries below row k.  Lanes are marked used instead of being moved;
             // the sign of det is the parity of the order in which the lanes were picked, counted
             // as inversions on the bitmask of unused lanes.
@@ -433,9 +433,14 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     if constexpr (sizeof(Real) == 4) mag = fabsf(W[k]); else mag = (float)fabs(W[k]);
                     // non-negative floats order like their bit patterns; the low 5 bits carry the lane
                     unsigned key = mine ? ((((__float_as_uint(mag) >> 5) + 1u) << 5) | (unsigned)g) : 0u;
+                    // one full-warp integer max per group (the other groups' lanes contribute 0)
+                    unsigned kmax = 0u;
 #pragma unroll
-                    for (int o = G / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(FULL, key, o, G));
-                    const int pl = (int)(key & 31u);
+                    for (int tt = 0; tt < T; ++tt) {
+                        const unsigned r = __reduce_max_sync(FULL, t == tt ? key : 0u);
+                        kmax = (t == tt) ? r : kmax;
+                    }
+                    const int pl = (int)(kmax & 31u);
                     const Real pk = __shfl_sync(FULL, W[k], base + pl);
                     parity ^= (unsigned)__popc(unused & ((1u << pl) - 1u)) & 1u;
                     unused &= ~(1u << pl);
@@ -561,49 +566,50 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             argA = (double)atan2f(ui, ur);
             lnAbsA = 0.5 * (double)lsum;
         } else {
-            double Ar[F][F], Ai[F][F];
-#pragma unroll
-            for (int a = 0; a < F; ++a)
-#pragma unroll
-                for (int b = 0; b < F; ++b) {
-                    const R2 v = sh.A[a * F + b][jswz(a * F + b, ln)];
-                    Ar[a][b] = (double)v.x;
-                    Ai[a][b] = (double)v.y;
-                }
+            // FP64 path: the same in-place elimination in FP64, with det A as the product of
+            // the pivots (no range concern in FP64)
+            auto at = [&](int e) -> R2 & { return sh.A[e][jswz(e, ln)]; };
             double dr = 1.0, di = 0.0;
 #pragma unroll
             for (int k = 0; k < F; ++k) {
                 int piv = k;
-                double best = Ar[k][k] * Ar[k][k] + Ai[k][k] * Ai[k][k];
-#pragma unroll
-                for (int i = k + 1; i < F; ++i) {
-                    const double v = Ar[i][k] * Ar[i][k] + Ai[i][k] * Ai[i][k];
-                    if (v > best) { best = v; piv = i; }
+                double best;
+                {
+                    const R2 v = at(k * F + k);
+                    best = v.x * v.x + v.y * v.y;
                 }
 #pragma unroll
                 for (int i = k + 1; i < F; ++i) {
-                    if (i == piv) {
-#pragma unroll
-                        for (int cc = k; cc < F; ++cc) {
-                            double tr = Ar[k][cc]; Ar[k][cc] = Ar[i][cc]; Ar[i][cc] = tr;
-                            double ti = Ai[k][cc]; Ai[k][cc] = Ai[i][cc]; Ai[i][cc] = ti;
-                        }
-                    }
+                    const R2 v = at(i * F + k);
+                    const double m = v.x * v.x + v.y * v.y;
+                    if (m > best) { best = m; piv = i; }
                 }
-                if (piv != k) { dr = -dr; di = -di; }
-                const double kr = Ar[k][k], ki = Ai[k][k];
+                R2 prow[F];
+#pragma unroll
+                for (int cc = k; cc < F; ++cc) prow[cc] = at(piv * F + cc);
+                if (piv != k) {
+#pragma unroll
+                    for (int cc = k; cc < F; ++cc) at(piv * F + cc) = at(k * F + cc);
+                    dr = -dr;
+                    di = -di;
+                }
+                const double kr = prow[k].x, ki = prow[k].y;
                 const double nr = fma(dr, kr, -di * ki), ni = fma(dr, ki, di * kr);
-                dr = nr; di = ni;
+                dr = nr;
+                di = ni;
                 const double rr = recip64(fma(kr, kr, ki * ki));
                 const double ir = kr * rr, ii = -ki * rr;
 #pragma unroll
                 for (int i = k + 1; i < F; ++i) {
-                    const double lr = fma(Ar[i][k], ir, -Ai[i][k] * ii);
-                    const double li = fma(Ar[i][k], ii, Ai[i][k] * ir);
+                    const R2 aik = at(i * F + k);
+                    const double lr = fma(aik.x, ir, -aik.y * ii);
+                    const double li = fma(aik.x, ii, aik.y * ir);
 #pragma unroll
                     for (int cc = k + 1; cc < F; ++cc) {
-                        Ar[i][cc] = fma(-lr, Ar[k][cc], fma(li, Ai[k][cc], Ar[i][cc]));
-                        Ai[i][cc] = fma(-lr, Ai[k][cc], fma(-li, Ar[k][cc], Ai[i][cc]));
+                        R2 a = at(i * F + cc);
+                        a.x = fma(-lr, prow[cc].x, fma(li, prow[cc].y, a.x));
+                        a.y = fma(-lr, prow[cc].y, fma(-li, prow[cc].x, a.y));
+                        at(i * F + cc) = a;
                     }
                 }
             }
