@@ -68,9 +68,11 @@ def sized(w8, args):
     return w8.with_(**kw) if kw else w8
 
 
-def describe(w8, precision="fp64", ft="fp64"):
+def describe(w8, precision="fp64", ft="fp64", amplitude="ta"):
+    spec = ("plain Herman-Kluk spectrum (survival amplitude, one-sided transform)" if amplitude == "hk"
+            else f"time-averaged spectrum, Fourier step {ft}")
     return (f"{w8.name}: F={w8.F}, {w8.n_traj} trajectories, {w8.n_steps} steps of {w8.dt} au, "
-            f"{w8.n_E} energies, propagation {precision}, Fourier step {ft}")
+            f"{w8.n_E} energies, propagation {precision}, {spec}")
 
 
 def propagate_flops_per_traj_step(F: int, n3: int, n4: int) -> float:
@@ -179,16 +181,21 @@ def measured_peaks():
         return {}
 
 
-def run_cpu_oracle(w8, n_sample: int, threads: int):
-    """Time the oracle (as it stands) on the first n_sample trajectories of the workload."""
+def run_cpu_oracle(w8, n_sample: int, threads: int, amplitude: str = "ta"):
+    """Time the oracle (as it stands) on the first n_sample trajectories of the workload
+    (amplitude "ta": time-averaged spectrum; "hk": plain Herman-Kluk spectrum)."""
     import oracle
     oracle.build()
     p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, n_sample, w8.seed)
+    hk = amplitude == "hk"
     t0 = time.perf_counter()
     amp, good = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0,
-                                 w8.stab_tol, threads)
+                                 w8.stab_tol, threads, amplitude=oracle.AMP_HK if hk else oracle.AMP_TA)
     t1 = time.perf_counter()
-    oracle.spectrum(amp[0], w, good, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, threads)
+    if hk:
+        oracle.spectrum_hk(amp[0], good, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E)
+    else:
+        oracle.spectrum(amp[0], w, good, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, threads)
     t2 = time.perf_counter()
     used = threads if threads > 0 else oracle.max_threads()
     return dict(seconds=t2 - t0, prop_s=t1 - t0, spec_s=t2 - t1, cores=used,
@@ -216,7 +223,7 @@ def reference_arm(args):
         w8 = sized(workload(args.workload, 0), args)
     times = []
     for i in range(args.warmup + args.steps):
-        r = run_cpu_oracle(w8, n_sample, 0)
+        r = run_cpu_oracle(w8, n_sample, 0, args.amplitude)
         if i >= args.warmup:
             times.append(r)
     sec = sum(t["seconds"] for t in times) / len(times)
@@ -226,7 +233,8 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": describe(w8), "sample": f"{n_sample} of {w8.n_traj} trajectories",
+        "config": {"workload": describe(w8, amplitude=args.amplitude),
+                   "sample": f"{n_sample} of {w8.n_traj} trajectories",
                    "l2": "n/a (host)"},
         "spectra_per_s": value / (w8.n_traj * w8.n_steps),
         "cpu_baseline": {"value": value, "unit": "trajectory-steps/s", "cores": times[0]["cores"],
@@ -694,6 +702,9 @@ def main(argv=None):
     ap.add_argument("--n-traj", type=int, default=None, help="override the workload's trajectory count")
     ap.add_argument("--n-steps", type=int, default=None, help="override the workload's step count")
     ap.add_argument("--n-E", type=int, default=None, help="override the workload's energy count")
+    ap.add_argument("--amplitude", default="ta", choices=["ta", "hk"],
+                    help="ta: time-averaged spectrum (Eq. I(E)_discreto); hk: plain Herman-Kluk SC-IVR "
+                         "spectrum (Eq. I(E)_SCIVR)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -727,8 +738,18 @@ def main(argv=None):
     n = w8.n_traj
 
     prec = PRECISIONS[args.precision]
-    ftm = FT_MODES[args.ft]
+    hk = args.amplitude == "hk"
+    ftm = 0 if hk else FT_MODES[args.ft]
+    amp_mode = scivr.SCIVR_AMP_HK if hk else scivr.SCIVR_AMP_TA
     tol = MIXED_STAB_TOL if prec == 1 else w8.stab_tol
+
+    def spectrum_call():
+        if hk:
+            scivr.scivr_spectrum_hk(bufs.amp[0], K, bufs.good, n, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E,
+                                    bufs.I[0], None, bufs.n_good, stream=stream)
+        else:
+            scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min,
+                                 w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, ft_mode=ftm, stream=stream)
     ev = {k: [] for k in ("prop0", "prop1", "spec1")}
     combined = [None]
 
@@ -738,11 +759,11 @@ def main(argv=None):
         if record:
             e0 = torch.cuda.Event(enable_timing=True); e0.record(stream); ev["prop0"].append(e0)
         scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0, bufs.q0,
-                              bufs.amp, K, bufs.good, precision=prec, stab_tol=tol, stream=stream)
+                              bufs.amp, K, bufs.good, precision=prec, stab_tol=tol, stream=stream,
+                              amplitude=amp_mode)
         if record:
             e1 = torch.cuda.Event(enable_timing=True); e1.record(stream); ev["prop1"].append(e1)
-        scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min,
-                             w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, ft_mode=ftm, stream=stream)
+        spectrum_call()
         if record:
             e2 = torch.cuda.Event(enable_timing=True); e2.record(stream); ev["spec1"].append(e2)
         if world > 1:
@@ -801,9 +822,8 @@ def main(argv=None):
             bufs.w.copy_(hw, non_blocking=True)
             scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0,
                                   bufs.q0, bufs.amp, K, bufs.good, precision=prec, stab_tol=tol,
-                                  stream=stream)
-            scivr.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min,
-                                 w8.E_max, w8.n_E, bufs.I[0], bufs.n_good, ft_mode=ftm, stream=stream)
+                                  stream=stream, amplitude=amp_mode)
+            spectrum_call()
             hI.copy_(bufs.I[0], non_blocking=True)
             hng.copy_(bufs.n_good, non_blocking=True)
         e1.record(stream)
@@ -824,7 +844,9 @@ def main(argv=None):
     value = world * n * w8.n_steps / (ms_per_step * 1e-3)
     prop_avg = float(np.mean(prop_ms))
     spec_avg = float(np.mean(spec_ms))
-    ft_flops = 8.0 * n * K * w8.n_E
+    # time-averaged: 8 N K N_E (complex multiply-add per trajectory, sample and energy);
+    # plain HK: the column sum (2 N K) and the transform of the mean (8 K N_E)
+    ft_flops = (2.0 * n * K + 8.0 * K * w8.n_E) if hk else 8.0 * n * K * w8.n_E
     bulk, kept = propagate_flops_split(w8.F, w8.pes.c3.size, w8.pes.c4.size)
     pr_flops = (bulk + kept) * n * w8.n_steps
     ft_tf = ft_flops / (spec_avg * 1e-3) / 1e12
@@ -867,7 +889,7 @@ def main(argv=None):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        r = run_cpu_oracle(w8, args.cpu_sample, 0)
+        r = run_cpu_oracle(w8, args.cpu_sample, 0, args.amplitude)
         cpu = {"value": r["value"], "unit": "trajectory-steps/s", "cores": r["cores"],
                "kind": "oracle",
                "sample": f"first {args.cpu_sample} of {n} trajectories, all {w8.n_steps} steps and "
@@ -879,7 +901,7 @@ def main(argv=None):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision] + ("" if ftm == 0 else f" + {args.ft} tensor FT"),
         "data": "synthetic",
-        "config": {"workload": describe(w8, args.precision, args.ft), "global_batch": world * n,
+        "config": {"workload": describe(w8, args.precision, args.ft, args.amplitude), "global_batch": world * n,
                    "seed": "base 0 + rank",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); amplitudes "
                          f"({n * K * 16 / 1e9:.2f} GB) exceed L2",
