@@ -19,10 +19,12 @@
 //     amplitude; each group writes G consecutive samples of its row.
 //
 // Real = float is the mixed-precision path: monodromy, potential, det M, A,
-// det A and each step's action increment in FP32; positions, momenta, the
-// accumulated action and the continuous phase in FP64; the amplitude's phase
-// is reduced modulo 2 pi in FP64 and its sine, cosine and magnitude are
-// evaluated in FP32.  Real = double is the same schedule in FP64 throughout.
+// det A, the overlap and each step's action increment in FP32; positions and
+// momenta as FP32 pairs (about 48 significant bits, advanced by error-free
+// transformations); the accumulated action and the continuous phase in FP64;
+// the amplitude's phase is reduced modulo 2 pi in FP64 and its sine, cosine and
+// magnitude are evaluated in FP32.  Real = double is the same schedule in FP64
+// throughout.
 //
 // On GB300 a warp-wide FP64 instruction holds a sub-partition's FP64 pipe for
 // about 64 cycles, so phase 1 keeps FP64 to the state updates (one FMA per
@@ -31,6 +33,7 @@
 
 #include <math_constants.h>
 #include <cstddef>
+#include <type_traits>
 
 #include "scivr_internal.cuh"
 
@@ -61,6 +64,79 @@ __device__ __forceinline__ double recip64(double x)
     r = r * fma(-x, r, 2.0);
     return r;
 }
+
+// A value as the unevaluated sum h + l of two floats (|l| <= ulp(h)/2, about 48
+// significant bits): the mixed path's positions and momenta.  They advance by
+// error-free transformations -- Knuth's two-sum and the FMA form of Dekker's exact
+// product -- so that the per-step loop issues no FP64 instruction; the FP32
+// intrinsics keep the compiler from contracting any of their steps into an FMA.
+struct F2 {
+    float h, l;
+};
+
+__device__ __forceinline__ F2 f2_from_double(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ double f2_to_double(F2 a) { return (double)a.h + (double)a.l; }
+
+// s + err = a.h + b exactly (two-sum), then err absorbs c and the sum is renormalised
+__device__ __forceinline__ F2 f2_add_renorm(float ah, float b, float c)
+{
+    const float s = __fadd_rn(ah, b);
+    const float bb = __fsub_rn(s, ah);
+    float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    err = __fadd_rn(err, c);
+    const float h = __fadd_rn(s, err);
+    return {h, __fsub_rn(err, __fsub_rn(h, s))};
+}
+
+// a + (th + tl) * b
+__device__ __forceinline__ F2 f2_axpy(F2 a, float th, float tl, F2 b)
+{
+    const float x = __fmul_rn(th, b.h);
+    float e = __fmaf_rn(th, b.h, -x);                        // exact error of th * b.h
+    e = __fmaf_rn(th, b.l, __fmaf_rn(tl, b.h, e));           // cross terms (tl * b.l is below the precision)
+    return f2_add_renorm(a.h, x, __fadd_rn(a.l, e));
+}
+
+// a - (th + tl) * g, g a float
+__device__ __forceinline__ F2 f2_sub_scaled(F2 a, float th, float tl, float g)
+{
+    const float x = __fmul_rn(th, g);
+    float e = __fmaf_rn(th, g, -x);
+    e = __fmaf_rn(tl, g, e);
+    return f2_add_renorm(a.h, -x, __fsub_rn(a.l, e));
+}
+
+// Mode state of the two paths: FP64 (Real = double) or FP32 pairs (Real = float).
+__device__ __forceinline__ void drift_q(double &q, const double &p, const PropArgs &A, int sub)
+{
+    q = fma(A.tdrift[sub], p, q);
+}
+__device__ __forceinline__ void drift_q(F2 &q, const F2 &p, const PropArgs &A, int sub)
+{
+    q = f2_axpy(q, A.tdrift_f[sub], A.tdrift_lo[sub], p);
+}
+__device__ __forceinline__ void kick_p(double &p, double force, const PropArgs &A, int sub)
+{
+    p = fma(-A.tkick[sub], force, p);
+}
+__device__ __forceinline__ void kick_p(F2 &p, float force, const PropArgs &A, int sub)
+{
+    p = f2_sub_scaled(p, A.tkick_f[sub], A.tkick_lo[sub], force);
+}
+__device__ __forceinline__ double hi_part(double a) { return a; }
+__device__ __forceinline__ float hi_part(F2 a) { return a.h; }
+__device__ __forceinline__ double as_double(double a) { return a; }
+__device__ __forceinline__ double as_double(F2 a) { return f2_to_double(a); }
+__device__ __forceinline__ bool pq_finite(double a) { return isfinite(a); }
+__device__ __forceinline__ bool pq_finite(F2 a) { return isfinite(a.h) && isfinite(a.l); }
+template <typename PQ> __device__ __forceinline__ PQ pq_from_double(double x);
+template <> __device__ __forceinline__ double pq_from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ F2 pq_from_double<F2>(double x) { return f2_from_double(x); }
 
 template <typename Real> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
@@ -150,7 +226,7 @@ __device__ __forceinline__ Real dot16(const Real *a, const Real *b)
 template <int F, typename Real>
 struct TensorLayout {
     static constexpr int P = F * (F + 1) / 2;
-    static constexpr int S3 = row_stride<Real>(F);
+    static constexpr int S3 = vec_len<Real>(F);   // short rows: fewer loads outweigh a 2-way conflict
     static constexpr int S4 = row_stride<Real>(P);
     static constexpr size_t bytes = ((sizeof(Real) * (size_t)(P * S3 + P * S4)) + 15) & ~(size_t)15;
 };
@@ -275,8 +351,9 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 
     // mode state (lane g < F)
     const int mode = g < F ? g : 0;
-    double p = L.p0[mode * n + jl], q = L.q0[mode * n + jl];
-    Real pr = (Real)p;          // the momentum as seen by the Real-precision bulk
+    using PQ = typename std::conditional<sizeof(Real) == 4, F2, double>::type;
+    PQ p = pq_from_double<PQ>(L.p0[mode * n + jl]), q = pq_from_double<PQ>(L.q0[mode * n + jl]);
+    Real pr = (Real)hi_part(p);   // the momentum as seen by the Real-precision bulk
     double S = 0.0;             // accumulated action (lane 0 of the group holds the total)
     // column state (lane g < 2F): column g of M = d(p,q)/d(p0,q0)
     Real Mp[F], Mq[F];
@@ -324,7 +401,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     Real rt;
                     if constexpr (sizeof(Real) == 4) rt = A.tdrift_f[sub]; else rt = A.tdrift[sub];
                     if (g < F) {
-                        q = fma(A.tdrift[sub], p, q);
+                        drift_q(q, p, A, sub);
                         dS = fma(rt * Real(0.5) * pr, pr, dS);
                     }
 #pragma unroll
@@ -336,7 +413,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 Real rtk;
                 if constexpr (sizeof(Real) == 4) rtk = A.tkick_f[sub]; else rtk = tk;
                 __syncwarp();   // previous kick's readers of qr/H are done
-                if (g < F) sh.qr[t][g] = (Real)q;
+                if (g < F) sh.qr[t][g] = (Real)hi_part(q);
                 __syncwarp();
 #pragma unroll
                 for (int i = 0; i < EPL; ++i) {
@@ -389,8 +466,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         Vd = Real(0.5) * w2 * sh.qr[t][g] * sh.qr[t][g];
                         gd = w2 * sh.qr[t][g];
                     }
-                    p = fma(-tk, (double)(gr + gd), p);
-                    pr = (Real)p;
+                    kick_p(p, gr + gd, A, sub);
+                    pr = (Real)hi_part(p);
                     vlane += Vd;
                 }
                 dS = fma(-rtk, vlane, dS);
@@ -431,8 +508,11 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     const bool mine = (unused >> g) & 1u;   // false for the idle lanes g >= 2F
                     float mag;
                     if constexpr (sizeof(Real) == 4) mag = fabsf(W[k]); else mag = (float)fabs(W[k]);
-                    // non-negative floats order like their bit patterns; the low 5 bits carry the lane
-                    unsigned key = mine ? ((((__float_as_uint(mag) >> 5) + 1u) << 5) | (unsigned)g) : 0u;
+                    // non-negative floats order like their bit patterns; the low 6 bits carry lane + 1
+                    // (so an unused lane's key 0 never wins), at the cost of 6 mantissa bits of the
+                    // comparison
+                    const unsigned key = mine ? ((__float_as_uint(mag) & ~63u) | (unsigned)(g + 1)) : 0u;
+
                     // one full-warp integer max per group (the other groups' lanes contribute 0)
                     unsigned kmax = 0u;
 #pragma unroll
@@ -440,13 +520,13 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         const unsigned r = __reduce_max_sync(FULL, t == tt ? key : 0u);
                         kmax = (t == tt) ? r : kmax;
                     }
-                    const int pl = (int)(kmax & 31u);
+                    const int pl = (int)(kmax & 63u) - 1;
                     const Real pk = __shfl_sync(FULL, W[k], base + pl);
+                    Real inv;   // correctly rounded 1/pk either way
+                    if constexpr (sizeof(Real) == 4) inv = __frcp_rn(pk); else inv = Real(1) / pk;
                     parity ^= (unsigned)__popc(unused & ((1u << pl) - 1u)) & 1u;
                     unused &= ~(1u << pl);
                     det *= pk;
-                    Real inv;   // correctly rounded 1/pk either way
-                    if constexpr (sizeof(Real) == 4) inv = __frcp_rn(pk); else inv = Real(1) / pk;
                     const Real l = W[k] * inv;
                     const bool elim = mine && g != pl;
 #pragma unroll
@@ -484,7 +564,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 }
                 if (g < F) {
                     sh.pj[g][jswz(g, job)] = pr;   // p did not change since the last kick set pr
-                    sh.qj[g][jswz(g, job)] = (Real)q;
+                    sh.qj[g][jswz(g, job)] = (Real)hi_part(q);
                 }
                 // the step's action increment, summed over the group, joins the FP64 action
 #pragma unroll
@@ -497,7 +577,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         }
         {
             // non-finite state persists, so testing once per chunk marks the same trajectories
-            const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(isfinite(p) && isfinite(q)));
+            const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(pq_finite(p) && pq_finite(q)));
             const unsigned gmask = (G == 32 ? FULL : (((1u << G) - 1u) << base));
             if (bad_bits & gmask) good = false;
         }
@@ -703,8 +783,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     if (g == 0) L.good[jl] = good ? 1 : 0;
     const FinalDev &fo = L.fin;
     if (g < F) {
-        if (fo.p) fo.p[g * n + jl] = p;
-        if (fo.q) fo.q[g * n + jl] = q;
+        if (fo.p) fo.p[g * n + jl] = as_double(p);
+        if (fo.q) fo.q[g * n + jl] = as_double(q);
     }
     if (g == 0) {
         if (fo.S) fo.S[jl] = sh.Sj[base + ((A.n_steps - 1) % C)];
