@@ -351,6 +351,14 @@ def test_mixed_propagate_close_to_oracle(G, F):
     e_det = np.max(np.abs(g["detM"][sel] - rf["detM"][sel]))
     print(f"F={F}: max |det M (mixed) - det M (FP64)| = {e_det:.2e}")
     assert e_det < 1e-2
+    # final positions and momenta (FP32-pair state driven by FP32 forces), in the
+    # dimensionless units sqrt(gamma) q and p / sqrt(gamma); measured 8e-6 (F = 2) to
+    # 1.1e-4 (F = 3) over 400 steps
+    rg_ = np.sqrt(w8.gamma)[:, None]
+    e_q = np.max(np.abs((g["q"] - rf["q"].T) * rg_)[:, sel])
+    e_p = np.max(np.abs((g["p"] - rf["p"].T) / rg_)[:, sel])
+    print(f"F={F}: max final-state deviation q {e_q:.2e}, p {e_p:.2e}")
+    assert e_q < 1e-3 and e_p < 1e-3
 
 
 def test_mixed_spectrum_peaks_within_1cm(G):
@@ -380,3 +388,70 @@ def test_mixed_spectrum_peaks_within_1cm(G):
     assert len(pr) > 0 and len(pr) == len(pg)
     assert np.max(np.abs(pr - pg)) <= 1.0
     assert np.max(np.abs(gi - ri)) <= 2e-2 * np.max(ri)
+
+
+def test_default_configuration_full_size_sampled(G):
+    """The configuration bench.py times by default, at its full size and launch shape:
+    F=6 workload (16384 trajectories, 4000 steps, 4000 energies), mixed propagation,
+    tensor-core bf16x3 Fourier step.
+
+    * 24 sampled amplitude rows (the ragged last one included) against the FP64 oracle,
+      to the mixed bound of 5e-2 of each row's largest amplitude;
+    * the full-set spectrum of the tensor-core step against the FP64 Fourier step on
+      the same device amplitudes (itself parity-tested to 1e-9), to the bf16x3 bound;
+    * the sample's spectrum (oracle flags as the good mask) against the oracle's: within
+      3e-2 of its maximum, and every oracle peak above 10 % of the maximum has a GPU peak
+      within 1 cm^-1 (24 trajectories give small side peaks near any count threshold, so
+      peaks are matched rather than counted)."""
+    import torch
+    from tests.test_gpu_tc import TOL
+    w8 = wl.config_f6()
+    n, K = w8.n_traj, w8.n_steps + 1
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, n, w8.seed)
+    pes = G.scivr_create_pes(w8.pes)
+    bufs = G.alloc_buffers(w8, n_traj=n)
+    bufs.p0.copy_(_t(p0))
+    bufs.q0.copy_(_t(q0))
+    bufs.w.copy_(_t(w))
+    G.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0, bufs.q0, bufs.amp, K,
+                      bufs.good, precision=G.SCIVR_MIXED, stab_tol=MIXED_STAB_TOL)
+    I_tc = torch.empty(w8.n_E, dtype=torch.float64, device="cuda")
+    I_64 = torch.empty_like(I_tc)
+    ng = torch.zeros(1, dtype=torch.int64, device="cuda")
+    G.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, I_tc,
+                     ng, ft_mode=G.SCIVR_FT_TC_BF16X3)
+    G.scivr_spectrum(bufs.amp[0], K, bufs.w, bufs.good, n, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, I_64,
+                     ng)
+    torch.cuda.synchronize()
+    assert G.scivr_check_status() == G.SCIVR_OK
+    gg = bufs.good.cpu().numpy()
+    assert gg.mean() > 0.99
+    e_tc = np.max(np.abs(I_tc.cpu().numpy() - I_64.cpu().numpy())) / np.max(np.abs(I_64.cpu().numpy()))
+    print(f"full set: bf16x3 vs FP64 Fourier step rel err {e_tc:.2e}")
+    assert e_tc <= TOL[2]
+    idx = np.sort(np.random.default_rng(1).choice(n, 24, replace=False))
+    idx[-1] = n - 1
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0[:, idx], q0[:, idx])
+    ga = bufs.amp[0, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    ga = ga[..., 0] + 1j * ga[..., 1]
+    sel = rg.astype(bool) & gg[idx].astype(bool)
+    assert sel.sum() >= 22
+    e_amp = amp_err(ga[None][:, sel], ra[:, sel], np.ones(sel.sum(), np.uint8))
+    print(f"sampled rows: mixed vs FP64 oracle max error {e_amp:.2e}")
+    assert e_amp < 5e-2
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    mask[torch.as_tensor(idx, device="cuda")] = _t(rg)
+    I_s = torch.empty_like(I_tc)
+    G.scivr_spectrum(bufs.amp[0], K, bufs.w, mask, n, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E, I_s, ng,
+                     ft_mode=G.SCIVR_FT_TC_BF16X3)
+    torch.cuda.synchronize()
+    ri, _ = oracle.spectrum(ra[0], w[idx], rg, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E)
+    gs = I_s.cpu().numpy()
+    e_s = np.max(np.abs(gs - ri)) / np.max(ri)
+    E = w8.energies()
+    pr = wl.to_cm1(cf.find_peaks(E, ri, 0.1))
+    pg = wl.to_cm1(cf.find_peaks(E, gs, 0.02))
+    shift = np.array([np.min(np.abs(pg - x)) for x in pr])
+    print(f"sample spectrum: rel err {e_s:.2e}; {len(pr)} peaks, max shift {shift.max():.3f} cm^-1")
+    assert e_s <= 3e-2
+    assert len(pr) > 0 and shift.max() <= 1.0
