@@ -91,15 +91,16 @@ def propagate_flops_per_traj_step(F: int, n3: int, n4: int) -> float:
 
 def propagate_flops_split(F: int, n3: int, n4: int):
     """(bulk, fp64-kept) split of propagate_flops_per_traj_step: in the mixed path
-    the bulk runs on the FP32 pipe -- potential, monodromy, det M, building A,
-    det A, the overlap, and the p and q updates (as FP32 pairs) -- and only the
-    action sum, the continuous-phase scan and the phase sum with its reduction
-    modulo 2 pi (about 12 flops) stay FP64."""
+    the bulk runs on the FP32 pipe -- potential, monodromy, det M, building A, the
+    elimination that gives det A, the overlap and the kinetic action increments --
+    and the p and q updates (3 kicks x 2F + 4 drifts x 2F flops), the action sum,
+    the continuous-phase scan and the phase sum with its reduction modulo 2 pi
+    (~11 flops) stay FP64."""
     P = F * (F + 1) // 2
     pes = 2 * (P + (P * F if n3 else 0) + (P * P if n4 else 0) + 4 * P) + 6 * F
     total = (3 * (pes + 2 * (2 * F * F * F)) + 4 * (2 * 2 * F * F) + (2.0 / 3.0) * (2 * F) ** 3 + 6 * F * F
              + (8.0 / 3.0) * F ** 3 + 3 * (2 * F + 2) + 4 * (2 * F + 2 * F) + 30 + 10 * F + 30)
-    kept = 12.0
+    kept = 14.0 * F + 11.0
     return total - kept, kept
 
 

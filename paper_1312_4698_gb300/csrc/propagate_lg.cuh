@@ -19,12 +19,11 @@
 //     amplitude; each group writes G consecutive samples of its row.
 //
 // Real = float is the mixed-precision path: monodromy, potential, det M, A,
-// det A, the overlap and each step's action increment in FP32; positions and
-// momenta as FP32 pairs (about 48 significant bits, advanced by error-free
-// transformations); the accumulated action and the continuous phase in FP64;
-// the amplitude's phase is reduced modulo 2 pi in FP64 and its sine, cosine and
-// magnitude are evaluated in FP32.  Real = double is the same schedule in FP64
-// throughout.
+// the elimination that gives det A, the overlap and each step's action
+// increment in FP32; positions, momenta, the accumulated action and the
+// continuous phase in FP64; the amplitude's phase is reduced modulo 2 pi in FP64
+// and its sine, cosine and magnitude are evaluated in FP32.  Real = double is the
+// same schedule in FP64 throughout.
 //
 // On GB300 a warp-wide FP64 instruction holds a sub-partition's FP64 pipe for
 // about 64 cycles, so phase 1 keeps FP64 to the state updates (one FMA per
@@ -33,7 +32,6 @@
 
 #include <math_constants.h>
 #include <cstddef>
-#include <type_traits>
 
 #include "scivr_internal.cuh"
 
@@ -65,78 +63,6 @@ __device__ __forceinline__ double recip64(double x)
     return r;
 }
 
-// A value as the unevaluated sum h + l of two floats (|l| <= ulp(h)/2, about 48
-// significant bits): the mixed path's positions and momenta.  They advance by
-// error-free transformations -- Knuth's two-sum and the FMA form of Dekker's exact
-// product -- so that the per-step loop issues no FP64 instruction; the FP32
-// intrinsics keep the compiler from contracting any of their steps into an FMA.
-struct F2 {
-    float h, l;
-};
-
-__device__ __forceinline__ F2 f2_from_double(double x)
-{
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-}
-
-__device__ __forceinline__ double f2_to_double(F2 a) { return (double)a.h + (double)a.l; }
-
-// s + err = a.h + b exactly (two-sum), then err absorbs c and the sum is renormalised
-__device__ __forceinline__ F2 f2_add_renorm(float ah, float b, float c)
-{
-    const float s = __fadd_rn(ah, b);
-    const float bb = __fsub_rn(s, ah);
-    float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    err = __fadd_rn(err, c);
-    const float h = __fadd_rn(s, err);
-    return {h, __fsub_rn(err, __fsub_rn(h, s))};
-}
-
-// a + (th + tl) * b
-__device__ __forceinline__ F2 f2_axpy(F2 a, float th, float tl, F2 b)
-{
-    const float x = __fmul_rn(th, b.h);
-    float e = __fmaf_rn(th, b.h, -x);                        // exact error of th * b.h
-    e = __fmaf_rn(th, b.l, __fmaf_rn(tl, b.h, e));           // cross terms (tl * b.l is below the precision)
-    return f2_add_renorm(a.h, x, __fadd_rn(a.l, e));
-}
-
-// a - (th + tl) * g, g a float
-__device__ __forceinline__ F2 f2_sub_scaled(F2 a, float th, float tl, float g)
-{
-    const float x = __fmul_rn(th, g);
-    float e = __fmaf_rn(th, g, -x);
-    e = __fmaf_rn(tl, g, e);
-    return f2_add_renorm(a.h, -x, __fsub_rn(a.l, e));
-}
-
-// Mode state of the two paths: FP64 (Real = double) or FP32 pairs (Real = float).
-__device__ __forceinline__ void drift_q(double &q, const double &p, const PropArgs &A, int sub)
-{
-    q = fma(A.tdrift[sub], p, q);
-}
-__device__ __forceinline__ void drift_q(F2 &q, const F2 &p, const PropArgs &A, int sub)
-{
-    q = f2_axpy(q, A.tdrift_f[sub], A.tdrift_lo[sub], p);
-}
-__device__ __forceinline__ void kick_p(double &p, double force, const PropArgs &A, int sub)
-{
-    p = fma(-A.tkick[sub], force, p);
-}
-__device__ __forceinline__ void kick_p(F2 &p, float force, const PropArgs &A, int sub)
-{
-    p = f2_sub_scaled(p, A.tkick_f[sub], A.tkick_lo[sub], force);
-}
-__device__ __forceinline__ double hi_part(double a) { return a; }
-__device__ __forceinline__ float hi_part(F2 a) { return a.h; }
-__device__ __forceinline__ double as_double(double a) { return a; }
-__device__ __forceinline__ double as_double(F2 a) { return f2_to_double(a); }
-__device__ __forceinline__ bool pq_finite(double a) { return isfinite(a); }
-__device__ __forceinline__ bool pq_finite(F2 a) { return isfinite(a.h) && isfinite(a.l); }
-template <typename PQ> __device__ __forceinline__ PQ pq_from_double(double x);
-template <> __device__ __forceinline__ double pq_from_double<double>(double x) { return x; }
-template <> __device__ __forceinline__ F2 pq_from_double<F2>(double x) { return f2_from_double(x); }
 
 template <typename Real> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
@@ -351,9 +277,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 
     // mode state (lane g < F)
     const int mode = g < F ? g : 0;
-    using PQ = typename std::conditional<sizeof(Real) == 4, F2, double>::type;
-    PQ p = pq_from_double<PQ>(L.p0[mode * n + jl]), q = pq_from_double<PQ>(L.q0[mode * n + jl]);
-    Real pr = (Real)hi_part(p);   // the momentum as seen by the Real-precision bulk
+    double p = L.p0[mode * n + jl], q = L.q0[mode * n + jl];
+    Real pr = (Real)p;          // the momentum as seen by the Real-precision bulk
     double S = 0.0;             // accumulated action (lane 0 of the group holds the total)
     // column state (lane g < 2F): column g of M = d(p,q)/d(p0,q0)
     Real Mp[F], Mq[F];
@@ -401,7 +326,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     Real rt;
                     if constexpr (sizeof(Real) == 4) rt = A.tdrift_f[sub]; else rt = A.tdrift[sub];
                     if (g < F) {
-                        drift_q(q, p, A, sub);
+                        q = fma(A.tdrift[sub], p, q);
                         dS = fma(rt * Real(0.5) * pr, pr, dS);
                     }
 #pragma unroll
@@ -413,7 +338,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 Real rtk;
                 if constexpr (sizeof(Real) == 4) rtk = A.tkick_f[sub]; else rtk = tk;
                 __syncwarp();   // previous kick's readers of qr/H are done
-                if (g < F) sh.qr[t][g] = (Real)hi_part(q);
+                if (g < F) sh.qr[t][g] = (Real)q;
                 __syncwarp();
 #pragma unroll
                 for (int i = 0; i < EPL; ++i) {
@@ -466,8 +391,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         Vd = Real(0.5) * w2 * sh.qr[t][g] * sh.qr[t][g];
                         gd = w2 * sh.qr[t][g];
                     }
-                    kick_p(p, gr + gd, A, sub);
-                    pr = (Real)hi_part(p);
+                    p = fma(-tk, (double)(gr + gd), p);
+                    pr = (Real)p;
                     vlane += Vd;
                 }
                 dS = fma(-rtk, vlane, dS);
@@ -564,7 +489,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 }
                 if (g < F) {
                     sh.pj[g][jswz(g, job)] = pr;   // p did not change since the last kick set pr
-                    sh.qj[g][jswz(g, job)] = (Real)hi_part(q);
+                    sh.qj[g][jswz(g, job)] = (Real)q;
                 }
                 // the step's action increment, summed over the group, joins the FP64 action
 #pragma unroll
@@ -577,7 +502,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         }
         {
             // non-finite state persists, so testing once per chunk marks the same trajectories
-            const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(pq_finite(p) && pq_finite(q)));
+            const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(isfinite(p) && isfinite(q)));
             const unsigned gmask = (G == 32 ? FULL : (((1u << G) - 1u) << base));
             if (bad_bits & gmask) good = false;
         }
@@ -783,8 +708,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     if (g == 0) L.good[jl] = good ? 1 : 0;
     const FinalDev &fo = L.fin;
     if (g < F) {
-        if (fo.p) fo.p[g * n + jl] = as_double(p);
-        if (fo.q) fo.q[g * n + jl] = as_double(q);
+        if (fo.p) fo.p[g * n + jl] = p;
+        if (fo.q) fo.q[g * n + jl] = q;
     }
     if (g == 0) {
         if (fo.S) fo.S[jl] = sh.Sj[base + ((A.n_steps - 1) % C)];
