@@ -119,6 +119,24 @@ __device__ __forceinline__ void pes_fp64(const PesDev &pes, const double (&q)[F]
         for (int b = a + 1; b < F; ++b) H[b][a] = H[a][b];
 }
 
+// Magnitude key of a double for pivot searches: the high word of |x|, an integer
+// whose order is that of |x| up to its low 32 mantissa bits.  Comparing keys keeps
+// the searches off the FP64 pipe (double comparisons execute there on GB300).
+__device__ __forceinline__ int mag_key(double x) { return __double2hiint(x) & 0x7fffffff; }
+
+// 1/x in FP64 from the FP32 reciprocal refined by two Newton steps (the error
+// squares each step: 2^-23 -> 2^-46 -> below FP64 rounding); FP64 division
+// outside the FP32 exponent range.
+__device__ __forceinline__ double recip_fp64(double x)
+{
+    const double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double r = (double)__frcp_rn((float)x);
+    r = r * fma(-x, r, 2.0);
+    r = r * fma(-x, r, 2.0);
+    return r;
+}
+
 // Determinant by LU with partial pivoting (row swaps as predicated moves).
 template <int N>
 __device__ __forceinline__ double det_real(double (&W)[N][N])
@@ -127,10 +145,10 @@ __device__ __forceinline__ double det_real(double (&W)[N][N])
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         int piv = k;
-        double best = fabs(W[k][k]);
+        int best = mag_key(W[k][k]);
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {
-            const double v = fabs(W[i][k]);
+            const int v = mag_key(W[i][k]);
             if (v > best) { best = v; piv = i; }
         }
 #pragma unroll
@@ -145,7 +163,7 @@ __device__ __forceinline__ double det_real(double (&W)[N][N])
         if (piv != k) det = -det;
         const double akk = W[k][k];
         det *= akk;
-        const double inv = 1.0 / akk;
+        const double inv = recip_fp64(akk);
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {
             const double l = W[i][k] * inv;
@@ -162,11 +180,12 @@ __device__ __forceinline__ cplx det_complex(cplx (&A)[N][N])
     cplx det = {1.0, 0.0};
 #pragma unroll
     for (int k = 0; k < N; ++k) {
+        // pivot by max(|re|, |im|), within a factor sqrt(2) of |z|
         int piv = k;
-        double best = A[k][k].re * A[k][k].re + A[k][k].im * A[k][k].im;
+        int best = max(mag_key(A[k][k].re), mag_key(A[k][k].im));
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {
-            const double v = A[i][k].re * A[i][k].re + A[i][k].im * A[i][k].im;
+            const int v = max(mag_key(A[i][k].re), mag_key(A[i][k].im));
             if (v > best) { best = v; piv = i; }
         }
 #pragma unroll
@@ -182,7 +201,7 @@ __device__ __forceinline__ cplx det_complex(cplx (&A)[N][N])
         const cplx akk = A[k][k];
         det = cmul(det, akk);
         const double n2 = akk.re * akk.re + akk.im * akk.im;
-        const double r = 1.0 / n2;
+        const double r = recip_fp64(n2);
         const cplx inv = {akk.re * r, -akk.im * r};
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {
