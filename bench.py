@@ -252,9 +252,10 @@ def reference_arm(args):
 
 
 def batch_arm(args):
-    """48 molecules (F cycling over the built classes 3, 6, 9; n_traj log-uniform in
-    [512, 32768]; steps uniform in [2000, 8000]) sampled, propagated in one
-    persistent launch per F-class and transformed, all captured in one CUDA graph."""
+    """48 molecules (F cycling over the recipe's classes 3, 6, 9, 12, 15 -- F = 24 is not
+    built; n_traj log-uniform in [512, 32768]; steps uniform in [2000, 8000]) sampled,
+    propagated in one persistent launch per F-class and transformed, all captured in
+    one CUDA graph.  One batch takes ~25 s on a GB300: time it with --steps 2."""
     import torch
     from paper_1312_4698_gb300 import scivr
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -264,7 +265,7 @@ def batch_arm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    mols = wl.batch_molecules(args.n_mol, seed=1000 * rank, Fs=(3, 6, 9))
+    mols = wl.batch_molecules(args.n_mol, seed=1000 * rank, Fs=(3, 6, 9, 12, 15))
     prec = PRECISIONS[args.precision]
     ftm = FT_MODES[args.ft]
     entries = []

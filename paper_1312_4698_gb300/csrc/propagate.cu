@@ -12,7 +12,8 @@ cudaError_t launch_group_batch_mixed_F(int warps, const PropLaunch *items, const
 
 int batch_warp_candidates(int F, int *out)
 {
-    if (F < 1 || F > 9) return 0;
+    if (F < 1 || F > 16) return 0;
+    if (F > 9) { out[0] = 2; return 1; }   // wide groups: the coupling tensors are shared by the CTA's warps
     if (2 * F > 16) { out[0] = 1; out[1] = 2; }
     else { out[0] = 2; out[1] = 4; }
     return 2;
@@ -24,6 +25,7 @@ cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, 
     switch (F) {
 #define SCIVR_B(FF) case FF: return launch_group_batch_mixed_F<FF>(warps, items, work, n_work, counter, n_sm, s);
     SCIVR_B(1) SCIVR_B(2) SCIVR_B(3) SCIVR_B(4) SCIVR_B(5) SCIVR_B(6) SCIVR_B(7) SCIVR_B(8) SCIVR_B(9)
+    SCIVR_B(10) SCIVR_B(11) SCIVR_B(12) SCIVR_B(13) SCIVR_B(14) SCIVR_B(15) SCIVR_B(16)
 #undef SCIVR_B
     default: return cudaErrorInvalidValue;
     }
@@ -32,7 +34,8 @@ cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, 
 namespace {
 
 constexpr int kMaxThreadF = 9;   // thread-per-trajectory FP64 kernel
-constexpr int kMaxGroupF = 9;    // lane-group kernels (2F <= 32 lanes)
+constexpr int kMaxGroupF = 9;    // FP64 lane-group kernel
+constexpr int kMaxMixedF = 16;   // mixed lane-group kernel (2F <= 32 lanes; one trajectory per warp above F = 9)
 
 // Schedule choice when the caller leaves it to the library: the lane-group
 // kernel keeps every SM busy with few trajectories (it launches G lanes per
@@ -55,7 +58,7 @@ int choose(int F, int precision, int64_t n_traj)
 bool propagate_supported(int F, int precision, int kernel)
 {
     if (F < 1) return false;
-    if (precision == SCIVR_MIXED) return kernel != SCIVR_KERNEL_THREAD && F <= kMaxGroupF;
+    if (precision == SCIVR_MIXED) return kernel != SCIVR_KERNEL_THREAD && F <= kMaxMixedF;
     if (precision != SCIVR_FP64) return false;
     if (kernel == SCIVR_KERNEL_THREAD) return F <= kMaxThreadF;
     if (kernel == SCIVR_KERNEL_GROUP) return F <= kMaxGroupF;
@@ -73,7 +76,18 @@ cudaError_t launch_propagate(const PropLaunch &L, cudaStream_t s, int *n_launch)
     const int kern = L.args.kernel == SCIVR_KERNEL_AUTO ? choose(L.args.F, L.args.precision, L.n_traj)
                                                           : L.args.kernel;
     if (L.args.precision == SCIVR_MIXED) {
-        switch (L.args.F) { SCIVR_CASES(launch_group_mixed, L) case 9: return launch_group_mixed<9>(L, s); default: break; }
+        switch (L.args.F) {
+            SCIVR_CASES(launch_group_mixed, L)
+            case 9: return launch_group_mixed<9>(L, s);
+            case 10: return launch_group_mixed<10>(L, s);
+            case 11: return launch_group_mixed<11>(L, s);
+            case 12: return launch_group_mixed<12>(L, s);
+            case 13: return launch_group_mixed<13>(L, s);
+            case 14: return launch_group_mixed<14>(L, s);
+            case 15: return launch_group_mixed<15>(L, s);
+            case 16: return launch_group_mixed<16>(L, s);
+            default: break;
+        }
     } else if (kern == SCIVR_KERNEL_GROUP) {
         switch (L.args.F) { SCIVR_CASES(launch_group_fp64, L) case 9: return launch_group_fp64<9>(L, s); default: break; }
     } else {

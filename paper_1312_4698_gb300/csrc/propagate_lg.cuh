@@ -92,7 +92,14 @@ template <typename Real, int F> __device__ __forceinline__ Real c_w2(const CtaCo
 // store one job into F different rows, which a plain [row][job] layout puts
 // into a single shared-memory bank; XOR-ing the job with the row spreads them
 // over banks, and every row is still a permutation of the 32 jobs.
-__device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & 15); }
+template <int JOBS>
+__device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & (JOBS >= 16 ? 15 : JOBS - 1)); }
+
+// Steps per chunk of a lane group.  Phases 2-4 give one job (trajectory, step) to
+// each lane: T * C jobs per warp.  Up to F = 9 a chunk holds 32 jobs; the wide
+// groups (F > 9, one trajectory per warp) take 8, so that the per-job prefactor
+// matrices (F^2 complex entries each) stay within shared memory.
+template <int F, int G> __host__ __device__ constexpr int lg_chunk() { return (G == 32 && F > 9) ? 8 : G; }
 
 // 16-byte vectors of Real for shared-memory loads.
 template <typename Real> struct V16;
@@ -161,6 +168,7 @@ template <int F, int G, typename Real>
 struct WarpShared {
     static constexpr int P = F * (F + 1) / 2;
     static constexpr int T = 32 / G;
+    static constexpr int JOBS = T * lg_chunk<F, G>();   // jobs per chunk (phases 2-4)
     static constexpr int S3 = TensorLayout<F, Real>::S3;   // q, zero-padded (also the Gc row stride)
     static constexpr int S4 = TensorLayout<F, Real>::S4;   // pair products q_k q_l, zero-padded
     static constexpr int SH = vec_len<Real>(F);            // row stride of H (rows read by the whole group)
@@ -168,11 +176,11 @@ struct WarpShared {
     alignas(16) Real qq[T][S4];
     alignas(16) Real Gc[T][F][S3];          // gradient coefficients, full symmetric matrix (row a read by mode lane a)
     alignas(16) Real H[T][F][SH];
-    typename Vec2<Real>::T A[F * F][32];   // prefactor matrix per job, entry-major (job column swizzled)
-    Real pj[F][32], qj[F][32];             // state per job, for the overlap (job column swizzled); FP32
+    typename Vec2<Real>::T A[F * F][JOBS]; // prefactor matrix per job, entry-major (job column swizzled)
+    Real pj[F][JOBS], qj[F][JOBS];         // state per job, for the overlap (job column swizzled); FP32
                                            // in the mixed path, where the overlap is evaluated in FP32
-    double Sj[32];                          // action per job
-    double lnA[32];                         // log |det A|^{1/2} per job (Herman-Kluk summand only)
+    double Sj[JOBS];                        // action per job
+    double lnA[JOBS];                       // log |det A|^{1/2} per job (Herman-Kluk summand only)
     double2 ov0[SCIVR_MAX_CHI][T];          // log <chi|p0 q0> per trajectory (Herman-Kluk summand only)
 };
 
@@ -186,7 +194,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     constexpr int N2 = 2 * F;
     constexpr int P = F * (F + 1) / 2;
     constexpr int T = 32 / G;
-    constexpr int C = G;                       // steps per chunk: T * C = 32 jobs
+    constexpr int C = lg_chunk<F, G>();        // steps per chunk
+    constexpr int JOBS = T * C;                // jobs per chunk: lane ln < JOBS takes job ln in phases 2-4
     constexpr int EPL = (P + G - 1) / G;       // packed Hessian entries per lane
     static_assert(N2 <= G, "group must hold all 2F columns");
     using Sh = WarpShared<F, G, Real>;
@@ -426,7 +435,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 #pragma unroll
                 for (int a = 0; a < F; ++a) { W[a] = Mp[a]; W[F + a] = Mq[a]; }
                 Real det = Real(1);
-                unsigned unused = (1u << N2) - 1u;
+                unsigned unused = N2 == 32 ? FULL : (1u << N2) - 1u;
                 unsigned parity = 0u;
 #pragma unroll
                 for (int k = 0; k < N2; ++k) {
@@ -484,12 +493,12 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         R2 v;
                         v.x = Real(0.5) * re;
                         v.y = Real(0.5) * im;
-                        sh.A[a * F + g][jswz(a * F + g, job)] = v;
+                        sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = v;
                     }
                 }
                 if (g < F) {
-                    sh.pj[g][jswz(g, job)] = pr;   // p did not change since the last kick set pr
-                    sh.qj[g][jswz(g, job)] = (Real)q;
+                    sh.pj[g][jswz<JOBS>(g, job)] = pr;   // p did not change since the last kick set pr
+                    sh.qj[g][jswz<JOBS>(g, job)] = (Real)q;
                 }
                 // the step's action increment, summed over the group, joins the FP64 action
 #pragma unroll
@@ -510,16 +519,18 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         // ---------------- phase 2: det A per job ----------------
         const int jc = g;                 // this lane's job: trajectory t, step step0 + jc + 1
         const bool jvalid = jc < cnt;
-        double argA;                      // arg det A of this lane's job (principal value)
+        double argA = 0.0;                // arg det A of this lane's job (principal value)
         double lnAbsA = 0.0;              // ln |det A| (mixed path always; FP64 path for the HK summand)
         double2 detA = make_double2(1.0, 0.0);   // FP64 path: det A itself
-        if constexpr (sizeof(Real) == 4) {
+        if (ln >= JOBS) {
+            // no job for this lane (wide groups): the in-place elimination must not touch a job's storage
+        } else if constexpr (sizeof(Real) == 4) {
             // Mixed path: the entries of A are FP32 (formed from the FP32 monodromy), so the
             // complex LU with partial pivoting runs in FP32, in place on this job's column of
             // the shared array (no per-lane matrix in registers).  ln|det A| = sum ln|pivot|
             // and the unit phasor prod pivot/|pivot| (sign flipped per row exchange) keep the
             // result free of FP32 overflow whatever the size of the entries.
-            auto at = [&](int e) -> R2 & { return sh.A[e][jswz(e, ln)]; };
+            auto at = [&](int e) -> R2 & { return sh.A[e][jswz<JOBS>(e, ln)]; };
             float ur = 1.0f, ui = 0.0f, lsum = 0.0f;
 #pragma unroll
             for (int k = 0; k < F; ++k) {
@@ -573,7 +584,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         } else {
             // FP64 path: the same in-place elimination in FP64, with det A as the product of
             // the pivots (no range concern in FP64)
-            auto at = [&](int e) -> R2 & { return sh.A[e][jswz(e, ln)]; };
+            auto at = [&](int e) -> R2 & { return sh.A[e][jswz<JOBS>(e, ln)]; };
             double dr = 1.0, di = 0.0;
 #pragma unroll
             for (int k = 0; k < F; ++k) {
@@ -623,7 +634,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             if (A.amplitude == SCIVR_AMP_HK) lnAbsA = log(hypot(dr, di));
         }
         // Herman-Kluk summand: log |det A|^{1/2}, the only part of det A phase 4 needs
-        if (A.amplitude == SCIVR_AMP_HK) sh.lnA[ln] = 0.5 * lnAbsA;
+        if (A.amplitude == SCIVR_AMP_HK && ln < JOBS) sh.lnA[ln] = 0.5 * lnAbsA;
         // ---------------- phase 3: continuous phase (segmented scan) ----------------
         const double arg = argA;
         double arg_prev = __shfl_up_sync(FULL, arg, 1, G);
@@ -637,7 +648,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             if (g >= o) inc += v;
         }
         const double theta = theta_last + inc;
-        const int lastlane = base + cnt - 1;
+        const int lastlane = t * C + cnt - 1;
         theta_last = __shfl_sync(FULL, theta, lastlane);
         arg_last = __shfl_sync(FULL, arg, lastlane);
         if constexpr (sizeof(Real) == 4) {
@@ -658,7 +669,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     float rf = 0.0f, imf = 0.0f;
 #pragma unroll
                     for (int a = 0; a < F; ++a) {
-                        const float pa = sh.pj[a][jswz(a, ln)], qa = sh.qj[a][jswz(a, ln)];
+                        const float pa = sh.pj[a][jswz<JOBS>(a, ln)], qa = sh.qj[a][jswz<JOBS>(a, ln)];
                         const float dq = cc.q_eqf[x][a] - qa, dp = cc.p_eqf[x][a] - pa;
                         rf = fmaf(-cc.qwf[a] * dq, dq, rf);
                         rf = fmaf(-cc.pwf[a] * dp, dp, rf);
@@ -681,7 +692,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     double re = 0.0, im = 0.0;
 #pragma unroll
                     for (int a = 0; a < F; ++a) {
-                        const double pa = sh.pj[a][jswz(a, ln)], qa = sh.qj[a][jswz(a, ln)];
+                        const double pa = sh.pj[a][jswz<JOBS>(a, ln)], qa = sh.qj[a][jswz<JOBS>(a, ln)];
                         const double dq = cc.q_eq[x][a] - qa, dp = cc.p_eq[x][a] - pa;
                         re = fma(-cc.qw[a] * dq, dq, re);
                         re = fma(-cc.pw[a] * dp, dp, re);
@@ -700,7 +711,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 }
             }
         }
-        if (!isfinite(sh.Sj[base + cnt - 1])) good = false;
+        if (!isfinite(sh.Sj[t * C + cnt - 1])) good = false;
         __syncwarp();
     }
 
@@ -712,7 +723,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         if (fo.q) fo.q[g * n + jl] = q;
     }
     if (g == 0) {
-        if (fo.S) fo.S[jl] = sh.Sj[base + ((A.n_steps - 1) % C)];
+        if (fo.S) fo.S[jl] = sh.Sj[t * C + ((A.n_steps - 1) % C)];
         if (fo.theta) fo.theta[jl] = theta_last;
         if (fo.detM) fo.detM[jl] = detM_last;
         if (fo.stab) fo.stab[jl] = (double)stab;
@@ -816,5 +827,37 @@ cudaError_t launch_lg(const PropLaunch &L, cudaStream_t s)
     kern<<<(unsigned)blocks, 32 * WARPS, bytes, s>>>(L);
     return cudaGetLastError();
 }
+
+// Launchers instantiated by the prop_lg_*.cu units: lanes per trajectory by F
+// (2F columns must fit), warps per CTA, and the batch variants the tuner may pick.
+template <int F> constexpr int group_lanes() { return 2 * F <= 8 ? 8 : (2 * F <= 16 ? 16 : 32); }
+
+template <int F> cudaError_t launch_group_mixed(const PropLaunch &L, cudaStream_t s)
+{
+    return launch_lg<F, group_lanes<F>(), float, group_lanes<F>() == 32 ? 2 : 4>(L, s);
+}
+
+template <int F>
+cudaError_t launch_group_batch_mixed_F(int warps, const PropLaunch *items, const int2 *work, int n_work,
+                                      int *counter, int n_sm, cudaStream_t s)
+{
+    constexpr int G = group_lanes<F>();
+    if constexpr (G == 32) {
+        if constexpr (F <= 9) {
+            if (warps == 1) return launch_lg_batch<F, G, float, 1>(items, work, n_work, counter, n_sm, s);
+        }
+        if (warps == 2) return launch_lg_batch<F, G, float, 2>(items, work, n_work, counter, n_sm, s);
+    } else {
+        if (warps == 2) return launch_lg_batch<F, G, float, 2>(items, work, n_work, counter, n_sm, s);
+        if (warps == 4) return launch_lg_batch<F, G, float, 4>(items, work, n_work, counter, n_sm, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int F> cudaError_t launch_group_fp64(const PropLaunch &L, cudaStream_t s)
+{
+    return launch_lg<F, group_lanes<F>(), double, group_lanes<F>() == 32 ? 2 : 4>(L, s);
+}
+
 
 }  // namespace scivr

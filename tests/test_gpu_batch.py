@@ -25,7 +25,7 @@ def G():
 
 def _molecules():
     specs = [(3, 100, 70, 1), (6, 257, 150, 2), (9, 64, 40, 3), (6, 1000, 96, 4), (3, 33, 33, 5),
-             (4, 50, 61, 6)]
+             (4, 50, 61, 6), (12, 45, 37, 7), (15, 70, 29, 8)]
     out = []
     for F, n, steps, seed in specs:
         w8 = wl.config_f3(n_traj=n, n_steps=steps, n_E=150) if F == 3 else \

@@ -462,3 +462,62 @@ def test_default_configuration_full_size_sampled(G):
     print(f"sample spectrum: rel err {e_s:.2e}; {len(pr)} peaks, max shift {shift.max():.3f} cm^-1")
     assert e_s <= 3e-2
     assert len(pr) > 0 and shift.max() <= 1.0
+
+
+# ---------------------------------------------------------------------------
+# Wide groups (F = 10..16, one trajectory per warp, mixed precision only).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("F", [10, 12, 15, 16])
+def test_wide_group_mixed_close_to_oracle(G, F):
+    """Mixed path for F > 9 against the FP64 oracle: 67 trajectories (ragged for two
+    trajectories per CTA) and 301 steps (not a multiple of the 8-step chunk); F = 16
+    fills all 32 lanes with monodromy columns.  Bounds as for F <= 9."""
+    w8 = wl.config_generic(F, seed=F, n_traj=67, n_steps=301)
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, 3)
+    ra, rg, rf = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0, final=True)
+    g = gpu_propagate(G, w8, p0, q0, precision=1, stab_tol=MIXED_STAB_TOL, fin=True)
+    assert G.scivr_check_status() == G.SCIVR_OK
+    sel = rg.astype(bool) & g["good"].astype(bool)
+    assert sel.sum() >= 0.9 * rg.sum() and sel.sum() > 0
+    e_amp = amp_err(g["amp"][:, sel], ra[:, sel], np.ones(sel.sum(), np.uint8))
+    e_det = np.max(np.abs(g["detM"][sel] - rf["detM"][sel]))
+    dA = g["detA"][:, 0] + 1j * g["detA"][:, 1]
+    e_dA = np.max(np.abs(dA[sel] - rf["detA"][sel]) / np.abs(rf["detA"][sel]))
+    rg_ = np.sqrt(w8.gamma)[:, None]
+    e_q = np.max(np.abs((g["q"] - rf["q"].T) * rg_)[:, sel])
+    e_S = np.max(np.abs(g["S"][sel] - rf["S"][sel]))
+    print(f"F={F}: {sel.sum()} of {rg.sum()} good; amp {e_amp:.2e} det M {e_det:.2e} det A {e_dA:.2e} "
+          f"q {e_q:.2e} S {e_S:.2e}")
+    assert e_amp < 5e-2 and e_det < 1e-2 and e_dA < 1e-3 and e_q < 1e-3
+
+
+def test_wide_group_several_reference_states_and_hk(G):
+    """F = 12: two reference states, time-averaged and Herman-Kluk summands."""
+    from tests.test_gpu_hk import hk_propagate
+    w8 = wl.config_generic(12, seed=5, n_traj=40, n_steps=120)
+    om = w8.gamma
+    w8 = w8.with_(p_eq=np.stack([np.sqrt(om), np.sqrt(3 * om)]), q_eq=np.zeros((2, 12)))
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq[0], w8.q_eq[0], w8.n_traj, 4)
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0)
+    g = gpu_propagate(G, w8, p0, q0, precision=1, stab_tol=MIXED_STAB_TOL)
+    sel = rg.astype(bool) & g["good"].astype(bool)
+    assert amp_err(g["amp"][:, sel], ra[:, sel], np.ones(sel.sum(), np.uint8)) < 5e-2
+    rh, rgh = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0,
+                               amplitude=oracle.AMP_HK)
+    gh = hk_propagate(G, w8, p0, q0, precision=1, stab_tol=MIXED_STAB_TOL)
+    sel = rgh.astype(bool) & gh["good"].astype(bool)
+    assert np.all(gh["amp"][:, :, 0] == 1.0)
+    assert amp_err(gh["amp"][:, sel], rh[:, sel], np.ones(sel.sum(), np.uint8)) < 5e-2
+
+
+def test_wide_group_fp64_is_unsupported(G):
+    import torch
+    w8 = wl.config_generic(12, seed=1, n_traj=4, n_steps=5)
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, 4, 0)
+    pes = G.scivr_create_pes(w8.pes)
+    amp = torch.empty((1, 4, 6, 2), dtype=torch.float64, device="cuda")
+    good = torch.empty(4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(G.ScivrError) as ei:
+        G.scivr_propagate(pes, w8.dt, 5, w8.gamma, w8.p_eq, w8.q_eq, 4, _t(p0), _t(q0), amp, 6, good)
+    assert ei.value.code == G.SCIVR_EUNSUPPORTED
