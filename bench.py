@@ -333,8 +333,8 @@ def batch_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision] + ("" if ftm == 0 else f" + {args.ft} tensor FT"),
         "data": "synthetic",
-        "config": {"workload": f"batch of {len(mols)} molecules, F cycling over 3/6/9 (the built classes; "
-                               f"F = 12, 15, 24 of the batched recipe are not built), n_traj log-uniform "
+        "config": {"workload": f"batch of {len(mols)} molecules, F cycling over 3/6/9/12/15 (F = 24 of the "
+                               f"batched recipe is not built), n_traj log-uniform "
                                f"[512, 32768], steps uniform [2000, 8000], 4000 energies; sampling, "
                                f"propagation (one persistent launch per F) and spectra in one CUDA graph",
                    "global_batch": world * sum(w8.n_traj for w8 in mols),
