@@ -96,10 +96,16 @@ template <int JOBS>
 __device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & (JOBS >= 16 ? 15 : JOBS - 1)); }
 
 // Steps per chunk of a lane group.  Phases 2-4 give one job (trajectory, step) to
-// each lane: T * C jobs per warp.  Up to F = 9 a chunk holds 32 jobs; the wide
-// groups (F > 9, one trajectory per warp) take 8, so that the per-job prefactor
-// matrices (F^2 complex entries each) stay within shared memory.
-template <int F, int G> __host__ __device__ constexpr int lg_chunk() { return (G == 32 && F > 9) ? 8 : G; }
+// each lane: T * C jobs per warp.  Groups of 8 and 16 lanes fill all 32 lanes; the
+// one-trajectory-per-warp groups take 16 jobs (F = 9) or 8 (F > 9), so that the
+// per-job prefactor matrices (F^2 complex entries each) leave room in shared memory
+// for more warps per SM.
+template <int F, int G> __host__ __device__ constexpr int lg_chunk() { return G < 32 ? G : (F > 9 ? 8 : 16); }
+
+// Warps per CTA and the launch-bounds CTA count: the wide groups (F > 9) put 8 warps
+// (4 at F = 16) on one copy of the coupling tensors, one CTA per SM.
+template <int F, int G> __host__ __device__ constexpr int lg_warps() { return G < 32 ? 4 : (F <= 9 ? 2 : (F <= 15 ? 8 : 4)); }
+template <int F> __host__ __device__ constexpr int lg_min_ctas() { return F > 9 ? 1 : 4; }
 
 // 16-byte vectors of Real for shared-memory loads.
 template <typename Real> struct V16;
@@ -749,7 +755,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 }
 
 template <int F, int G, typename Real, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch L)
+__global__ void __launch_bounds__(32 * WARPS, lg_min_ctas<F>()) k_propagate_lg(const PropLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     lg_body<F, G, Real, WARPS>(L, blockIdx.x, smem_raw);
@@ -759,7 +765,7 @@ __global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg(const PropLaunch
 // list sorted by decreasing cost until it is exhausted.  items: device array
 // of per-molecule launches (all of this F); work: (item, tile) pairs.
 template <int F, int G, typename Real, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, 4) k_propagate_lg_batch(const PropLaunch *__restrict__ items,
+__global__ void __launch_bounds__(32 * WARPS, lg_min_ctas<F>()) k_propagate_lg_batch(const PropLaunch *__restrict__ items,
                                                                        const int2 *__restrict__ work,
                                                                        int n_work, int *__restrict__ counter)
 {
@@ -834,7 +840,7 @@ template <int F> constexpr int group_lanes() { return 2 * F <= 8 ? 8 : (2 * F <=
 
 template <int F> cudaError_t launch_group_mixed(const PropLaunch &L, cudaStream_t s)
 {
-    return launch_lg<F, group_lanes<F>(), float, group_lanes<F>() == 32 ? 2 : 4>(L, s);
+    return launch_lg<F, group_lanes<F>(), float, lg::lg_warps<F, group_lanes<F>()>()>(L, s);
 }
 
 template <int F>
@@ -842,10 +848,11 @@ cudaError_t launch_group_batch_mixed_F(int warps, const PropLaunch *items, const
                                       int *counter, int n_sm, cudaStream_t s)
 {
     constexpr int G = group_lanes<F>();
-    if constexpr (G == 32) {
-        if constexpr (F <= 9) {
-            if (warps == 1) return launch_lg_batch<F, G, float, 1>(items, work, n_work, counter, n_sm, s);
-        }
+    if constexpr (G == 32 && F > 9) {
+        constexpr int W = lg::lg_warps<F, G>();
+        if (warps == W) return launch_lg_batch<F, G, float, W>(items, work, n_work, counter, n_sm, s);
+    } else if constexpr (G == 32) {
+        if (warps == 1) return launch_lg_batch<F, G, float, 1>(items, work, n_work, counter, n_sm, s);
         if (warps == 2) return launch_lg_batch<F, G, float, 2>(items, work, n_work, counter, n_sm, s);
     } else {
         if (warps == 2) return launch_lg_batch<F, G, float, 2>(items, work, n_work, counter, n_sm, s);
