@@ -369,19 +369,10 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         const Real h3 = use3 ? dot16<Real, S3>(sT3 + e * S3, sh.qr[t]) : Real(0);
                         const Real h4 = use4 ? dot16<Real, S4>(sT4 + e * S4, sh.qq[t]) : Real(0);
                         const int a = ea[i], b = eb[i];
-                        Real hd = Real(0);
-                        if (a == b) {
-                            if (pes.diag_kind == SCIVR_DIAG_MORSE) {
-                                const Real Dm = c_D<Real>(cc, a), am = c_a<Real>(cc, a);
-                                const Real u = rexp<Real>(-am * sh.qr[t][a]);
-                                hd = Real(2) * Dm * am * am * u * (Real(2) * u - Real(1));
-                            } else {
-                                hd = c_w2<Real>(cc, a);
-                            }
-                        }
+                        // coupling part only: the mode lanes add the diagonal term below
                         const Real h = h3 + h4;
-                        sh.H[t][a][b] = h + hd;
-                        sh.H[t][b][a] = h + hd;
+                        sh.H[t][a][b] = h;
+                        sh.H[t][b][a] = h;
                         const Real gce = fma(Real(0.5), h3, h4 * Real(1.0 / 3.0));
                         sh.Gc[t][a][b] = gce;
                         sh.Gc[t][b][a] = gce;
@@ -394,22 +385,26 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 Real vlane = vpart;
                 if (g < F) {
                     const Real gr = dot16<Real, S3>(sh.Gc[t][g], sh.qr[t]);
-                    Real Vd, gd;
+                    Real Vd, gd, hd;   // the separable diagonal: value, gradient, Hessian
                     if (pes.diag_kind == SCIVR_DIAG_MORSE) {
                         const Real Dm = c_D<Real>(cc, g), am = c_a<Real>(cc, g);
                         const Real u = rexp<Real>(-am * sh.qr[t][g]);
                         const Real omu = Real(1) - u;
                         Vd = Dm * omu * omu;
                         gd = Real(2) * Dm * am * u * omu;
+                        hd = Real(2) * Dm * am * am * u * (Real(2) * u - Real(1));
                     } else {
                         const Real w2 = c_w2<Real>(cc, g);
                         Vd = Real(0.5) * w2 * sh.qr[t][g] * sh.qr[t][g];
                         gd = w2 * sh.qr[t][g];
+                        hd = w2;
                     }
+                    sh.H[t][g][g] += hd;
                     p = fma(-tk, (double)(gr + gd), p);
                     pr = (Real)p;
                     vlane += Vd;
                 }
+                __syncwarp();   // H complete before the monodromy kick reads it
                 dS = fma(-rtk, vlane, dS);
                 // monodromy kick: M_p -= tau H M_q (column lanes; rows of H by 16-byte broadcast loads)
                 {
@@ -462,8 +457,10 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     }
                     const int pl = (int)(kmax & 63u) - 1;
                     const Real pk = __shfl_sync(FULL, W[k], base + pl);
-                    Real inv;   // correctly rounded 1/pk either way
-                    if constexpr (sizeof(Real) == 4) inv = __frcp_rn(pk); else inv = Real(1) / pk;
+                    // FP32: the hardware reciprocal (det M only feeds the stability test, whose FP32
+                    // tolerance is far above its ulp-level error); FP64: exact division
+                    Real inv;
+                    if constexpr (sizeof(Real) == 4) inv = __fdividef(1.0f, pk); else inv = Real(1) / pk;
                     parity ^= (unsigned)__popc(unused & ((1u << pl) - 1u)) & 1u;
                     unused &= ~(1u << pl);
                     det *= pk;
