@@ -210,3 +210,41 @@ def test_hk_f3_workload_spectrum_peaks_match_oracle(G):
     assert len(pr) > 0 and len(pr) == len(pg)
     assert np.max(np.abs(pr - pg)) <= 0.1
     assert np.max(np.abs(gI - rI)) <= 1e-8 * np.max(np.abs(rI))
+
+
+def test_hk_default_workload_full_size_sampled(G):
+    """The plain HK configuration bench.py times (--amplitude hk) at its full size and
+    launch shape: F = 6, 16384 trajectories x 4000 steps, mixed propagation.  24 sampled
+    summand rows (the ragged last one included) against the FP64 oracle within the mixed
+    bound, and the HK spectrum of that sample (oracle flags as the good mask) against
+    the oracle's: within 3e-2 of its maximum, every oracle peak above 10 % matched
+    within 1 cm^-1."""
+    import torch
+    from tests import closed_forms as cf
+    from tests.test_gpu_parity import MIXED_STAB_TOL as TOL
+    w8 = wl.config_f6()
+    n, K = w8.n_traj, w8.n_steps + 1
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, n, w8.seed)
+    g = hk_propagate(G, w8, p0, q0, precision=1, stab_tol=TOL)
+    idx = np.sort(np.random.default_rng(2).choice(n, 24, replace=False))
+    idx[-1] = n - 1
+    ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0[:, idx], q0[:, idx],
+                              amplitude=oracle.AMP_HK)
+    sel = rg.astype(bool) & g["good"][idx].astype(bool)
+    assert sel.sum() >= 22
+    e_amp = amp_err(g["amp"][:, idx][:, sel], ra[:, sel], np.ones(sel.sum(), np.uint8))
+    print(f"sampled HK rows: max error {e_amp:.2e}")
+    assert e_amp < 5e-2
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    mask[torch.as_tensor(idx, device="cuda")] = _t(rg)
+    gI, gng, _ = hk_spectrum(G, g["dev_amp"][0], mask, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E)
+    rI, rng_, _ = oracle.spectrum_hk(ra[0], rg, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E)
+    assert gng == rng_
+    e_s = np.max(np.abs(gI - rI)) / np.max(np.abs(rI))
+    E = w8.energies()
+    pr = wl.to_cm1(cf.find_peaks(E, rI, 0.1))
+    pg = wl.to_cm1(cf.find_peaks(E, gI, 0.02))
+    shift = np.array([np.min(np.abs(pg - x)) for x in pr])
+    print(f"sample HK spectrum: rel err {e_s:.2e}; {len(pr)} peaks, max shift {shift.max():.3f} cm^-1")
+    assert e_s <= 3e-2
+    assert len(pr) > 0 and shift.max() <= 1.0
