@@ -13,7 +13,7 @@ cudaError_t launch_group_batch_mixed_F(int warps, const PropLaunch *items, const
 int batch_warp_candidates(int F, int *out)
 {
     if (F < 1 || F > 16) return 0;
-    if (F > 9) { out[0] = F <= 15 ? 8 : 4; return 1; }   // wide groups: one CTA per SM shares the tensors
+    if (F > 9) { out[0] = F <= 12 ? 8 : 4; return 1; }   // wide groups: one CTA per SM shares the tensors
     if (2 * F > 16) { out[0] = 1; out[1] = 2; }
     else { out[0] = 2; out[1] = 4; }
     return 2;

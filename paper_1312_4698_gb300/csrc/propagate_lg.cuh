@@ -102,9 +102,11 @@ __device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & (JOBS >= 16 
 // for more warps per SM.
 template <int F, int G> __host__ __device__ constexpr int lg_chunk() { return G < 32 ? G : (F > 9 ? 8 : 16); }
 
-// Warps per CTA and the launch-bounds CTA count: the wide groups (F > 9) put 8 warps
-// (4 at F = 16) on one copy of the coupling tensors, one CTA per SM.
-template <int F, int G> __host__ __device__ constexpr int lg_warps() { return G < 32 ? 4 : (F <= 9 ? 2 : (F <= 15 ? 8 : 4)); }
+// Warps per CTA and the launch-bounds CTA count: the wide groups (F > 9) run one CTA per
+// SM on one copy of the coupling tensors, 8 warps up to F = 12 and 4 above (measured:
+// at F = 15 the 8-warp CTA's 216 KB of shared memory leaves too little L1 and runs 16 %
+// slower; at F = 12 8 warps are 5 % faster).
+template <int F, int G> __host__ __device__ constexpr int lg_warps() { return G < 32 ? 4 : (F <= 9 ? 2 : (F <= 12 ? 8 : 4)); }
 template <int F> __host__ __device__ constexpr int lg_min_ctas() { return F > 9 ? 1 : 4; }
 
 // 16-byte vectors of Real for shared-memory loads.
