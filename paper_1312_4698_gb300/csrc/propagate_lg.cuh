@@ -1,22 +1,25 @@
 // Lane-group propagation kernel (Sec. III.A / III.B of arXiv:1312.4698).
 //
 // A group of G lanes (G = 8, 16 or 32, 2F <= G) owns one trajectory; a warp
-// holds T = 32/G trajectories.  Work is split by what parallelises:
+// holds T = 32/G trajectories.  Steps are processed in chunks of C (C = G, or
+// 16 / 8 steps for the one-trajectory-per-warp groups at F = 9 / F > 9), and
+// work is split by what parallelises:
 //
 //   phase 1 (per step, group-parallel, arithmetic type Real):
 //     lane g < 2F owns column g of the monodromy matrix M (its p- and q-rows
-//     in registers); lane a < F owns mode a: p_a, q_a and the action
-//     partial sum in FP64.  The Hessian's packed entries e(a,b) are spread
-//     over the group; the tensors T3/T4 live in shared memory.  det M is an
-//     LU over the group's columns (pivot and multipliers by warp shuffle).
-//     The Herman-Kluk matrix A of the step is written to shared memory.
-//   phase 2 (once per G steps, job-parallel): lane j takes job j =
-//     (trajectory j / G, step j % G) and computes det A and its argument
-//     by an LU in place in shared memory (FP64 path in FP64; mixed path in
-//     FP32, the entries being FP32 already).
+//     in registers); lane a < F owns mode a: p_a, q_a (FP64) and the
+//     separable diagonal of the potential.  The Hessian's packed coupling
+//     entries e(a,b) are spread over the group, reading the coupling tensors
+//     staged in shared memory.  det M is Gaussian elimination of M^T across the
+//     group (pivot column by warp reduction, pivot entries by shuffle).  The
+//     Herman-Kluk matrix A of the step goes to shared memory.
+//   phase 2 (once per chunk, job-parallel): lane j < T*C takes job j =
+//     (trajectory j / C, step j % C) and computes det A and its argument by an
+//     LU in place in shared memory (FP64 path in FP64; mixed path in FP32, the
+//     entries being FP32 already).
 //   phase 3: the continuous phase, a segmented prefix sum over each group.
-//   phase 4 (job-parallel, FP64): overlap <chi|p q>, action, phase and the
-//     amplitude; each group writes G consecutive samples of its row.
+//   phase 4 (job-parallel): overlap <chi|p q>, action, phase and the amplitude;
+//     each group writes C consecutive samples of its row.
 //
 // Real = float is the mixed-precision path: monodromy, potential, det M, A,
 // the elimination that gives det A, the overlap and each step's action
@@ -26,8 +29,8 @@
 // same schedule in FP64 throughout.
 //
 // On GB300 a warp-wide FP64 instruction holds a sub-partition's FP64 pipe for
-// about 64 cycles, so phase 1 keeps FP64 to the state updates (one FMA per
-// drift and per kick in the mode lanes) and one FP64 add per step.
+// about 64 cycles, so in the mixed path phase 1 keeps FP64 to the state updates
+// (one FMA per drift and per kick in the mode lanes) and one FP64 add per step.
 #pragma once
 
 #include <math_constants.h>
@@ -91,7 +94,7 @@ template <typename Real, int F> __device__ __forceinline__ Real c_w2(const CtaCo
 // Column of job j in row r of the per-job arrays: the F mode lanes of a group
 // store one job into F different rows, which a plain [row][job] layout puts
 // into a single shared-memory bank; XOR-ing the job with the row spreads them
-// over banks, and every row is still a permutation of the 32 jobs.
+// over banks, and every row is still a permutation of the chunk's jobs.
 template <int JOBS>
 __device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & (JOBS >= 16 ? 15 : JOBS - 1)); }
 
