@@ -41,8 +41,10 @@ def _sinc_kinetic(n, h):
     return np.where(d == 0, np.pi ** 2 / 3.0, off) / (2.0 * h * h)
 
 
-def _quantum(kappa, n0, n1):
-    """Eigenvalues and weights |<chi|psi_n>|^2 of H = p^2/2 + V on the product sinc grid."""
+def _quantum(kappa, n0, n1, p_eq=None):
+    """Eigenvalues and weights |<chi|psi_n>|^2 of H = p^2/2 + V on the product sinc grid
+    (chi: coherent states at q = 0 with momenta p_eq [n_chi][2], default sqrt(omega);
+    with p_eq given the weights are returned as a list, one array per state)."""
     a = OMEGA / np.sqrt(2.0 * D)
     c = kappa * REL
     x0 = np.linspace(*GRID[0], n0)
@@ -54,12 +56,14 @@ def _quantum(kappa, n0, n1):
     H = np.kron(_sinc_kinetic(n0, h0), np.eye(n1)) + np.kron(np.eye(n0), _sinc_kinetic(n1, h1))
     H[np.diag_indices_from(H)] += V.ravel()
     E, U = np.linalg.eigh(H)
-    # chi: coherent state at q = 0, p = sqrt(omega), widths gamma = omega (normalised per mode)
-    g, pe = OMEGA, np.sqrt(OMEGA)
-    chi = ((g[0] / np.pi) * (g[1] / np.pi)) ** 0.25 * np.exp(
-        -0.5 * g[0] * X0 ** 2 - 0.5 * g[1] * X1 ** 2 + 1j * (pe[0] * X0 + pe[1] * X1))
-    w = np.abs((np.sqrt(h0 * h1) * chi.ravel().conj()) @ U) ** 2
-    return E, w
+    # chi: coherent states at q = 0, momentum pe, widths gamma = omega (normalised per mode)
+    g = OMEGA
+    ws = []
+    for pe in (np.sqrt(OMEGA)[None] if p_eq is None else p_eq):
+        chi = ((g[0] / np.pi) * (g[1] / np.pi)) ** 0.25 * np.exp(
+            -0.5 * g[0] * X0 ** 2 - 0.5 * g[1] * X1 ** 2 + 1j * (pe[0] * X0 + pe[1] * X1))
+        ws.append(np.abs((np.sqrt(h0 * h1) * chi.ravel().conj()) @ U) ** 2)
+    return (E, ws[0]) if p_eq is None else (E, ws)
 
 
 def _sc_peaks(kappa, n_traj=2000, n_steps=3000, dt=10.0):
@@ -139,3 +143,28 @@ def test_plain_hk_peaks_match_quantum_levels(levels):
               f"HK {s1 - s0:+6.2f}")
         assert abs(s1 - e1) < 5.0
         assert abs((s1 - s0) - (e1 - e0)) < 5.0
+
+
+def test_several_reference_states_share_trajectories(levels):
+    """Two reference states on the same trajectories (sampled around the first):
+    chi_1 at p = sqrt(omega), chi_2 with mode 0 excited (p_0 = sqrt(3 omega_0)).  The
+    exact weights move the strongest line from the zero-point level (chi_1) to the
+    mode-0 fundamental (chi_2); the oracle's spectrum for each state must put its
+    strongest peak within 16 cm^-1 of that state's strongest exact line and a peak
+    within 16 cm^-1 of each of its lines of weight >= 0.1 (the method's bias, as above)."""
+    p_eq = np.stack([np.sqrt(OMEGA), np.array([np.sqrt(3.0 * OMEGA[0]), np.sqrt(OMEGA[1])])])
+    E, ws = _quantum(KAPPA, 48, 40, p_eq)
+    assert np.argmax(ws[0]) != np.argmax(ws[1])
+    pes = wl.morse_pes(OMEGA, D, IDX3, KAPPA * REL)
+    p0, q0, w = oracle.sample_initial(OMEGA, p_eq[0], np.zeros(2), 2000, 0)
+    amp, good = oracle.propagate(pes, OMEGA, p_eq, np.zeros((2, 2)), 10.0, 3000, p0, q0)
+    Eg = wl.cm1(np.linspace(1500.0, 8000.0, 2601))
+    for x in range(2):
+        I, ng = oracle.spectrum(amp[x], w, good, 3000, 10.0, Eg[0], Eg[-1], Eg.size)
+        pk = wl.to_cm1(cf.find_peaks(Eg, I, 0.02))
+        strongest = wl.to_cm1(Eg[np.argmax(I)])
+        exact = wl.to_cm1(E[np.argmax(ws[x])])
+        print(f"chi {x}: strongest SC line {strongest:8.2f}, strongest exact line {exact:8.2f}")
+        assert abs(strongest - exact) < 16.0
+        for e in wl.to_cm1(E[ws[x] > 0.1]):
+            assert np.min(np.abs(pk - e)) < 16.0
