@@ -155,20 +155,20 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
 // Validate scivr_spectrum's arguments (shared with the batch path).
 int check_spectrum_args(const void *amp, int64_t amp_ld, int32_t amp_prec, const double *w, const uint8_t *good,
                         int64_t n_traj, int32_t n_steps, double dt, double E_min, double E_max, int32_t n_E,
-                        int32_t ft_mode, const double *I_out)
+                        int32_t ft_mode, const double *I_out, const char *who)
 {
-    if (!amp || !w || !good || !I_out) return fail(SCIVR_EINVAL, "scivr_spectrum: NULL device pointer");
-    if (n_traj < 1) return fail(SCIVR_EINVAL, "scivr_spectrum: n_traj=%lld < 1", (long long)n_traj);
-    if (n_steps < 1) return fail(SCIVR_EINVAL, "scivr_spectrum: n_steps=%d < 1", n_steps);
-    if (n_E < 2) return fail(SCIVR_EINVAL, "scivr_spectrum: n_E=%d < 2", n_E);
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SCIVR_EINVAL, "scivr_spectrum: dt must be positive");
+    if (!amp || !w || !good || !I_out) return fail(SCIVR_EINVAL, "%s: NULL device pointer", who);
+    if (n_traj < 1) return fail(SCIVR_EINVAL, "%s: n_traj=%lld < 1", who, (long long)n_traj);
+    if (n_steps < 1) return fail(SCIVR_EINVAL, "%s: n_steps=%d < 1", who, n_steps);
+    if (n_E < 2) return fail(SCIVR_EINVAL, "%s: n_E=%d < 2", who, n_E);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SCIVR_EINVAL, "%s: dt must be positive", who);
     if (!std::isfinite(E_min) || !std::isfinite(E_max) || !(E_max > E_min))
-        return fail(SCIVR_EINVAL, "scivr_spectrum: need finite E_min < E_max");
-    if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "scivr_spectrum: amp_ld < n_steps+1");
-    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "scivr_spectrum: amp not 16-byte aligned");
-    if (amp_prec != SCIVR_FP64) return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: amp_prec %d not supported", amp_prec);
+        return fail(SCIVR_EINVAL, "%s: need finite E_min < E_max", who);
+    if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "%s: amp_ld < n_steps+1", who);
+    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "%s: amp not 16-byte aligned", who);
+    if (amp_prec != SCIVR_FP64) return fail(SCIVR_EUNSUPPORTED, "%s: amp_prec %d not supported", who, amp_prec);
     if (ft_mode != SCIVR_FT_FP64 && ft_tc_digits(ft_mode) == 0)
-        return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum: ft_mode %d not supported", ft_mode);
+        return fail(SCIVR_EUNSUPPORTED, "%s: ft_mode %d not supported", who, ft_mode);
     return SCIVR_OK;
 }
 
@@ -382,7 +382,7 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
 {
     {
         const int rc = check_spectrum_args(amp, amp_ld, amp_prec, w, good, n_traj, n_steps, dt, E_min, E_max, n_E,
-                                           ft_mode, I_out);
+                                           ft_mode, I_out, "scivr_spectrum");
         if (rc != SCIVR_OK) return rc;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -423,7 +423,7 @@ int scivr_spectrum_hk(const void *amp, int64_t amp_ld, const uint8_t *good, int6
     // same argument rules as scivr_spectrum (weights are not used: the summands carry them)
     const double one = 1.0;
     int rc = check_spectrum_args(amp, amp_ld, SCIVR_FP64, &one, good, n_traj, n_steps, dt, E_min, E_max, n_E,
-                                 SCIVR_FT_FP64, I_out);
+                                 SCIVR_FT_FP64, I_out, "scivr_spectrum_hk");
     if (rc != SCIVR_OK) return rc;
     if (C_out && reinterpret_cast<uintptr_t>(C_out) % 16 != 0)
         return fail(SCIVR_EINVAL, "scivr_spectrum_hk: C_out not 16-byte aligned");

@@ -186,7 +186,7 @@ int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t f
         int rc = prepare_propagate(it.pes, &it.prm, it.n_traj, it.p0, it.q0, it.amp, it.amp_ld, it.good, nullptr, &L);
         if (rc == SCIVR_OK)
             rc = check_spectrum_args(it.amp, it.amp_ld, SCIVR_FP64, it.w, it.good, it.n_traj, it.prm.n_steps,
-                                     it.prm.dt, it.E_min, it.E_max, it.n_E, ft_mode, it.I_out);
+                                     it.prm.dt, it.E_min, it.E_max, it.n_E, ft_mode, it.I_out, "scivr_batch_create");
         if (rc == SCIVR_OK && it.prm.precision == SCIVR_MIXED && it.pes->dev.F > 16)
             rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: mixed precision is built for F <= 16");
         if (rc == SCIVR_OK && it.prm.amplitude != SCIVR_AMP_TA)

@@ -126,7 +126,8 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
                       const scivr_final_state *fin, PropLaunch *out);
 int check_spectrum_args(const void *amp, int64_t amp_ld, int32_t amp_prec, const double *w, const uint8_t *good,
                         int64_t n_traj, int32_t n_steps, double dt, double E_min, double E_max, int32_t n_E,
-                        int32_t ft_mode, const double *I_out);
+                        int32_t ft_mode, const double *I_out,
+                        const char *who);
 int set_error(int code, const char *msg);
 void clear_error();
 void count_launches(int n);
