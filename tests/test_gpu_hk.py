@@ -46,7 +46,7 @@ def hk_propagate(G, w8, p0, q0, precision=0, kernel=0, stab_tol=None, fin=False)
     torch.cuda.synchronize()
     assert G.scivr_check_status() == G.SCIVR_OK
     a = amp.cpu().numpy()
-    out = dict(amp=a[..., 0] + 1j * a[..., 1], good=good.cpu().numpy(), dev_amp=amp, dev_good=good)
+    out = dict(amp=np.ascontiguousarray(a).view(np.complex128)[..., 0], good=good.cpu().numpy(), dev_amp=amp, dev_good=good)
     if fin:
         out["stab"] = fd["stab"].cpu().numpy()
     return out

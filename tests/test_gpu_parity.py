@@ -58,7 +58,7 @@ def gpu_propagate(G, w8, p0, q0, precision=0, fin=False, kernel=0, stab_tol=None
                       good, precision=precision, stab_tol=tol, fin=fd, kernel=kernel)
     torch.cuda.synchronize()
     a = amp.cpu().numpy()
-    a = a[..., 0] + 1j * a[..., 1]
+    a = np.ascontiguousarray(a).view(np.complex128)[..., 0]
     out = dict(amp=a, good=good.cpu().numpy())
     if fin:
         out.update({k: v.cpu().numpy() for k, v in fd.items()})
