@@ -705,6 +705,8 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the untimed comparison of the spectrum with the FP64 GPU path")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="propagation arithmetic (mixed: FP32 monodromy/potential, FP64 p, q, S, det A)")
     ap.add_argument("--ft", default="bf16x3", choices=list(FT_MODES),
@@ -851,6 +853,37 @@ def main(argv=None):
             dist.destroy_process_group()
         return 0
 
+    # ---- accuracy of the timed configuration (untimed): the same initial conditions through
+    # the FP64 GPU path, itself parity-tested against the FP64 oracle to 1e-9 relative
+    accuracy = None
+    if not args.no_accuracy and (prec != 0 or ftm != 0):
+        ref = scivr.alloc_buffers(w8, device=dev)
+        ref.p0.copy_(bufs.p0)
+        ref.q0.copy_(bufs.q0)
+        ref.w.copy_(bufs.w)
+        scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, ref.p0, ref.q0, ref.amp, K,
+                              ref.good, precision=0, stab_tol=w8.stab_tol, stream=stream, amplitude=amp_mode)
+        if hk:
+            scivr.scivr_spectrum_hk(ref.amp[0], K, ref.good, n, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E,
+                                    ref.I[0], None, ref.n_good, stream=stream)
+        else:
+            scivr.scivr_spectrum(ref.amp[0], K, ref.w, ref.good, n, w8.n_steps, w8.dt, w8.E_min, w8.E_max,
+                                 w8.n_E, ref.I[0], ref.n_good, stream=stream)
+        torch.cuda.synchronize()
+        E = w8.energies()
+        I_ref = ref.I[0].cpu().numpy()
+        I_got = bufs.I[0].cpu().numpy()
+        pk_ref = wl.spectrum_peaks(E, I_ref)
+        accuracy = {
+            "reference": "FP64 GPU propagation and FP64 Fourier step on the same initial conditions "
+                         "(parity-tested against the FP64 oracle to 1e-9 relative)",
+            "n_peaks": int(pk_ref.size),
+            "max_peak_shift_cm1": float(wl.to_cm1(wl.peak_shift(pk_ref, wl.spectrum_peaks(E, I_got)))),
+            "max_rel_error": float(np.max(np.abs(I_got - I_ref)) / np.max(np.abs(I_ref))),
+            "n_good": int(bufs.n_good.item()), "n_good_fp64": int(ref.n_good.item()),
+        }
+        del ref
+
     value = world * n * w8.n_steps / (ms_per_step * 1e-3)
     prop_avg = float(np.mean(prop_ms))
     spec_avg = float(np.mean(spec_ms))
@@ -922,6 +955,7 @@ def main(argv=None):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "accuracy": accuracy,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
