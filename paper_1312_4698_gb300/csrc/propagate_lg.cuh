@@ -75,9 +75,8 @@ template <> struct Vec2<double> { using T = double2; };
 // lane- or chi-dependent indexing never touches the kernel-parameter space.
 template <int F>
 struct CtaConst {
-    double rg[F], irg[F], qw[F], pw[F];
+    double qw[F], pw[F];
     double p_eq[SCIVR_MAX_CHI][F], q_eq[SCIVR_MAX_CHI][F];
-    float rgf[F], irgf[F];                 // FP32 copies: conversions occupy the FP64 pipe
     float Df[F], af[F], w2f[F];            // diagonal parameters in FP32
     double Dd[F], ad[F], w2d[F];           // and in FP64
     float qwf[F], pwf[F];                  // overlap constants in FP32 (mixed path's overlap)
@@ -85,8 +84,6 @@ struct CtaConst {
 };
 
 // Real-typed views of the staged constants.
-template <typename Real, int F> __device__ __forceinline__ Real c_rg(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.rgf[i]; else return c.rg[i]; }
-template <typename Real, int F> __device__ __forceinline__ Real c_irg(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.irgf[i]; else return c.irg[i]; }
 template <typename Real, int F> __device__ __forceinline__ Real c_D(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.Df[i]; else return c.Dd[i]; }
 template <typename Real, int F> __device__ __forceinline__ Real c_a(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.af[i]; else return c.ad[i]; }
 template <typename Real, int F> __device__ __forceinline__ Real c_w2(const CtaConst<F> &c, int i) { if constexpr (sizeof(Real) == 4) return c.w2f[i]; else return c.w2d[i]; }
@@ -172,7 +169,9 @@ struct TensorLayout {
     static constexpr int P = F * (F + 1) / 2;
     static constexpr int S3 = vec_len<Real>(F);   // short rows: fewer loads outweigh a 2-way conflict
     static constexpr int S4 = row_stride<Real>(P);
-    static constexpr size_t bytes = ((sizeof(Real) * (size_t)(P * S3 + P * S4)) + 15) & ~(size_t)15;
+    // after the tensors: the Herman-Kluk matrix coefficients acoef[a][b][4] =
+    // (1/2) {rg_a/rg_b, rg_b/rg_a, -rg_a rg_b, 1/(rg_a rg_b)}, rg = sqrt(gamma)
+    static constexpr size_t bytes = ((sizeof(Real) * (size_t)(P * S3 + P * S4 + 4 * F * F)) + 15) & ~(size_t)15;
 };
 
 template <int F, int G, typename Real>
@@ -216,6 +215,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     constexpr int S3 = TL::S3, S4 = TL::S4;
     Real *sT3 = reinterpret_cast<Real *>(smem_raw);
     Real *sT4 = sT3 + P * S3;
+    Real *sAc = sT4 + P * S4;   // Herman-Kluk matrix coefficients [a][b][4] (16-byte aligned: P * (S3 + S4) is a vector multiple)
     size_t off = TL::bytes;
     CtaConst<F> &cc = *reinterpret_cast<CtaConst<F> *>(smem_raw + off);
     off += (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
@@ -241,14 +241,10 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int a = 0; a < F; ++a) {
-            cc.rg[a] = A.rg[a];
-            cc.irg[a] = A.irg[a];
             cc.qw[a] = A.qw[a];
             cc.pw[a] = A.pw[a];
             cc.qwf[a] = (float)A.qw[a];
             cc.pwf[a] = (float)A.pw[a];
-            cc.rgf[a] = (float)A.rg[a];
-            cc.irgf[a] = (float)A.irg[a];
             cc.Dd[a] = pes.D[a];
             cc.ad[a] = pes.a[a];
             cc.w2d[a] = pes.omega[a] * pes.omega[a];
@@ -256,6 +252,17 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             cc.af[a] = pes.a_f[a];
             cc.w2f[a] = pes.omega_f[a] * pes.omega_f[a];
         }
+#pragma unroll
+        for (int a = 0; a < F; ++a)
+#pragma unroll
+            for (int b = 0; b < F; ++b) {
+                const Real rga = (Real)A.rg[a], irga = (Real)A.irg[a], rgb = (Real)A.rg[b], irgb = (Real)A.irg[b];
+                Real *k = sAc + 4 * (a * F + b);
+                k[0] = Real(0.5) * (rga * irgb);
+                k[1] = Real(0.5) * (rgb * irga);
+                k[2] = Real(-0.5) * (rga * rgb);
+                k[3] = Real(0.5) * (irga * irgb);
+            }
 #pragma unroll
         for (int x = 0; x < SCIVR_MAX_CHI; ++x)
 #pragma unroll
@@ -494,13 +501,18 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     const Real mpq = __shfl_sync(FULL, Mp[a], src);
                     const Real mqq = __shfl_sync(FULL, Mq[a], src);
                     if (g < F) {
-                        const Real rga = c_rg<Real>(cc, a), irga = c_irg<Real>(cc, a);
-                        const Real rgb = c_rg<Real>(cc, g), irgb = c_irg<Real>(cc, g);
-                        const Real re = fma(rga * irgb, mqq, (rgb * irga) * Mp[a]);
-                        const Real im = fma(-(rga * rgb), Mq[a], (irga * irgb) * mpq);
+                        using VT = typename V16<Real>::T;
+                        constexpr int NV = V16<Real>::N;
+                        Real k4[4];
+#pragma unroll
+                        for (int j0 = 0; j0 < 4; j0 += NV) {
+                            const VT kv = *reinterpret_cast<const VT *>(sAc + 4 * (a * F + g) + j0);
+#pragma unroll
+                            for (int j = 0; j < NV; ++j) k4[j0 + j] = vcomp<Real>(kv, j);
+                        }
                         R2 v;
-                        v.x = Real(0.5) * re;
-                        v.y = Real(0.5) * im;
+                        v.x = fma(k4[0], mqq, k4[1] * Mp[a]);
+                        v.y = fma(k4[2], Mq[a], k4[3] * mpq);
                         sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = v;
                     }
                 }
