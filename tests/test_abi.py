@@ -123,3 +123,115 @@ def test_plain_scivr_spectrum_arguments_validated(lib):
         rc = scivr._lib.scivr_spectrum_hk(a["amp"], a["amp_ld"], a["good"], a["n_traj"], a["n_steps"], a["dt"],
                                           a["E_min"], a["E_max"], a["n_E"], a["I_out"], a["C_out"], None, None)
         assert rc == scivr.SCIVR_EINVAL, over
+
+
+def test_remaining_entry_points_validate_before_any_launch(lib):
+    """Sampling, the wait self-test, the allocation-free spectrum and the batch plan
+    reject bad arguments on the host, name the failing call, and leave no plan behind."""
+    from paper_1312_4698_gb300 import scivr
+    L = scivr._lib
+    fake = 0x1000
+    g = np.ones(3)
+    rc = L.scivr_sample_initial(None, g.ctypes.data, g.ctypes.data, g.ctypes.data, 8, 0, fake, fake, fake, None)
+    assert rc == scivr.SCIVR_EINVAL and "scivr_sample_initial" in scivr.last_error()
+    for s in (0.0, -1.0, 10.5, float("nan")):
+        assert L.scivr_selftest_wait_timeout(s, None) == scivr.SCIVR_EINVAL, s
+    assert L.scivr_pes_modes(None) == 0
+
+    base = dict(amp=fake, amp_ld=11, prec=0, n_traj=4, n_steps=10, dt=10.0, E_min=0.0, E_max=0.1, n_E=16, ft=0)
+    for over, code in ((dict(n_E=1 << 20), scivr.SCIVR_EINVAL), (dict(n_E=1), scivr.SCIVR_EINVAL),
+                       (dict(amp=fake + 8), scivr.SCIVR_EINVAL), (dict(E_max=float("inf")), scivr.SCIVR_EINVAL),
+                       (dict(prec=1), scivr.SCIVR_EUNSUPPORTED), (dict(ft=2), scivr.SCIVR_EUNSUPPORTED)):
+        a = dict(base, **over)
+        rc = L.scivr_spectrum_noalloc(a["amp"], a["amp_ld"], a["prec"], fake, fake, a["n_traj"], a["n_steps"],
+                                      a["dt"], a["E_min"], a["E_max"], a["n_E"], a["ft"], fake, None, None)
+        assert rc == code, over
+        assert scivr.last_error().startswith("scivr_spectrum_noalloc"), over
+    L.scivr_spectrum_noalloc(fake, 11, 0, fake, fake, 4, 10, 10.0, 0.0, 0.1, 1 << 20, 0, fake, None, None)
+    assert "scratch limit" in scivr.last_error()
+
+    out = C.c_void_p(7)
+    assert L.scivr_batch_create(None, 1, 0, C.byref(out)) == scivr.SCIVR_EINVAL
+    items = (scivr.scivr_batch_item * 2)()
+    assert L.scivr_batch_create(items, 0, 0, C.byref(out)) == scivr.SCIVR_EINVAL
+    assert L.scivr_batch_create(items, 2, 99, C.byref(out)) == scivr.SCIVR_EUNSUPPORTED
+    assert not out.value
+    assert L.scivr_batch_create(items, 2, 0, C.byref(out)) == scivr.SCIVR_EINVAL
+    assert scivr.last_error().startswith("scivr_batch_create: item 0: scivr_propagate: NULL")
+    assert not out.value
+    n = C.c_int32(-1)
+    assert L.scivr_batch_info(None, -1, C.byref(n), None, None, None) == scivr.SCIVR_EINVAL
+    assert L.scivr_batch_destroy(None) == scivr.SCIVR_OK
+
+
+def test_potential_descriptor_checks(lib):
+    """Each malformed potential descriptor is refused with SCIVR_EINVAL or
+    SCIVR_EUNSUPPORTED before any device allocation."""
+    from paper_1312_4698_gb300 import scivr
+    from paper_1312_4698_gb300 import workloads as wl
+    L = scivr._lib
+    d0 = wl.config_f6().pes
+    keep = []
+
+    def desc(**over):
+        arr = dict(omega=d0.omega, D=d0.D, a=d0.a, idx3=d0.idx3, c3=d0.c3, idx4=d0.idx4, c4=d0.c4)
+        arr.update({k: v for k, v in over.items() if k in arr and v is not None})
+        arr = {k: np.ascontiguousarray(v, dtype=np.int32 if k.startswith("idx") else np.float64)
+               for k, v in arr.items()}
+        keep.append(arr)
+        n3 = over.get("n3", arr["c3"].size)
+        n4 = over.get("n4", arr["c4"].size)
+        ptr = lambda k: None if over.get(k, 0) is None else arr[k].ctypes.data
+        return scivr.scivr_pes_desc(over.get("F", d0.F), over.get("kind", scivr.SCIVR_PES_POLY),
+                                    over.get("diag_kind", d0.diag_kind), ptr("omega"), ptr("D"), ptr("a"),
+                                    n3, ptr("idx3"), ptr("c3"), n4, ptr("idx4"), ptr("c4"))
+
+    bad_c3 = d0.c3.copy(); bad_c3[5] = np.nan
+    bad_c4 = d0.c4.copy(); bad_c4[-1] = np.inf
+    bad_i4 = d0.idx4.copy(); bad_i4[3] = bad_i4[3][::-1]
+    bad_om = d0.omega.copy(); bad_om[2] = 0.0
+    bad_a = d0.a.copy(); bad_a[0] = -1.0
+    cases = [
+        (dict(kind=1), scivr.SCIVR_EUNSUPPORTED),
+        (dict(diag_kind=7), scivr.SCIVR_EINVAL),
+        (dict(omega=bad_om), scivr.SCIVR_EINVAL),
+        (dict(a=bad_a), scivr.SCIVR_EINVAL),
+        (dict(n3=-1), scivr.SCIVR_EINVAL),
+        (dict(idx3=None), scivr.SCIVR_EINVAL),
+        (dict(c4=None), scivr.SCIVR_EINVAL),
+        (dict(c3=bad_c3), scivr.SCIVR_EINVAL),
+        (dict(c4=bad_c4), scivr.SCIVR_EINVAL),
+        (dict(idx4=bad_i4), scivr.SCIVR_EINVAL),
+        (dict(F=-3), scivr.SCIVR_EINVAL),
+    ]
+    for over, code in cases:
+        h = C.c_void_p(7)
+        rc = L.scivr_create_pes(C.byref(desc(**over)), C.byref(h))
+        assert rc == code, over
+        assert not h.value, over
+        assert scivr.last_error().startswith("scivr_create_pes"), over
+    assert L.scivr_create_pes(None, None) == scivr.SCIVR_EINVAL
+
+
+def test_last_error_is_per_thread(lib):
+    """scivr_last_error belongs to the calling thread: an error raised in one thread
+    does not show in another thread's message."""
+    import threading
+    from paper_1312_4698_gb300 import scivr
+    L = scivr._lib
+    seen = {}
+
+    def worker():
+        seen["before"] = scivr.last_error()
+        L.scivr_selftest_wait_timeout(-1.0, None)
+        seen["after"] = scivr.last_error()
+
+    L.scivr_batch_info(None, -1, None, None, None, None)
+    mine = scivr.last_error()
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert mine.startswith("scivr_batch_info")
+    assert seen["before"] == ""
+    assert seen["after"].startswith("scivr_selftest_wait_timeout")
+    assert scivr.last_error() == mine
