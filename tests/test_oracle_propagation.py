@@ -50,6 +50,47 @@ def test_harmonic_amplitude_closed_form(omegas):
         assert abs(r["S"][-1] - 0.5 * np.sum(r["p"] * r["q"] - p0 * q0)) < 1e-10
 
 
+def test_phase_unwrapping_when_arg_det_A_turns_more_than_pi_per_step():
+    """24 harmonic modes at 2900-3900 cm^-1 with dt = 10 au turn arg det A by 3.7 rad
+    per step, so a principal-value unwrapping of the bare increments loses whole turns.
+    The oracle unwraps relative to the reference rotation exp(-i sum_i gamma_i t) and
+    must still give the closed-form theta_c = -c sum_i theta_i and amplitude series."""
+    omegas = wl.cm1(np.linspace(2900.0, 3900.0, 24))
+    F, dt, n_steps = omegas.size, 10.0, 600
+    thetas, gts = zip(*[cf.harmonic_rotation(w, dt) for w in omegas])
+    gts = np.array(gts)
+    assert np.sum(thetas) > np.pi
+    pes = wl.harmonic_pes(omegas)
+    p_eq, q_eq = np.sqrt(gts), np.zeros(F)
+    rng = np.random.default_rng(5)
+    q0 = rng.normal(0, 1, F) / np.sqrt(gts)
+    p0 = p_eq + rng.normal(0, 1, F) * np.sqrt(gts)
+    r = oracle.propagate_one(pes, gts, p_eq, q_eq, dt, n_steps, p0, q0)
+    ref, th, _ = cf.harmonic_amplitude(omegas, dt, n_steps, p0, q0, p_eq, q_eq)
+    c = np.arange(n_steps + 1)
+    exact = -c * np.sum(th)
+    assert r["good"]
+    assert np.max(np.abs(r["amp"][0] - ref)) < 1e-10
+    assert np.max(np.abs(r["theta"] - exact)) < 1e-9
+    bare = np.angle(r["detA"])
+    naive = np.concatenate([[0.0], np.cumsum(np.angle(np.exp(1j * np.diff(bare))))])
+    assert np.max(np.abs(naive - exact)) > 1.0       # the case the reference rotation exists for
+
+
+def test_recipe_surface_with_24_modes_stays_symplectic():
+    """The F = 24 surface of the synthetic recipe (2576 cubic and 17526 quartic
+    couplings): along a Husimi trajectory M^T J M = J and det M = 1 to rounding."""
+    w8 = wl.config_generic(24, 0, 1, 300)
+    assert (w8.pes.c3.size, w8.pes.c4.size) == (2576, 17526)
+    p0, q0, _ = oracle.sample_initial(w8.gamma, w8.p_eq[0], w8.q_eq[0], 1, 0)
+    r = oracle.propagate_one(w8.pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], w8.dt, w8.n_steps, p0[:, 0], q0[:, 0])
+    M = r["M"]
+    J = _J(24)
+    assert r["good"]
+    assert np.max(np.abs(M.T @ J @ M - J)) / max(1.0, np.max(np.abs(M)) ** 2) < 1e-12
+    assert abs(r["detM"][-1] - 1.0) < 1e-9
+
+
 def test_harmonic_prefactor_limits_with_frequency_widths():
     """With gamma = omega: |C_t| -> 1 and phi_t -> -sum omega t / 2 as dt -> 0 (O((omega dt)^4))."""
     omegas = wl.cm1([1600.0, 3650.0])
