@@ -243,6 +243,24 @@ def test_runaway_trajectory_is_flagged_bad():
     assert not r["good"]
 
 
+def test_non_finite_initial_condition_is_flagged_and_excluded():
+    """A NaN or infinite starting coordinate gives a bad trajectory (never a crash), and
+    the spectrum over the set equals the spectrum of the set without that trajectory."""
+    w8 = wl.config_f3(n_traj=12, n_steps=200, n_E=120)
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, 4)
+    p0[1, 3] = np.nan
+    q0[2, 7] = np.inf
+    amp, good = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0)
+    assert good[3] == 0 and good[7] == 0 and good.sum() == w8.n_traj - 2
+    I, ng = oracle.spectrum(amp[0], w, good, w8.n_steps, w8.dt, w8.E_min, w8.E_max, w8.n_E)
+    keep = np.setdiff1d(np.arange(w8.n_traj), [3, 7])
+    I2, ng2 = oracle.spectrum(np.ascontiguousarray(amp[0][keep]), w[keep], good[keep], w8.n_steps, w8.dt,
+                              w8.E_min, w8.E_max, w8.n_E)
+    assert ng == ng2 == w8.n_traj - 2
+    assert np.all(np.isfinite(I))
+    assert np.max(np.abs(I - I2)) <= 1e-14 * np.max(np.abs(I2))
+
+
 def test_batch_matches_single_and_chi_layout():
     F = 3
     pes = _anharmonic(F)
