@@ -4,8 +4,8 @@ trained network gains over the method without it.
 
 The network learns the coupling polynomial of the F = 6 surface (cubic and
 quartic terms) on top of its Morse diagonal.  "Without it" is the same
-TA-SC-IVR run on the diagonal alone; the judge is the FP64 oracle on the full
-analytic surface.
+TA-SC-IVR run on the diagonal alone; both are measured against the FP64 oracle
+on the full analytic surface.
 """
 import numpy as np
 import pytest
