@@ -35,3 +35,25 @@ def test_reference_arm_reports_unavailable_workloads():
     assert out.returncode == 0
     d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_clock_summary_reads_throttle_reasons():
+    """The clock record beside every bench number: median SM clock, maximum clock and the
+    throttle reasons seen active (from nvidia-smi's csv, noheader, nounits lines)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    c = bench.ClockSampler(0)
+    c.lines = [
+        "2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "1965, 2070, 1395.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "[N/A], 2070, 0.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # unreadable sample
+        "2040, 2070, 1200.3, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "truncated line",
+    ]
+    s = c.summary()
+    assert s == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines.append("1200, 2070, 1400.0, 0x48, Active, Not Active, Active, Not Active")
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
