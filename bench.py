@@ -708,7 +708,7 @@ def main(argv=None):
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the untimed comparison of the spectrum with the FP64 GPU path")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
-                    help="propagation arithmetic (mixed: FP32 monodromy/potential, FP64 p, q, S, det A)")
+                    help="propagation arithmetic (mixed: FP32 monodromy, potential and determinants; FP64 p, q, S, phase)")
     ap.add_argument("--ft", default="bf16x3", choices=list(FT_MODES),
                     help="Fourier step: fp64 CUDA cores or tensor-core BF16 digit splits")
     ap.add_argument("--n-traj", type=int, default=None, help="override the workload's trajectory count")

@@ -53,13 +53,14 @@ enum { SCIVR_PES_POLY = 0 };      /* diagonal + cubic + quartic coupling monomia
 
 /* Arithmetic of the propagation. */
 enum { SCIVR_FP64 = 0,            /* everything in IEEE double */
-       SCIVR_MIXED = 1 };         /* monodromy + potential in FP32; p, q, S,
-                                     prefactor determinant and phase in FP64 */
+       SCIVR_MIXED = 1 };         /* monodromy, potential, det M and the det A
+                                     elimination in FP32; p, q, S and the
+                                     continuous prefactor phase in FP64 */
 
 /* Kernel schedule of scivr_propagate. */
 enum { SCIVR_KERNEL_AUTO = 0,     /* library choice (tuned per F, precision, n_traj) */
        SCIVR_KERNEL_THREAD = 1,   /* one thread per trajectory */
-       SCIVR_KERNEL_GROUP = 2 };  /* a lane group per trajectory, batched FP64 determinants */
+       SCIVR_KERNEL_GROUP = 2 };  /* a lane group per trajectory, batched determinants */
 
 /* Arithmetic of the time -> energy Fourier step. */
 enum { SCIVR_FT_FP64 = 0,         /* FP64 fused-multiply-add contraction (CUDA cores) */

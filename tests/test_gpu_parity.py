@@ -328,8 +328,8 @@ def test_propagate_several_reference_states_both_schedules(G, kernel):
 
 
 # ---------------------------------------------------------------------------
-# Mixed precision (FP32 monodromy / potential / det M; FP64 p, q, S, det A,
-# phase).  Bounds: amplitudes within 5e-2 of the trajectory's largest
+# Mixed precision (FP32 monodromy / potential / det M / det A elimination;
+# FP64 p, q, S, continuous phase).  Bounds: amplitudes within 5e-2 of the trajectory's largest
 # amplitude (FP32 rounding of the force and of M perturbs the trajectory and
 # the prefactor phase; measured 3e-3 typical, 2.3e-2 worst over 16384
 # trajectories of the F=6 workload); spectra within 1 cm^-1 per peak.
