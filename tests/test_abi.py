@@ -235,3 +235,19 @@ def test_last_error_is_per_thread(lib):
     assert seen["before"] == ""
     assert seen["after"].startswith("scivr_selftest_wait_timeout")
     assert scivr.last_error() == mine
+
+
+def test_binding_constants_equal_the_header_values():
+    """Every enumerator and #define of include/*.h that the binding mirrors has the same value."""
+    import glob
+    from paper_1312_4698_gb300 import scivr
+    text = "".join(open(f).read() for f in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(SCIVR_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    values.update({m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(SCIVR_[A-Z0-9_]+)\s+(-?\d+)", text)})
+    assert len(values) >= 20
+    mirrored = [k for k in values if hasattr(scivr, k)]
+    assert {"SCIVR_MIXED", "SCIVR_FT_TC_BF16X3", "SCIVR_AMP_HK", "SCIVR_KERNEL_GROUP", "SCIVR_MAX_F",
+            "SCIVR_ETIMEOUT"} <= set(mirrored)
+    for k in mirrored:
+        assert getattr(scivr, k) == values[k], k
