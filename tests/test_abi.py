@@ -251,3 +251,35 @@ def test_binding_constants_equal_the_header_values():
             "SCIVR_ETIMEOUT"} <= set(mirrored)
     for k in mirrored:
         assert getattr(scivr, k) == values[k], k
+
+
+def test_binding_struct_layouts_match_the_headers(tmp_path):
+    """Each ctypes mirror of a header struct has the C compiler's size and field offsets
+    (a probe compiled with gcc against include/*.h)."""
+    import shutil
+    import subprocess
+    from paper_1312_4698_gb300 import scivr
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(scivr, n) for n in ("scivr_pes_desc", "scivr_prop_params", "scivr_final_state",
+                                           "scivr_batch_item", "scivr_mlp_desc")]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "scivr.h"', '#include "scivr_mlp.h"',
+             'int main(void) {']
+    for S in structs:
+        lines.append(f'  printf("{S.__name__} size %zu\\n", sizeof({S.__name__}));')
+        for f in S._fields_:
+            lines.append(f'  printf("{S.__name__} {f[0]} %zu\\n", offsetof({S.__name__}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = ln.split()
+        got[(name, field)] = int(val)
+    for S in structs:
+        assert got[(S.__name__, "size")] == C.sizeof(S), S.__name__
+        for f in S._fields_:
+            assert got[(S.__name__, f[0])] == getattr(S, f[0]).offset, (S.__name__, f[0])
