@@ -283,3 +283,43 @@ def test_binding_struct_layouts_match_the_headers(tmp_path):
         assert got[(S.__name__, "size")] == C.sizeof(S), S.__name__
         for f in S._fields_:
             assert got[(S.__name__, f[0])] == getattr(S, f[0]).offset, (S.__name__, f[0])
+
+
+def _c_kind(decl):
+    """(kind, bytes) of a C parameter or return type as written in include/*.h."""
+    t = " ".join(decl.replace("const", " ").split())
+    t = re.sub(r"\s+\w+$", "", t) if not t.endswith("*") and len(t.split()) > 1 else t
+    if "*" in t or t in ("scivr_pes", "scivr_batch"):
+        return ("ptr", C.sizeof(C.c_void_p))
+    table = {"int": ("int", 4), "int32_t": ("int", 4), "int64_t": ("int", 8), "uint64_t": ("uint", 8),
+             "uint8_t": ("uint", 1), "double": ("float", 8), "float": ("float", 4)}
+    return table[t]
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return None
+    if t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer):
+        return ("ptr", C.sizeof(C.c_void_p))
+    if t in (C.c_double, C.c_float):
+        return ("float", C.sizeof(t))
+    signed = t(-1).value < 0
+    return ("int" if signed else "uint", C.sizeof(t))
+
+
+def test_binding_signatures_match_the_headers():
+    """argtypes and restype of every declared entry point agree with the C declaration
+    (pointer, signed/unsigned integer or floating point, and width)."""
+    import glob
+    from paper_1312_4698_gb300 import scivr
+    text = "".join(open(f).read() for f in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    decls = re.findall(r"([A-Za-z_][\w\s\*]*?)\b(scivr_\w+)\s*\(([^;{]*?)\)\s*;", text)
+    assert len(decls) >= 20
+    for ret, name, args in decls:
+        fn = getattr(scivr._lib, name)
+        params = [a.strip() for a in args.split(",") if a.strip() and a.strip() != "void"]
+        assert fn.argtypes is not None and len(fn.argtypes) == len(params), name
+        for decl, t in zip(params, fn.argtypes):
+            assert _ctypes_kind(t) == _c_kind(decl), (name, decl, t)
+        assert _ctypes_kind(fn.restype) == _c_kind(ret.strip()), (name, ret, fn.restype)
