@@ -157,10 +157,14 @@ int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
  *   amp[x][j][c] = <chi_x|p_j(c dt), q_j(c dt)> exp(i (S_j(c dt) + phi_j(c dt)))
  * (the summand of Eq. I(E)_discreto without the energy factor).  With
  * prm->amplitude = SCIVR_AMP_HK it records instead the Herman-Kluk summand of
- * Eq. I(E)_SCIVR times the sampling weight w_j = 1/|<p_j(0) q_j(0)|chi_x>|^2,
- *   amp[x][j][c] = C_j(c dt) e^{i S_j(c dt)} <chi_x|p_j(c dt), q_j(c dt)> / <chi_x|p_j(0), q_j(0)>,
+ * Eq. I(E)_SCIVR times the importance weight of the Husimi density of the first
+ * reference state, w_j = 1/|<p_j(0) q_j(0)|chi_0>|^2 (the density scivr_sample_initial
+ * draws from when given chi_0; every reference state shares the trajectories),
+ *   amp[x][j][c] = C_j(c dt) e^{i S_j(c dt)} <chi_x|p_j(c dt), q_j(c dt)> <p_j(0), q_j(0)|chi_x> w_j,
  * C = |det A|^{1/2} e^{i theta/2} (Eq. prefactor on the branch theta follows),
- * whose mean over trajectories is <chi_x|e^{-iHt}|chi_x> (scivr_spectrum_hk).  Integrator:
+ * whose mean over trajectories drawn from that density is <chi_x|e^{-iHt}|chi_x>
+ * (scivr_spectrum_hk).  For x = 0 the summand is C e^{iS} <chi_0|p q> / <chi_0|p0 q0>,
+ * exactly 1 at c = 0.  Integrator:
  * Yoshida's fourth-order triple jump of exact drift/kick sub-flows for (p, q),
  * the action S and the monodromy M (Sec. III.A).  phi = theta/2 with theta the
  * continuous arg det A of the Herman-Kluk matrix (Eq. prefactor), unwrapped

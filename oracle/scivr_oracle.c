@@ -443,15 +443,22 @@ int or_propagate_one(const or_pes *pes, const or_prop *prm, const double *p0, co
                 double complex lo = or_log_overlap(F, prm->gamma, prm->p_eq + x * F,
                                                    prm->q_eq + x * F, p, q);
                 if (prm->amplitude == 1) {
-                    /* Herman-Kluk summand of Eq. I(E)_SCIVR times the sampling weight
-                     * w = 1 / |<p0 q0|chi>|^2:  C_t e^{i S_t} <chi|p_t q_t> <p0 q0|chi> w,
+                    /* Herman-Kluk summand of Eq. I(E)_SCIVR times the importance weight
+                     * of the density the initial conditions were drawn from, the Husimi
+                     * density of the first reference state:
+                     *   C_t e^{i S_t} <chi_x|p_t q_t> <p0 q0|chi_x> w,  w = 1 / |<p0 q0|chi_0>|^2,
                      * with C_t = |det A|^{1/2} e^{i theta/2} (Eq. prefactor on the branch
-                     * that theta follows) */
+                     * that theta follows).  Every reference state shares the trajectories,
+                     * so every state takes the same w (for x = 0 the summand is
+                     * C_t e^{i S_t} <chi|p_t q_t> / <chi|p0 q0>). */
                     double complex lo0 = or_log_overlap(F, prm->gamma, prm->p_eq + x * F,
                                                         prm->q_eq + x * F, p0, q0);
+                    double complex lo00 = x == 0 ? lo0 : or_log_overlap(F, prm->gamma, prm->p_eq,
+                                                                        prm->q_eq, p0, q0);
                     double complex Ct = sqrt(cabs(detA)) * cexp(0.5 * I * theta);
                     double complex ov0 = cexp(lo0);
-                    double w0 = 1.0 / (creal(ov0) * creal(ov0) + cimag(ov0) * cimag(ov0));
+                    double complex ov00 = cexp(lo00);
+                    double w0 = 1.0 / (creal(ov00) * creal(ov00) + cimag(ov00) * cimag(ov00));
                     amp[x * amp_chi_stride + step] = Ct * cexp(I * S) * cexp(lo) * conj(ov0) * w0;
                 } else {
                     double phase = cimag(lo) + S + 0.5 * theta;

@@ -30,7 +30,7 @@ struct State {
 
 // Amplitude of step `step` for every reference state: the time-averaged summand,
 // or with SCIVR_AMP_HK the Herman-Kluk summand (|det A|^{1/2} = sqrt(absA), divided
-// by the initial overlap).
+// by the initial overlap times the sampling weight, chi_log_overlap0).
 template <int F>
 __device__ __forceinline__ void record(const PropLaunch &L, int64_t j, int step, const double (&p)[F],
                                        const double (&q)[F], double S, double theta, double absA)

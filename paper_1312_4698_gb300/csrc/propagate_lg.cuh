@@ -191,7 +191,7 @@ struct WarpShared {
                                            // in the mixed path, where the overlap is evaluated in FP32
     double Sj[JOBS];                        // action per job
     double lnA[JOBS];                       // log |det A|^{1/2} per job (Herman-Kluk summand only)
-    double2 ov0[SCIVR_MAX_CHI][T];          // log <chi|p0 q0> per trajectory (Herman-Kluk summand only)
+    double2 ov0[SCIVR_MAX_CHI][T];          // log of the Herman-Kluk summand's divisor per trajectory
 };
 
 // One CTA's share of a propagation: trajectories (cta * WARPS + warp) * T + t.
@@ -323,6 +323,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 
     // amplitude at c = 0 (M = I, S = 0, theta = 0): lane 0 of each group
     if (g == 0 && active) {
+        double re00 = 0.0;   // Re log <chi_0|p0 q0>
         for (int x = 0; x < A.n_chi; ++x) {
             double re = 0.0, im = 0.0;
             for (int a = 0; a < F; ++a) {
@@ -332,13 +333,20 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 re = fma(-cc.pw[a] * dp, dp, re);
                 im = fma(0.5 * (cc.p_eq[x][a] + pa), dq, im);
             }
-            sh.ov0[x][t] = make_double2(re, im);
+            if (x == 0) re00 = re;
+            // what the Herman-Kluk summand divides by: <chi_x|p0 q0> |<p0 q0|chi_0>|^2 / |<p0 q0|chi_x>|^2,
+            // i.e. the initial overlap times the importance weight of the sampling density (the first
+            // reference state's); its real logarithm 2 re00 - re equals re for x = 0
+            const double rdiv = x == 0 ? re : 2.0 * re00 - re;
+            sh.ov0[x][t] = make_double2(rdiv, im);
             double sn, cs;
             sincos(im, &sn, &cs);
             const double mag = exp(re);
-            // the Herman-Kluk summand is exactly 1 at t = 0 (C = 1, S = 0, the overlaps cancel)
+            // the Herman-Kluk summand at t = 0 (C = 1, S = 0) is |<chi_x|p0 q0>|^2 / |<chi_0|p0 q0>|^2,
+            // exactly 1 for x = 0
             L.amp[x * L.chi_stride + jl * L.amp_ld] =
-                A.amplitude == SCIVR_AMP_HK ? make_double2(1.0, 0.0) : make_double2(mag * cs, mag * sn);
+                A.amplitude == SCIVR_AMP_HK ? make_double2(x == 0 ? 1.0 : exp(re - rdiv), 0.0)
+                                            : make_double2(mag * cs, mag * sn);
         }
     }
 
@@ -697,7 +705,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     }
                     double ph = fma(0.5, theta, (double)imf + S);
                     if (A.amplitude == SCIVR_AMP_HK) {
-                        // Herman-Kluk summand: |det A|^{1/2} and the division by <chi|p0 q0>
+                        // Herman-Kluk summand: |det A|^{1/2} and the division by the initial
+                        // overlap times the sampling weight
                         const double2 o = sh.ov0[x][t];
                         rf = (float)((double)rf - o.x + sh.lnA[ln]);
                         ph -= o.y;

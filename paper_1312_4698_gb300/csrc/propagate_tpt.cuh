@@ -324,7 +324,8 @@ __global__ void __launch_bounds__(64) k_propagate_tpt_fp64(const PropLaunch L)
             }
             double ph = im + S + 0.5 * theta;
             if (A.amplitude == SCIVR_AMP_HK) {
-                // Herman-Kluk summand: |det A|^{1/2} and the division by <chi|p0 q0>
+                // Herman-Kluk summand: |det A|^{1/2} and the division by the initial
+                // overlap times the sampling weight (chi_log_overlap0)
                 double re0, im0;
                 chi_log_overlap0<F>(A, L.p0, L.q0, n, j, x, re0, im0);
                 re = re - re0 + 0.5 * log(hypot(detA.re, detA.im));

@@ -138,21 +138,38 @@ cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, 
                                      int *counter, int n_sm, cudaStream_t s);
 int batch_warp_candidates(int F, int *out);   // returns the count (<= 2)
 
-// log <chi_x|p0_j, q0_j> = re0 + i im0 (Eq. coherent_state with unit-norm
-// states): the initial overlap that the Herman-Kluk summand divides by.
+// log <chi_x|p0_j, q0_j> (Eq. coherent_state with unit-norm states).
 template <int F>
-__device__ __forceinline__ void chi_log_overlap0(const PropArgs &A, const double *p0, const double *q0,
-                                                 int64_t n, int64_t j, int x, double &re0, double &im0)
+__device__ __forceinline__ void chi_log_overlap_at(const PropArgs &A, const double *p0, const double *q0,
+                                                   int64_t n, int64_t j, int x, double &re, double &im)
 {
-    re0 = 0.0;
-    im0 = 0.0;
+    re = 0.0;
+    im = 0.0;
 #pragma unroll
     for (int a = 0; a < F; ++a) {
         const double pa = p0[a * n + j], qa = q0[a * n + j];
         const double dq = A.q_eq[x * F + a] - qa, dp = A.p_eq[x * F + a] - pa;
-        re0 = fma(-A.qw[a] * dq, dq, re0);
-        re0 = fma(-A.pw[a] * dp, dp, re0);
-        im0 = fma(0.5 * (A.p_eq[x * F + a] + pa), dq, im0);
+        re = fma(-A.qw[a] * dq, dq, re);
+        re = fma(-A.pw[a] * dp, dp, re);
+        im = fma(0.5 * (A.p_eq[x * F + a] + pa), dq, im);
+    }
+}
+
+// The logarithm re0 + i im0 that the Herman-Kluk summand of reference state x
+// divides by.  The summand is C e^{iS} <chi_x|p_t q_t> <p0 q0|chi_x> / |<p0 q0|chi_0>|^2:
+// the initial conditions are drawn from the Husimi density of the first reference
+// state, so that density's inverse is every state's importance weight.  Hence
+// im0 = Im log <chi_x|p0 q0> and re0 = 2 Re log <chi_0|p0 q0> - Re log <chi_x|p0 q0>
+// (for x = 0 exactly Re log <chi_0|p0 q0>, since 2a - a = a in floating point).
+template <int F>
+__device__ __forceinline__ void chi_log_overlap0(const PropArgs &A, const double *p0, const double *q0,
+                                                 int64_t n, int64_t j, int x, double &re0, double &im0)
+{
+    chi_log_overlap_at<F>(A, p0, q0, n, j, x, re0, im0);
+    if (x != 0) {
+        double r00, i00;
+        chi_log_overlap_at<F>(A, p0, q0, n, j, 0, r00, i00);
+        re0 = 2.0 * r00 - re0;
     }
 }
 

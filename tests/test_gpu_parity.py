@@ -507,7 +507,9 @@ def test_wide_group_several_reference_states_and_hk(G):
                                amplitude=oracle.AMP_HK)
     gh = hk_propagate(G, w8, p0, q0, precision=1, stab_tol=MIXED_STAB_TOL)
     sel = rgh.astype(bool) & gh["good"].astype(bool)
-    assert np.all(gh["amp"][:, :, 0] == 1.0)
+    # t = 0: 1 for the sampling state, the density ratio |<chi_1|p0 q0>|^2 / |<chi_0|p0 q0>|^2 for the other
+    assert np.all(gh["amp"][0, :, 0] == 1.0)
+    assert np.max(np.abs(gh["amp"][1, :, 0] - rh[1, :, 0]) / np.abs(rh[1, :, 0])) < 1e-12
     assert amp_err(gh["amp"][:, sel], rh[:, sel], np.ones(sel.sum(), np.uint8)) < 5e-2
 
 

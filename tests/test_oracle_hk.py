@@ -72,6 +72,38 @@ def test_displaced_coherent_state_autocorrelation():
     assert abs(mean[0] - 1.0) < 1e-14
 
 
+@pytest.mark.parametrize("dq,dp", [(0.5, 0.0), (0.0, 0.5), (0.7, -0.7)])
+def test_reference_states_share_trajectories_sampled_around_the_first(dq, dp):
+    """Two reference states on one set of trajectories drawn from the first state's
+    Husimi density: the importance weight is that density's, so the mean of the second
+    state's summands must still be its own exact autocorrelation (chi_1 displaced from
+    chi_0 by dq, dp widths).  Weighting by the second state's own density instead
+    misses it by 50 to 100 standard errors."""
+    omega = np.array([float(wl.cm1(1600.0))])
+    pes = wl.harmonic_pes(omega)
+    om = omega[0]
+    p_eq = np.array([[np.sqrt(om)], [np.sqrt(om) * (1.0 + dp)]])
+    q_eq = np.array([[0.0], [dq / np.sqrt(om)]])
+    dt, n_steps, N = 5.0, 400, 20000
+    p0, q0, w = oracle.sample_initial(omega, p_eq[0], q_eq[0], N, 11)
+    amp, good = oracle.propagate(pes, omega, p_eq, q_eq, dt, n_steps, p0, q0, amplitude=oracle.AMP_HK)
+    assert good.all()
+    t = dt * np.arange(n_steps + 1)
+    for x in (0, 1):
+        alpha2 = 0.5 * (om * q_eq[x, 0] ** 2 + p_eq[x, 0] ** 2 / om)
+        exact = np.exp(-0.5j * om * t) * np.exp(alpha2 * (np.exp(-1j * om * t) - 1.0))
+        mean = amp[x].mean(axis=0)
+        se = np.sqrt(amp[x].real.var(axis=0) + amp[x].imag.var(axis=0)) / np.sqrt(N)
+        z = np.abs(mean - exact) / np.maximum(se, 1e-15)
+        print(f"chi {x}: max deviation in standard errors {z[1:].max():.2f}")
+        assert np.all(z[1:] < 5.0), x
+    # t = 0: the first state's summands are 1; the second's are the density ratio
+    r = np.exp([2 * (oracle.log_overlap(omega, p_eq[1], q_eq[1], p0[:, j], q0[:, j]).real
+                     - oracle.log_overlap(omega, p_eq[0], q_eq[0], p0[:, j], q0[:, j]).real) for j in range(8)])
+    assert np.max(np.abs(amp[0][:, 0] - 1.0)) < 1e-14
+    assert np.max(np.abs(amp[1][:8, 0] - r)) < 1e-12 * np.max(r)
+
+
 def test_one_sided_transform_is_the_dirichlet_kernel():
     dt, n_steps, n = 10.0, 300, 7
     E0 = float(wl.cm1(2000.0))

@@ -168,3 +168,27 @@ def test_several_reference_states_share_trajectories(levels):
         assert abs(strongest - exact) < 16.0
         for e in wl.to_cm1(E[ws[x] > 0.1]):
             assert np.min(np.abs(pk - e)) < 16.0
+
+
+def test_plain_hk_several_reference_states_share_trajectories(levels):
+    """The plain HK spectrum for two reference states on trajectories drawn around the
+    first (chi_2 with mode 0 excited, as above): each state's strongest peak lies within
+    5 cm^-1 of its strongest exact line and every line of weight >= 0.1 has a peak
+    within 5 cm^-1 (measured <= 2.0).  Weighting the second state's summands by its own
+    density instead of the sampling density puts its strongest peak on the zero-point
+    line, 1578 cm^-1 away."""
+    p_eq = np.stack([np.sqrt(OMEGA), np.array([np.sqrt(3.0 * OMEGA[0]), np.sqrt(OMEGA[1])])])
+    E, ws = _quantum(KAPPA, 48, 40, p_eq)
+    pes = wl.morse_pes(OMEGA, D, IDX3, KAPPA * REL)
+    p0, q0, w = oracle.sample_initial(OMEGA, p_eq[0], np.zeros(2), 8000, 0)
+    amp, good = oracle.propagate(pes, OMEGA, p_eq, np.zeros((2, 2)), 10.0, 3000, p0, q0, amplitude=oracle.AMP_HK)
+    Eg = wl.cm1(np.linspace(1500.0, 8000.0, 2601))
+    for x in range(2):
+        I, ng, _ = oracle.spectrum_hk(amp[x], good, 3000, 10.0, Eg[0], Eg[-1], Eg.size)
+        pk = wl.to_cm1(cf.find_peaks(Eg, I, 0.02))
+        strongest = wl.to_cm1(Eg[np.argmax(I)])
+        exact = wl.to_cm1(E[np.argmax(ws[x])])
+        print(f"chi {x}: strongest HK line {strongest:8.2f}, strongest exact line {exact:8.2f}")
+        assert abs(strongest - exact) < 5.0
+        for e in wl.to_cm1(E[ws[x] > 0.1]):
+            assert np.min(np.abs(pk - e)) < 5.0
