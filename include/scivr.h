@@ -215,7 +215,8 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
  * from amplitudes recorded with SCIVR_AMP_HK:
  *   C(c dt) = (1/n_good) sum_{j: good[j] != 0} amp[j][c]   (the survival amplitude),
  *   I(E_k) = (dt/pi) Re[ C(0)/2 + sum_{c=1}^{n_steps} C(c dt) e^{i E_k c dt} ]
- * (Eq. I(E)_timedependent's one-sided integral by the trapezoid rule), E_k as
+ * (Eq. I(E)_timedependent by the rectangle rule on the symmetric grid
+ * c = -n_steps..n_steps, folded onto c >= 0 with C(-t) = conj C(t)), E_k as
  * for scivr_spectrum.  amp: device complex double [n_traj][amp_ld].  good:
  * device [n_traj].  I_out: device [n_E].  C_out: device complex double
  * [n_steps+1] (may be NULL).  n_good_out: device int64 (may be NULL).  The

@@ -566,9 +566,9 @@ int or_spectrum(const double complex *amp, int64_t amp_ld, const double *w, cons
  * of the Herman-Kluk summands (propagation with amplitude = 1, which carries
  * the weights) over the good trajectories,
  *   C(c dt) = (1/n_good) sum_{j good} amp_j(c),
- * and I(E) = (Re / pi) int_0^T C(t) e^{i E t} dt by the trapezoid rule,
- *   I(E_k) = (dt/pi) Re[ C(0)/2 + sum_{c=1}^{n_steps} C(c dt) e^{i E_k c dt} ]
- * (the full-line rectangle rule with C(-t) = conj C(t)). */
+ * and I(E) = (1/2pi) int_{-T}^{T} C(t) e^{i E t} dt by the rectangle rule on the
+ * symmetric grid c = -n_steps..n_steps, folded onto c >= 0 with C(-t) = conj C(t):
+ *   I(E_k) = (dt/pi) Re[ C(0)/2 + sum_{c=1}^{n_steps} C(c dt) e^{i E_k c dt} ]. */
 int or_spectrum_hk(const double complex *amp, int64_t amp_ld, const uint8_t *good, int64_t n_traj,
                    int32_t n_steps, double dt, double E_min, double E_max, int32_t n_E, double *I_out,
                    int64_t *n_good_out, double complex *C_out)

@@ -174,7 +174,7 @@ def test_hk_spectrum_no_good_rows_is_zero(G):
 
 
 def test_hk_spectrum_dirichlet_closed_form(G):
-    """C(t) = e^{-i E0 t} on every row: the one-sided trapezoid transform is the
+    """C(t) = e^{-i E0 t} on every row: the folded rectangle-rule transform is the
     Dirichlet kernel (dt/pi) sin((n+1/2) x) / (2 sin(x/2)), x = (E - E0) dt."""
     dt, n_steps, n = 10.0, 300, 7
     E0 = float(wl.cm1(2000.0))

@@ -13,7 +13,7 @@ mathematics fixes:
   exact autocorrelation e^{-i omega t/2} exp(|alpha|^2 (e^{-i omega t} - 1))
   within five standard errors.  The same holds for a second reference state on trajectories drawn around the
   first, whose summands carry the sampling density's importance weight.
-* The one-sided transform: for C(t) = e^{-i E0 t} the trapezoid rule gives the
+* The folded transform: for C(t) = e^{-i E0 t} the symmetric rectangle rule gives the
   Dirichlet kernel (dt/pi) sin((n+1/2) x) / (2 sin(x/2)), x = (E - E0) dt.
 * A 1D Morse oscillator: the peaks sit near the closed-form levels.
 """
