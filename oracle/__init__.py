@@ -10,13 +10,25 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
   log_overlap       numerical quadrature of the coherent-state wavefunctions
   det_real/complex  numpy.linalg.det (LAPACK) on random matrices
   propagate         harmonic closed form (Glauber coherent-state algebra),
-                    symplecticity M^T J M = J, energy O(dt^4), time reversal,
-                    finite-difference monodromy, order-4 convergence,
-                    generating-function identity of the action
+                    also where arg det A turns by more than pi per step
+                    (24 modes); symplecticity M^T J M = J (F up to 24),
+                    energy O(dt^4), time reversal, finite-difference
+                    monodromy, order-4 convergence, generating-function
+                    identity of the action; non-finite starts flagged bad
+    (HK summands)   harmonic ground state (every summand the exact phase),
+                    displaced coherent-state autocorrelation, also for a
+                    second state on trajectories drawn around the first
   spectrum          Dirichlet-kernel closed form, harmonic eigen-expansion,
-                    Parseval, 1D Morse closed-form levels
+                    Parseval, 1D Morse closed-form levels, exact levels and
+                    coupling shifts of two coupled Morse modes (sinc DVR)
+  spectrum_hk       Dirichlet kernel of the folded rectangle rule, 1D Morse
+                    levels, exact levels and line weights of the coupled
+                    Morse pair for one and two reference states
   sample_initial    Philox4x32-10 known-answer vectors, moments, the
                     resolution-of-identity expectation of the weights
+  mlp_eval          fourth-order finite differences of the value (gradient,
+                    Hessian), closed form of a network with zero weights
+  mlp_loss_grad     central differences of the training objective
 """
 from __future__ import annotations
 
