@@ -28,8 +28,9 @@
  *   7. The discrete time-averaged spectrum, Eq. I(E)_discreto, as a direct
  *      O(K * N_E) Fourier sum per good trajectory.
  *   8. The plain Herman-Kluk SC-IVR spectrum, Eq. I(E)_SCIVR: each trajectory's
- *      summand C_t e^{iS_t} <chi|p_t q_t> <p0 q0|chi> (times its weight), their
- *      mean over trajectories, and the one-sided Fourier transform.
+ *      summand C_t e^{iS_t} <chi|p_t q_t> <p0 q0|chi> times the importance weight
+ *      of the density the initial conditions were drawn from, their mean over
+ *      trajectories, and the Fourier transform folded onto t >= 0.
  *
  * Every number is IEEE double; transcendental functions come from libm.
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.
