@@ -172,6 +172,11 @@ int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
  * trajectory is marked bad (good[j] = 0) once |det(M)^2 - 1| > stab_tol or any
  * state value is not finite (Sec. II, Sec. III.B); bad trajectories are still
  * propagated to T and their amplitudes are unspecified.
+ * A reference state that combines the recorded coherent states, chi = sum_x c_x chi_x
+ * (the symmetry-adapted states of Sec. IV), has the time-averaged amplitude
+ * sum_x conj(c_x) amp[x][j][c]: the overlap is linear in <chi| and e^{i (S + phi)} is
+ * common to all x, so its spectrum is scivr_spectrum of those combined rows with the same
+ * weights.  The Herman-Kluk summand is bilinear in chi and has no such form.
  * p0, q0: device [F][n_traj].  amp: device complex double (re, im interleaved)
  * [n_chi][n_traj][amp_ld], amp_ld >= n_steps + 1, 16-byte aligned.  good:
  * device [n_traj].  fin: host struct of optional device outputs (NULL = none).
