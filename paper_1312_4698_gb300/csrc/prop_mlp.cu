@@ -36,6 +36,7 @@ __device__ __forceinline__ void record(const PropLaunch &L, int64_t j, int step,
                                        const double (&q)[F], double S, double theta, double absA)
 {
     const PropArgs &A = L.args;
+    double re00 = 0.0;   // Re log <chi_0|p0 q0>, set by the x = 0 iteration (Herman-Kluk summand)
     for (int x = 0; x < A.n_chi; ++x) {
         double re = 0.0, im = 0.0;
 #pragma unroll
@@ -49,7 +50,7 @@ __device__ __forceinline__ void record(const PropLaunch &L, int64_t j, int step,
         double ph = im + S + 0.5 * theta;
         if (A.amplitude == SCIVR_AMP_HK) {
             double re0, im0;
-            chi_log_overlap0<F>(A, L.p0, L.q0, L.n_traj, j, x, re0, im0);
+            chi_log_overlap0<F>(A, L.p0, L.q0, L.n_traj, j, x, re00, re0, im0);
             re = re - re0 + 0.5 * log(absA);
             ph -= im0;
         }

@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(64) k_propagate_tpt_fp64(const PropLaunch L)
             if (!finite) good = false;
         }
         // amplitudes <chi_x|p q> e^{i (S + theta/2)}
+        double re00 = 0.0;   // Re log <chi_0|p0 q0>, set by the x = 0 iteration (Herman-Kluk summand)
         for (int x = 0; x < A.n_chi; ++x) {
             double re = 0.0, im = 0.0;
 #pragma unroll
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(64) k_propagate_tpt_fp64(const PropLaunch L)
                 // Herman-Kluk summand: |det A|^{1/2} and the division by the initial
                 // overlap times the sampling weight (chi_log_overlap0)
                 double re0, im0;
-                chi_log_overlap0<F>(A, L.p0, L.q0, n, j, x, re0, im0);
+                chi_log_overlap0<F>(A, L.p0, L.q0, n, j, x, re00, re0, im0);
                 re = re - re0 + 0.5 * log(hypot(detA.re, detA.im));
                 ph -= im0;
             }

@@ -160,17 +160,16 @@ __device__ __forceinline__ void chi_log_overlap_at(const PropArgs &A, const doub
 // the initial conditions are drawn from the Husimi density of the first reference
 // state, so that density's inverse is every state's importance weight.  Hence
 // im0 = Im log <chi_x|p0 q0> and re0 = 2 Re log <chi_0|p0 q0> - Re log <chi_x|p0 q0>
-// (for x = 0 exactly Re log <chi_0|p0 q0>, since 2a - a = a in floating point).
+// (for x = 0 exactly Re log <chi_0|p0 q0>).  Call it for x = 0, 1, ... in order:
+// the x = 0 call stores Re log <chi_0|p0 q0> in re00 for the later ones.
 template <int F>
 __device__ __forceinline__ void chi_log_overlap0(const PropArgs &A, const double *p0, const double *q0,
-                                                 int64_t n, int64_t j, int x, double &re0, double &im0)
+                                                 int64_t n, int64_t j, int x, double &re00, double &re0,
+                                                 double &im0)
 {
     chi_log_overlap_at<F>(A, p0, q0, n, j, x, re0, im0);
-    if (x != 0) {
-        double r00, i00;
-        chi_log_overlap_at<F>(A, p0, q0, n, j, 0, r00, i00);
-        re0 = 2.0 * r00 - re0;
-    }
+    if (x == 0) re00 = re0;
+    else re0 = 2.0 * re00 - re0;
 }
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
