@@ -10,10 +10,12 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.mark.parametrize("amplitude", ["ta", "hk"])
-def test_reference_arm_json_line(amplitude):
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--amplitude", amplitude,
-           "--n-traj", "64", "--n-steps", "40", "--n-E", "32", "--cpu-sample", "8", "--steps", "1", "--warmup", "3"]
+@pytest.mark.parametrize("workload,amplitude", [("f6", "ta"), ("f6", "hk"), ("f3", "ta"), ("f9", "ta"),
+                                               ("f9mlp", "ta")])
+def test_reference_arm_json_line(workload, amplitude):
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", workload,
+           "--amplitude", amplitude, "--n-traj", "64", "--n-steps", "40", "--n-E", "32", "--cpu-sample", "8",
+           "--steps", "1", "--warmup", "3"]
     out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
