@@ -1,6 +1,7 @@
 """Plain Herman-Kluk SC-IVR on the GPU (Eq. I(E)_SCIVR): the per-trajectory
 summands C_t e^{iS_t} <chi|p_t q_t> / <chi|p0 q0> that scivr_propagate records
-with SCIVR_AMP_HK, and the survival-amplitude spectrum of scivr_spectrum_hk,
+with SCIVR_AMP_HK (a further reference state chi_x on the same trajectories:
+C_t e^{iS_t} <chi_x|p_t q_t> <p0 q0|chi_x> / |<p0 q0|chi_0>|^2), and the survival-amplitude spectrum of scivr_spectrum_hk,
 against the FP64 oracle element by element and against closed forms.
 
 Tolerances follow those of the time-averaged path: FP64 summands to 1e-9 of a
