@@ -16,6 +16,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
                     monodromy, order-4 convergence, generating-function
                     identity of the action; non-finite starts flagged bad
     (HK summands)   harmonic ground state (every summand the exact phase),
+                    exact survival amplitude for widths gamma != omega
+                    (the prefactor modulus |det A|^{1/2}),
                     displaced coherent-state autocorrelation, also for a
                     second state on trajectories drawn around the first
   spectrum          Dirichlet-kernel closed form, harmonic eigen-expansion,

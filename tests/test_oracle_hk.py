@@ -13,6 +13,9 @@ mathematics fixes:
   exact autocorrelation e^{-i omega t/2} exp(|alpha|^2 (e^{-i omega t} - 1))
   within five standard errors.  The same holds for a second reference state on trajectories drawn around the
   first, whose summands carry the sampling density's importance weight.
+* Widths unequal to the frequency (gamma = omega/4, 2 omega): |det A| leaves 1, and
+  the mean must match the exact survival amplitude of a sinc-DVR diagonalisation,
+  which pins the prefactor's modulus |det A|^{1/2}.
 * The folded transform: for C(t) = e^{-i E0 t} the symmetric rectangle rule gives the
   Dirichlet kernel (dt/pi) sin((n+1/2) x) / (2 sin(x/2)), x = (E - E0) dt.
 * A 1D Morse oscillator: the peaks sit near the closed-form levels.
@@ -71,6 +74,40 @@ def test_displaced_coherent_state_autocorrelation():
     print("max deviation in standard errors:", z.max())
     assert np.all(z[1:] < 5.0)
     assert abs(mean[0] - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("g_over_omega", [0.25, 2.0])
+def test_widths_unequal_to_the_frequency_exercise_the_prefactor_modulus(g_over_omega):
+    """Herman-Kluk is exact for a harmonic oscillator with any coherent-state width, but
+    only with gamma != omega does |det A| leave 1 (here up to 1.25), so only then is the
+    modulus |det A|^{1/2} of the prefactor tested.  The Monte Carlo mean of the summands
+    must match the exact survival amplitude sum_n |<n|chi>|^2 e^{-i E_n t} (a sinc-DVR
+    diagonalisation) within five standard errors; dropping the modulus, or taking
+    |det A| instead of its square root, misses by 9 to 39 standard errors."""
+    om = float(wl.cm1(1600.0))
+    g = g_over_omega * om
+    gamma, p_eq, q_eq = np.array([g]), np.array([0.8 * np.sqrt(g)]), np.array([0.3 / np.sqrt(g)])
+    n = 400
+    x = np.linspace(-1.0, 1.0, n) * 14.0 / np.sqrt(min(g, om))
+    h = x[1] - x[0]
+    i = np.arange(n)
+    d = i[:, None] - i[None, :]
+    H = np.where(d == 0, np.pi ** 2 / 3.0, 2.0 * (-1.0) ** d / np.where(d == 0, 1, d) ** 2) / (2.0 * h * h)
+    H[np.diag_indices(n)] += 0.5 * om * om * x * x
+    E, U = np.linalg.eigh(H)
+    chi = (g / np.pi) ** 0.25 * np.exp(-0.5 * g * (x - q_eq[0]) ** 2 + 1j * p_eq[0] * (x - q_eq[0]))
+    weights = np.abs((np.sqrt(h) * chi).conj() @ U) ** 2
+    assert abs(weights.sum() - 1.0) < 1e-9
+    dt, n_steps, N = 5.0, 400, 20000
+    t = dt * np.arange(n_steps + 1)
+    exact = (weights[None, :] * np.exp(-1j * np.outer(t, E))).sum(axis=1)
+    amp, good = _hk_amp(wl.harmonic_pes(np.array([om])), gamma, p_eq, q_eq, dt, n_steps, N, 11)
+    assert good.all()
+    mean = amp.mean(axis=0)
+    se = np.sqrt(amp.real.var(axis=0) + amp.imag.var(axis=0)) / np.sqrt(N)
+    z = np.abs(mean - exact) / np.maximum(se, 1e-15)
+    print(f"gamma/omega = {g_over_omega}: max deviation in standard errors {z[1:].max():.2f}")
+    assert np.all(z[1:] < 5.0)
 
 
 @pytest.mark.parametrize("dq,dp", [(0.5, 0.0), (0.0, 0.5), (0.7, -0.7)])
