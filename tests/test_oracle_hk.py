@@ -11,8 +11,9 @@ mathematics fixes:
   must approach it at the integrator's fourth order in dt.
 * A displaced coherent state chi = |alpha>: the Monte Carlo mean must match the
   exact autocorrelation e^{-i omega t/2} exp(|alpha|^2 (e^{-i omega t} - 1))
-  within five standard errors.  The same holds for a second reference state on trajectories drawn around the
-  first, whose summands carry the sampling density's importance weight.
+  within five standard errors.  The same holds for a second reference state on
+  trajectories drawn around the first, whose summands carry the sampling
+  density's importance weight.
 * Widths unequal to the frequency (gamma = omega/4, 2 omega): |det A| leaves 1, and
   the mean must match the exact survival amplitude of a sinc-DVR diagonalisation,
   which pins the prefactor's modulus |det A|^{1/2}.
