@@ -14,7 +14,9 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
                     (24 modes); symplecticity M^T J M = J (F up to 24),
                     energy O(dt^4), time reversal, finite-difference
                     monodromy, order-4 convergence, generating-function
-                    identity of the action; non-finite starts flagged bad
+                    identity of the action; non-finite starts flagged bad;
+                    the prefactor matrix is the analytic block of the
+                    symplectic map in complex coordinates (A A^+ - B B^+ = I)
     (HK summands)   harmonic ground state (every summand the exact phase),
                     exact survival amplitude for widths gamma != omega
                     (the prefactor modulus |det A|^{1/2}),
