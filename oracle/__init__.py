@@ -23,7 +23,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
                     displaced coherent-state autocorrelation, also for a
                     second state on trajectories drawn around the first
   spectrum          Dirichlet-kernel closed form, harmonic eigen-expansion,
-                    Parseval, 1D Morse closed-form levels, exact levels and
+                    Parseval, the sum rule (integral = <chi|chi>), 1D Morse
+                    closed-form levels, exact levels and
                     coupling shifts of two coupled Morse modes (sinc DVR)
   spectrum_hk       Dirichlet kernel of the folded rectangle rule, 1D Morse
                     levels, exact levels and line weights of the coupled

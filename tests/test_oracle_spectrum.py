@@ -8,6 +8,8 @@
 * 1D Morse: peaks at the closed-form levels omega (n+1/2) - omega^2 (n+1/2)^2 / (4D)
   within semiclassical accuracy.
 * Philox4x32-10 known-answer vectors; Husimi moments; the weights' unbiasedness.
+* The sum rule: a spectral density integrates to <chi|chi> = 1 (time-averaged and
+  plain Herman-Kluk), which pins the normalisation independently of its formula.
 """
 import os
 
@@ -189,3 +191,32 @@ def test_weights_are_inverse_husimi_density():
     f0 = np.exp(-0.5 * np.sum(gamma[:, None] * (q0 - q_eq[:, None]) ** 2
                               + (p0 - p_eq[:, None]) ** 2 / gamma[:, None], axis=0))
     assert np.max(np.abs(w * f0 - 1.0)) < 1e-12
+
+
+def test_spectra_obey_the_sum_rule():
+    """A spectral density integrates to <chi|chi> = 1.  Over one period 2 pi / dt, on the
+    grid of K = n_steps + 1 points where the sum is exact:
+    * time-averaged: for the harmonic ground state (gamma = the integrator's modified
+      frequency, chi at the origin) every trajectory has w |a(c)|^2 = 1, so the integral
+      is (1/T) dt (n_steps + 1) = (n_steps + 1) / n_steps, the rectangle rule's value;
+      a lost factor dt or 2 pi in the normalisation would be visible at once;
+    * plain Herman-Kluk: only the c = 0 term survives the integration, so the integral
+      is Re C(0) = 1 on any surface."""
+    omegas = wl.cm1([1600.0, 3650.0])
+    dt, n_steps = 10.0, 400
+    K = n_steps + 1
+    gts = np.array([cf.harmonic_rotation(w, dt)[1] for w in omegas])
+    z = np.zeros(2)
+    p0, q0, w = oracle.sample_initial(gts, z, z, 64, 3)
+    amp, good = oracle.propagate(wl.harmonic_pes(omegas), gts, z[None], z[None], dt, n_steps, p0, q0)
+    assert np.max(np.abs(w[:, None] * np.abs(amp[0]) ** 2 - 1.0)) < 1e-12
+    period = 2.0 * np.pi / dt
+    I, ng = oracle.spectrum(amp[0], w, good, n_steps, dt, 0.0, period * (K - 1) / K, K)
+    assert abs(I.sum() * period / K - K / n_steps) < 1e-12
+
+    w8 = wl.config_f3(n_traj=64, n_steps=n_steps)
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, 64, 1)
+    ah, gh = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, dt, n_steps, p0, q0, amplitude=oracle.AMP_HK)
+    Ih, ngh, C = oracle.spectrum_hk(ah[0], gh, n_steps, dt, 0.0, period * (K - 1) / K, K)
+    assert ngh > 0 and C[0] == 1.0
+    assert abs(Ih.sum() * period / K - 1.0) < 1e-12
