@@ -93,10 +93,13 @@ class _Final(C.Structure):
 
 
 def _load():
+    """Load the oracle library: the in-tree build, or the shared object named by
+    SCIVR_ORACLE_LIB (the oracle's mutation tests load deliberately broken builds
+    through it, in child processes)."""
     global _lib
     with _lock:
         if _lib is None:
-            lib = C.CDLL(build())
+            lib = C.CDLL(os.environ.get("SCIVR_ORACLE_LIB") or build())
             vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
             lib.or_pes_eval.restype = d
             lib.or_pes_eval.argtypes = [vp, vp, vp, vp]

@@ -1,0 +1,121 @@
+"""Planted mistakes in the oracle, on the CPU: each mutant of scivr_oracle.c (one
+plausible slip: a dropped term, a wrong sign, factor or index) is compiled into its own
+shared object and the pin that should catch it is run against that build in a child
+process (SCIVR_ORACLE_LIB).  Every mutant must fail its pin, and the unmodified source
+compiled the same way must pass all of them.  Nothing here runs on a GPU."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "scivr_oracle.c")
+
+P = "tests/test_oracle_propagation.py::"
+S = "tests/test_oracle_spectrum.py::"
+H = "tests/test_oracle_hk.py::"
+E = "tests/test_oracle_pes.py::"
+N = "tests/test_oracle_mlp.py::"
+
+# name: ([(exact source text, replacement), ...], [pins that must fail])
+MUTANTS = {
+    "kick with the wrong sign": (
+        [("for (int a = 0; a < F; ++a) p[a] -= tau * g[a];", "for (int a = 0; a < F; ++a) p[a] += tau * g[a];")],
+        [P + "test_harmonic_amplitude_closed_form"]),
+    "kinetic action of the drift dropped": (
+        [("    *S += tau * kin;", "    (void)kin;")],
+        [P + "test_action_is_a_generating_function"]),
+    "wrong triple-jump weight": (
+        [("double w0 = -cbrt2 / (2.0 - cbrt2);", "double w0 = -cbrt2 / (2.0 + cbrt2);")],
+        [P + "test_fourth_order_convergence_of_the_flow"]),
+    "monodromy kick halved": (
+        [("M[a * n + col] -= tau * hm;", "M[a * n + col] -= 0.5 * tau * hm;")],
+        [P + "test_monodromy_matches_finite_differences"]),
+    "overlap phase factor": (
+        [("im += 0.5 * (p1[i] + p2[i]) * dq;", "im += (p1[i] + p2[i]) * dq;")],
+        [E + "test_overlap_vs_quadrature"]),
+    "overlap width factor": (
+        [("re += -0.25 * gamma[i] * dq * dq", "re += -0.5 * gamma[i] * dq * dq")],
+        [E + "test_overlap_vs_quadrature"]),
+    "prefactor phase not halved": (
+        [("double phase = cimag(lo) + S + 0.5 * theta;", "double phase = cimag(lo) + S + theta;")],
+        [P + "test_harmonic_amplitude_closed_form"]),
+    "width ordering of the prefactor matrix": (
+        [("double re = ga / gb * Mqq + gb / ga * Mpp;", "double re = gb / ga * Mqq + ga / gb * Mpp;")],
+        [P + "test_prefactor_matrix_is_the_analytic_block_of_the_monodromy"]),
+    "unwrapping without the reference rotation": (
+        [("double d = arg_new - arg_old + ref_step;", "double d = arg_new - arg_old;"),
+         ("return theta + d - ref_step;", "return theta + d;")],
+        [P + "test_phase_unwrapping_when_arg_det_A_turns_more_than_pi_per_step"]),
+    "stability quantity |det M - 1|": (
+        [("fabs(detM * detM - 1.0)", "fabs(detM - 1.0)")],
+        [P + "test_stability_quantity_is_det_squared_minus_one"]),
+    "spectrum normalisation missing dt": (
+        [("dt * dt / (OR_TWO_PI * T * (double)n_good)", "dt / (OR_TWO_PI * T * (double)n_good)")],
+        [S + "test_spectra_obey_the_sum_rule"]),
+    "Husimi position width": (
+        [("qj[i] = q_eq[i] + or_normal(seed, j, i) / sqrt(gamma[i]);",
+          "qj[i] = q_eq[i] + or_normal(seed, j, i) / sqrt(2.0 * gamma[i]);")],
+        [S + "test_husimi_moments_and_normality"]),
+    "sampling weight exponent": (
+        [("w[j] = exp(-2.0 * creal(lo));", "w[j] = exp(-creal(lo));")],
+        [S + "test_weights_are_inverse_husimi_density"]),
+    "HK weight of each state's own density": (
+        [("double complex lo00 = x == 0 ? lo0 : or_log_overlap(F, prm->gamma, prm->p_eq,\n"
+          "                                                                        prm->q_eq, p0, q0);",
+          "double complex lo00 = lo0;")],
+        [H + "test_reference_states_share_trajectories_sampled_around_the_first"]),
+    "HK prefactor modulus dropped": (
+        [("double complex Ct = sqrt(cabs(detA)) * cexp(0.5 * I * theta);",
+          "double complex Ct = cexp(0.5 * I * theta);")],
+        [H + "test_widths_unequal_to_the_frequency_exercise_the_prefactor_modulus"]),
+    "Morse curvature": (
+        [("H[i * F + i] += 2.0 * Dm * am * am * u * (2.0 * u - 1.0);",
+          "H[i * F + i] += 2.0 * Dm * am * am * u * (u - 1.0);")],
+        [E + "test_gradient_and_hessian_match_finite_differences"]),
+    "coupling Hessian halved": (
+        [("H[idx[s] * F + idx[t]] += prod;", "H[idx[s] * F + idx[t]] += 0.5 * prod;")],
+        [E + "test_gradient_and_hessian_match_finite_differences"]),
+    "activation's second derivative": (
+        [("*f2 = s * (1.0 - s) * (2.0 + z * (1.0 - 2.0 * s));", "*f2 = s * (1.0 - s) * (1.0 + z * (1.0 - 2.0 * s));")],
+        [N + "test_mlp_gradient_and_hessian_vs_finite_differences"]),
+    "pivot swap without the sign change": (
+        [("            det = -det;\n        }\n        double akk = A[k * n + k];",
+          "        }\n        double akk = A[k * n + k];")],
+        [E + "test_real_determinant_vs_lapack"]),
+}
+
+
+def _build(tmp_path, name, pairs):
+    src = open(SRC).read()
+    for old, new in pairs:
+        assert src.count(old) == 1, (name, old)
+        src = src.replace(old, new)
+    c = tmp_path / "mutant.c"
+    c.write_text(src)
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", *oracle._CFLAGS, str(c), "-o", str(so), "-lm"], check=True)
+    return str(so)
+
+
+def _run_pins(lib, pins):
+    env = dict(os.environ, SCIVR_ORACLE_LIB=lib)
+    return subprocess.run([sys.executable, "-m", "pytest", *pins, "-x", "-q", "-p", "no:cacheprovider"],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    pairs, pins = MUTANTS[name]
+    out = _run_pins(_build(tmp_path, name, pairs), pins)
+    assert out.returncode == 1, (name, out.returncode, out.stdout[-1500:], out.stderr[-1500:])
+    assert " failed" in out.stdout, out.stdout[-1500:]
+
+
+def test_unmodified_source_passes_every_pin(tmp_path):
+    pins = sorted({p for _, ps in MUTANTS.values() for p in ps})
+    out = _run_pins(_build(tmp_path, "control", []), pins)
+    assert out.returncode == 0, (out.stdout[-2000:], out.stderr[-1500:])

@@ -265,6 +265,23 @@ def test_stability_threshold_direction():
     assert not oracle.propagate_one(pes, om, *chi, 10.0, 300, p0, q0, stab_tol=1e-300)["good"]
 
 
+def test_stability_quantity_is_det_squared_minus_one():
+    """The monitored quantity is |det(M^T M) - 1| = |det(M)^2 - 1| (reading of Sec. II),
+    tested every step and sticky: with D its largest value along the trajectory (from the
+    det M series, itself pinned against LAPACK), a tolerance of 0.75 D flags the
+    trajectory bad and 1.25 D keeps it good.  Monitoring |det M - 1|, about D / 2,
+    would keep it good at 0.75 D."""
+    F = 3
+    pes = _anharmonic(F)
+    p0, q0, om = _start(pes)
+    chi = (np.sqrt(om), np.zeros(F))
+    r = oracle.propagate_one(pes, om, *chi, 10.0, 2000, p0, q0, stab_tol=1.0)
+    D = np.max(np.abs(r["detM"][1:] ** 2 - 1.0))
+    assert D > 1e-14
+    assert not oracle.propagate_one(pes, om, *chi, 10.0, 2000, p0, q0, stab_tol=0.75 * D)["good"]
+    assert oracle.propagate_one(pes, om, *chi, 10.0, 2000, p0, q0, stab_tol=1.25 * D)["good"]
+
+
 def test_runaway_trajectory_is_flagged_bad():
     # a strongly negative quartic coupling makes large-amplitude motion escape to infinity
     F = 2
