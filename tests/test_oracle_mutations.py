@@ -86,6 +86,31 @@ MUTANTS = {
         [("            det = -det;\n        }\n        double akk = A[k * n + k];",
           "        }\n        double akk = A[k * n + k];")],
         [E + "test_real_determinant_vs_lapack"]),
+    "complex pivot swap without the sign change": (
+        [("            det = -det;\n        }\n        double complex akk = A[k * n + k];",
+          "        }\n        double complex akk = A[k * n + k];")],
+        [E + "test_complex_determinant_vs_lapack"]),
+    "monodromy drift with the wrong sign": (
+        [("M[(F + a) * n + col] += tau * M[a * n + col];", "M[(F + a) * n + col] -= tau * M[a * n + col];")],
+        [P + "test_monodromy_matches_finite_differences"]),
+    "coupling gradient halved": (
+        [("g[idx[s]] += prod;", "g[idx[s]] += 0.5 * prod;")],
+        [E + "test_gradient_and_hessian_match_finite_differences"]),
+    "time-to-energy transform with the wrong sign": (
+        [("tw[c] = cos(ang) + I * sin(ang);", "tw[c] = cos(ang) - I * sin(ang);")],
+        [S + "test_dirichlet_closed_form"]),
+    "HK transform without the half weight at t = 0": (
+        [("double complex acc = 0.5 * C[0];", "double complex acc = C[0];")],
+        [H + "test_one_sided_transform_is_the_dirichlet_kernel"]),
+    "nine Philox rounds": (
+        [("for (int r = 0; r < 10; ++r) {", "for (int r = 0; r < 9; ++r) {")],
+        [S + "test_philox_known_answers"]),
+    "Box-Muller radius": (
+        [("double r = sqrt(-2.0 * log(u1));", "double r = sqrt(-log(u1));")],
+        [S + "test_husimi_moments_and_normality"]),
+    "gradient-matching term of the training gradient halved": (
+        [("u[i] = 2.0 * beta * e / (double)n;", "u[i] = beta * e / (double)n;")],
+        [N + "test_training_gradient_vs_finite_differences"]),
 }
 
 
