@@ -323,3 +323,36 @@ def test_binding_signatures_match_the_headers():
         for decl, t in zip(params, fn.argtypes):
             assert _ctypes_kind(t) == _c_kind(decl), (name, decl, t)
         assert _ctypes_kind(fn.restype) == _c_kind(ret.strip()), (name, ret, fn.restype)
+
+
+def test_missing_library_fails_loudly():
+    """Without libscivr.so the binding refuses to import: there is no CPU fallback."""
+    import subprocess
+    import sys
+    code = ("import paper_1312_4698_gb300.build as b; b.LIB = '/nonexistent/libscivr.so'\n"
+            "try:\n"
+            "    import paper_1312_4698_gb300.scivr\n"
+            "except ImportError as e:\n"
+            "    print('ImportError:', e)\n"
+            "else:\n"
+            "    raise SystemExit('imported without the library')\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-1500:]
+    assert "ImportError: libscivr.so is not built" in out.stdout
+
+
+def test_no_gpu_means_an_error_not_a_fallback(lib):
+    """On a machine without a GPU the first call that needs the device returns a CUDA
+    error code; nothing is computed on the host instead."""
+    import torch
+    from paper_1312_4698_gb300 import scivr
+    from paper_1312_4698_gb300 import workloads as wl
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(scivr.ScivrError) as ei:
+        scivr.scivr_create_pes(wl.config_f3().pes)
+    assert ei.value.code in (scivr.SCIVR_ECUDA, scivr.SCIVR_ENOMEM)
+    assert scivr.last_error().startswith("scivr_create_pes")
+    import __graft_entry__ as ge
+    with pytest.raises(AssertionError, match="needs cuda:0"):
+        ge.smoke()
