@@ -13,7 +13,7 @@
  * Hessian come from BF16-input / FP32-accumulate tensor-core GEMMs batched
  * over trajectories, and which is trained on the GPU by the library's own
  * forward and backward kernels.  The analytic surface stays available as the
- * judge (scivr_pes_eval).
+ * reference the network is measured against (scivr_pes_eval).
  *
  * Parameter vector theta (FP32, device): the concatenation
  *   [W1 (H x F, row-major, output index first), b1 (H), W2 (H x H), b2 (H),
