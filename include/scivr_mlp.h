@@ -121,8 +121,8 @@ int scivr_mlp_adamw(scivr_pes pes, const float *grad, float *m1, float *m2, int3
 
 /* Analytic potential (FP64, no learned term): V, gradient and Hessian of the
  * selected terms at n points -- the force-stage evaluation of the
- * propagation (Sec. III.A), exposed to make training targets and to judge a
- * learned residual.  q: device [n][F]; V: [n]; g: [n][F] (or NULL);
+ * propagation (Sec. III.A), exposed to make training targets and to measure a
+ * learned residual's error.  q: device [n][F]; V: [n]; g: [n][F] (or NULL);
  * H: [n][F][F] (or NULL) -- all FP64 device.  Errors: SCIVR_EINVAL. */
 int scivr_pes_eval(scivr_pes pes, int64_t n, const double *q, int32_t terms, double *V, double *g, double *H,
                    void *stream);
