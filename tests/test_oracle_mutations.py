@@ -108,39 +108,76 @@ MUTANTS = {
     "Box-Muller radius": (
         [("double r = sqrt(-2.0 * log(u1));", "double r = sqrt(-log(u1));")],
         [S + "test_husimi_moments_and_normality"]),
+    "bad trajectories kept in the time-averaged sum": (
+        [("                if (!good[j]) continue;\n                double complex X = 0.0;",
+          "                double complex X = 0.0;")],
+        [S + "test_bad_trajectories_are_excluded_and_n_good_normalises"]),
+    "sampling weights left out of the time-averaged sum": (
+        [("acc += w[j] * (creal(X) * creal(X) + cimag(X) * cimag(X));",
+          "acc += (creal(X) * creal(X) + cimag(X) * cimag(X));")],
+        [S + "test_parseval_on_the_dft_grid"]),
+    "bad trajectories kept in the survival amplitude": (
+        [("            if (good[j]) acc += amp[j * amp_ld + c];", "            acc += amp[j * amp_ld + c];")],
+        [H + "test_one_sided_transform_is_the_dirichlet_kernel"]),
+    "every reference state given the first one's overlap": (
+        [("double complex lo = or_log_overlap(F, prm->gamma, prm->p_eq + x * F,\n"
+          "                                                   prm->q_eq + x * F, p, q);",
+          "double complex lo = or_log_overlap(F, prm->gamma, prm->p_eq,\n"
+          "                                                   prm->q_eq, p, q);")],
+        [H + "test_reference_states_share_trajectories_sampled_around_the_first"]),
     "gradient-matching term of the training gradient halved": (
         [("u[i] = 2.0 * beta * e / (double)n;", "u[i] = beta * e / (double)n;")],
         [N + "test_training_gradient_vs_finite_differences"]),
 }
 
 
-def _build(tmp_path, name, pairs):
+def _build(workdir, name, pairs):
     src = open(SRC).read()
     for old, new in pairs:
         assert src.count(old) == 1, (name, old)
         src = src.replace(old, new)
-    c = tmp_path / "mutant.c"
-    c.write_text(src)
-    so = tmp_path / "libmutant.so"
-    subprocess.run(["gcc", *oracle._CFLAGS, str(c), "-o", str(so), "-lm"], check=True)
-    return str(so)
+    os.makedirs(workdir, exist_ok=True)
+    c = os.path.join(workdir, "mutant.c")
+    with open(c, "w") as f:
+        f.write(src)
+    so = os.path.join(workdir, "libmutant.so")
+    subprocess.run(["gcc", *oracle._CFLAGS, c, "-o", so, "-lm"], check=True)
+    return so
 
 
 def _run_pins(lib, pins):
-    env = dict(os.environ, SCIVR_ORACLE_LIB=lib)
+    # one OpenMP thread per child: the children run side by side
+    env = dict(os.environ, SCIVR_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
     return subprocess.run([sys.executable, "-m", "pytest", *pins, "-x", "-q", "-p", "no:cacheprovider"],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
 
+CONTROL = "unmodified source"
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Build every mutant (and the unmodified source) and run its pins, in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
+    base = tmp_path_factory.mktemp("mutants")
+    jobs = {name: (pairs, pins) for name, (pairs, pins) in MUTANTS.items()}
+    jobs[CONTROL] = ([], sorted({p for _, ps in MUTANTS.values() for p in ps}))
+
+    def one(item):
+        k, (name, (pairs, pins)) = item
+        return name, _run_pins(_build(os.path.join(base, str(k)), name, pairs), pins)
+
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(ex.map(one, enumerate(sorted(jobs.items()))))
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_planted_mistake_is_caught(tmp_path, name):
-    pairs, pins = MUTANTS[name]
-    out = _run_pins(_build(tmp_path, name, pairs), pins)
+def test_planted_mistake_is_caught(outcomes, name):
+    out = outcomes[name]
     assert out.returncode == 1, (name, out.returncode, out.stdout[-1500:], out.stderr[-1500:])
     assert " failed" in out.stdout, out.stdout[-1500:]
 
 
-def test_unmodified_source_passes_every_pin(tmp_path):
-    pins = sorted({p for _, ps in MUTANTS.values() for p in ps})
-    out = _run_pins(_build(tmp_path, "control", []), pins)
+def test_unmodified_source_passes_every_pin(outcomes):
+    out = outcomes[CONTROL]
     assert out.returncode == 0, (out.stdout[-2000:], out.stderr[-1500:])
