@@ -3,9 +3,12 @@
 One step = one pass of the whole hot path over one batch: Husimi sampling
 of n_traj initial conditions, propagation of (p, q, S, M, prefactor phase,
 amplitudes) over n_steps, and the time -> energy transform with the weighted
-|.|^2 reduction into I(E).  Default workload: F = 6 (formaldehyde-sized)
-Morse + cubic + quartic surface, 16384 trajectories, 4000 steps of 10 au,
-4000 energies, FP64 propagation and FP64 Fourier step.
+|.|^2 reduction into I(E).  Default workload: F = 9 (methane-sized) Morse +
+156 cubic + 486 quartic couplings, 65536 trajectories, 5000 steps of 10 au,
+4000 energies; mixed-precision propagation (FP32 monodromy and potential,
+FP64 positions, momenta, action and prefactor phase) and the tensor-core
+Fourier step with two BF16 digits per operand and FP32 accumulation
+(--precision fp64 --ft fp64 --workload f6 gives the plain FP64 F = 6 form).
 
   python bench.py [--gpus N --steps K --warmup W] [--workload f6|f3|f9|batch|f9mlp|speedup]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
@@ -45,6 +48,12 @@ FP64_PEAK_NOTE = ("GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table
 # scaled to the full launch where the capture used fewer trajectories
 TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9, ("k_ft_tc2", "f6"): 7.98e9,
            ("k_mlp_fused", "f9mlp"): 0.914e6 * 8}
+
+
+# trajectories of the oracle's timed sample per workload (10-30 s of host work on 16 cores),
+# and of each step of the reference arm (whose --steps K --warmup W run must end in minutes)
+CPU_SAMPLE = {"f3": 1024, "f6": 768, "f9": 256}
+REFERENCE_SAMPLE = {"f3": 1024, "f6": 768, "f9": 64}
 
 
 def workload(name: str, seed: int):
@@ -214,7 +223,7 @@ def reference_arm(args):
                           "configuration (its line carries the oracle's own rates); time --workload "
                           "f3/f6/f9/f9mlp instead"}))
         return 0
-    n_sample = args.cpu_sample
+    n_sample = min(args.cpu_sample, REFERENCE_SAMPLE.get(args.workload, args.cpu_sample))
     if args.workload == "f9mlp":
         # the oracle on the same surface type: Morse diagonal + a network of the same shape
         base = sized(wl.config_f9(seed=0), args)
@@ -697,12 +706,13 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="f6", choices=["f3", "f6", "f9", "batch", "f9mlp", "speedup"])
+    ap.add_argument("--workload", default="f9", choices=["f3", "f6", "f9", "batch", "f9mlp", "speedup"])
     ap.add_argument("--train-epochs", type=int, default=40, help="training epochs of --workload f9mlp")
     ap.add_argument("--check-traj", type=int, default=2048,
                     help="trajectories of the --workload f9mlp accuracy check")
     ap.add_argument("--n-mol", type=int, default=48, help="molecules in --workload batch")
-    ap.add_argument("--cpu-sample", type=int, default=768)
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="trajectories of the oracle timing (default: 1024 at F = 3, 768 at F = 6, 256 at F = 9)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
@@ -718,6 +728,8 @@ def main(argv=None):
                     help="ta: time-averaged spectrum (Eq. I(E)_discreto); hk: plain Herman-Kluk SC-IVR "
                          "spectrum (Eq. I(E)_SCIVR)")
     args = ap.parse_args(argv)
+    if args.cpu_sample is None:
+        args.cpu_sample = CPU_SAMPLE.get(args.workload, 768)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

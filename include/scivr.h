@@ -295,9 +295,11 @@ int scivr_batch_destroy(scivr_batch b);
  * Its scratch (the good count and per-slice column sums) lives in one
  * library-owned device array of 4 MiB (2^19 doubles) that every GPU which loads
  * libscivr holds until the process exits.  Limit: n_E <= 524256; larger grids
- * return SCIVR_EINVAL and launch nothing.  The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture begins.  All calls
+ * return SCIVR_EINVAL and launch nothing.  Each call looks up the array's
+ * device address (cudaGetSymbolAddress) with the calling device current, so a
+ * device reset between calls is harmless; a call made while `stream` is being
+ * captured reuses the address of the last call on that device instead, so make
+ * the first call on each device before any stream capture begins.  All calls
  * share the one array and overwrite what the previous call left there (nothing
  * in it needs to start at zero), so calls that overlap on the GPU -- on
  * different streams, or on different host threads -- race and must be

@@ -158,16 +158,22 @@ __global__ void k_na_reduce(const double *__restrict__ scratch, const double *__
     I_out[k] = ng > 0 ? s * (scale / (double)ng) : 0.0;
 }
 
-// Device address of this device's copy of g_spectrum_scratch, looked up once
-// per device with that device current.
-cudaError_t scratch_address(double **out)
+// Device address of this device's copy of g_spectrum_scratch, looked up with
+// that device current.  Outside stream capture the address is looked up on
+// every call (a device reset or a new primary context reloads the module at
+// another address, so a remembered one could be stale); during capture the
+// address remembered from the last call on this device is used.
+cudaError_t scratch_address(cudaStream_t s, double **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_spectrum_scratch);
         if (e != cudaSuccess) return e;
@@ -188,7 +194,7 @@ cudaError_t launch_spectrum_noalloc(const double2 *amp, int64_t amp_ld, const do
 {
     *n_launch = 0;
     double *scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
+    cudaError_t e = scratch_address(s, &scratch);
     if (e != cudaSuccess) return e;
     const int K = n_steps + 1;
     const int64_t n_mt = (n_traj + NB - 1) / NB;

@@ -323,3 +323,31 @@ def test_batch_matches_single_and_chi_layout():
         r = oracle.propagate_one(pes, om, p_eq, q_eq, 10.0, 50, p0[:, j], q0[:, j])
         assert np.array_equal(r["amp"], amp[:, j, :], equal_nan=True)
         assert r["good"] == bool(good[j])
+
+
+@pytest.mark.parametrize("sigma", [(3e-8, 3e-9), (5e-8, 5e-9)])
+def test_chunk_end_stability_cadence_selects_the_per_step_good_set(sigma):
+    """The mixed-precision kernels test det M at the last step of each chunk of C
+    steps instead of every step (Sec. II, Sec. III.A: a trajectory is discarded as
+    soon as |det(M^T M) - 1| exceeds the tolerance; the flag is sticky and the whole
+    trajectory is dropped).  On the oracle's own per-step det M series, over surfaces
+    where about half the trajectories go bad (couplings on mass-weighted q), the
+    chunk-end test with C = 8 and 16 must keep exactly the trajectories the per-step
+    test keeps, at the FP64 threshold and at the mixed path's FP32 one."""
+    rng = np.random.default_rng(3)
+    pes = wl.recipe_pes(6, rng, sigma3=sigma[0], sigma4=sigma[1], units=wl.COUPLING_MASS_WEIGHTED)
+    p_eq, q_eq = wl.ground_chi(pes.omega)
+    n, n_steps = 96, 600
+    p0, q0, _ = oracle.sample_initial(pes.omega, p_eq, q_eq, n, 5)
+    dev = np.empty((n, n_steps))
+    for j in range(n):
+        r = oracle.propagate_one(pes, pes.omega, p_eq, q_eq, 10.0, n_steps, p0[:, j], q0[:, j])
+        d = r["detM"][1:]
+        dev[j] = np.where(np.isfinite(d), np.abs(d * d - 1.0), np.inf)
+    for tol in (1e-6, 1e-6 * 2.0 ** 29):
+        every = ~(dev > tol).any(axis=1)
+        assert 0 < every.sum() < n
+        for C in (8, 16):
+            ends = np.r_[np.arange(C - 1, n_steps, C), n_steps - 1]
+            chunk = ~(dev[:, ends] > tol).any(axis=1)
+            assert np.array_equal(every, chunk), (tol, C, np.flatnonzero(every != chunk))

@@ -56,6 +56,8 @@ def test_noalloc_spectrum_matches_allocating_entry_point():
         (1100, 333, 2001, 0.002, 0.055, 1),
         (1100, 333, 2001, 0.002, 0.055, 1),   # the same call again: stale scratch must not matter
         (70, 40, 77, 0.0, 0.03, 2),            # a different shape after a larger one
+        (70, 10, 300001, 0.0, 0.2, 3),         # a grid that leaves room for one row slice only
+        (70, 10, 524256, 0.0, 0.2, 4),         # the largest grid: the slice fills the scratch to its end
     ]
     for n, n_steps, n_E, E_min, E_max, seed in cases:
         amp, w, good = _inputs(n, n_steps, seed)
