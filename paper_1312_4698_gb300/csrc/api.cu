@@ -270,6 +270,14 @@ int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out)
     const size_t o_T3 = push(T3.data(), T3.size());
     const size_t o_T4 = push(T4.data(), T4.size());
     std::vector<float> T3f(T3.begin(), T3.end()), T4f(T4.begin(), T4.end());
+    // the same tensors with every row padded to a multiple of 4 floats (16-byte loads of four
+    // consecutive Hessian entries; the kernels above F = 16 read them from global memory)
+    const int P4 = (P + 3) & ~3;
+    std::vector<float> T3p((size_t)F * P4, 0.0f), T4p((size_t)P * P4, 0.0f);
+    for (int k = 0; k < F; ++k)
+        for (int e = 0; e < P; ++e) T3p[(size_t)k * P4 + e] = T3f[(size_t)k * P + e];
+    for (int kl = 0; kl < P; ++kl)
+        for (int e = 0; e < P; ++e) T4p[(size_t)kl * P4 + e] = T4f[(size_t)kl * P + e];
     std::vector<float> diagf(3 * 64, 0.0f);   // omega, D, a in FP32, 64-float slots
     for (int i = 0; i < F; ++i) {
         diagf[i] = (float)d->omega[i];
@@ -277,7 +285,8 @@ int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out)
         diagf[128 + i] = d->diag_kind == SCIVR_DIAG_MORSE ? (float)d->a[i] : 0.0f;
     }
     const size_t nd = hostblob.size();
-    const size_t bytes = nd * sizeof(double) + (T3f.size() + T4f.size() + diagf.size() + 256) * sizeof(float);
+    const size_t bytes = nd * sizeof(double) +
+                         (T3f.size() + T4f.size() + diagf.size() + T3p.size() + T4p.size() + 4 * 256) * sizeof(float);
 
     void *blob = nullptr;
     cudaError_t e = cudaMalloc(&blob, bytes);
@@ -290,6 +299,10 @@ int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out)
     if (e == cudaSuccess) e = cudaMemcpy(b + o_T4f, T4f.data(), T4f.size() * sizeof(float), cudaMemcpyHostToDevice);
     const size_t o_diagf = o_T4f + ((T4f.size() * sizeof(float) + 255) & ~(size_t)255);
     if (e == cudaSuccess) e = cudaMemcpy(b + o_diagf, diagf.data(), diagf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    const size_t o_T3p = o_diagf + ((diagf.size() * sizeof(float) + 255) & ~(size_t)255);
+    const size_t o_T4p = o_T3p + ((T3p.size() * sizeof(float) + 255) & ~(size_t)255);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_T3p, T3p.data(), T3p.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_T4p, T4p.data(), T4p.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blob);
         return cuda_fail(e, "scivr_create_pes: cudaMemcpy");
@@ -311,6 +324,9 @@ int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out)
     dv.T4 = db + o_T4;
     dv.T3f = reinterpret_cast<const float *>(b + o_T3f);
     dv.T4f = reinterpret_cast<const float *>(b + o_T4f);
+    dv.P4 = P4;
+    dv.T3p = reinterpret_cast<const float *>(b + o_T3p);
+    dv.T4p = reinterpret_cast<const float *>(b + o_T4p);
     dv.omega_f = reinterpret_cast<const float *>(b + o_diagf);
     dv.D_f = dv.omega_f + 64;
     dv.a_f = dv.omega_f + 128;

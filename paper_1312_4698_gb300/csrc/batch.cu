@@ -75,7 +75,7 @@ void save_tune_file()
 // Time one candidate CTA shape on a probe copy of launch record L.
 cudaError_t time_candidate(const PropLaunch &L, int warps, int n_sm, float *ms)
 {
-    const int G = 2 * L.args.F <= 8 ? 8 : (2 * L.args.F <= 16 ? 16 : 32);
+    const int G = mixed_group_lanes(L.args.F);
     const int per_tile = warps * (32 / G);
     PropLaunch P = L;
     P.args.n_steps = std::min(L.args.n_steps, 64);
@@ -231,7 +231,7 @@ int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t f
             delete B;
             return cuda_error(e, "scivr_batch_create: autotune");
         }
-        const int G = 2 * g.F <= 8 ? 8 : (2 * g.F <= 16 ? 16 : 32);
+        const int G = mixed_group_lanes(g.F);
         const int per_tile = g.warps * (32 / G);
         std::vector<int2> &w = works[gi];
         for (int k = 0; k < (int)g.members.size(); ++k) {

@@ -1,0 +1,14 @@
+// Instantiations of the lane-group propagation kernel above F = 16 (two monodromy
+// columns per lane, coupling tensors read from L2; mixed precision only; split for
+// parallel builds).
+#include "propagate_lg.cuh"
+
+namespace scivr {
+
+template cudaError_t launch_group_mixed<17>(const PropLaunch &, cudaStream_t);
+template cudaError_t launch_group_mixed<18>(const PropLaunch &, cudaStream_t);
+
+template cudaError_t launch_group_batch_mixed_F<17>(int, const PropLaunch *, const int2 *, int, int *, int, cudaStream_t);
+template cudaError_t launch_group_batch_mixed_F<18>(int, const PropLaunch *, const int2 *, int, int *, int, cudaStream_t);
+
+}  // namespace scivr

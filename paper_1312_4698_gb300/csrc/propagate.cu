@@ -12,9 +12,9 @@ cudaError_t launch_group_batch_mixed_F(int warps, const PropLaunch *items, const
 
 int batch_warp_candidates(int F, int *out)
 {
-    if (F < 1 || F > 16) return 0;
+    if (F < 1 || F > 24) return 0;
     if (F > 9) { out[0] = F <= 12 ? 8 : 4; return 1; }   // wide groups: one CTA per SM shares the tensors
-    if (2 * F > 16) { out[0] = 1; out[1] = 2; }
+    if (mixed_group_lanes(F) == 32) { out[0] = 1; out[1] = 2; }
     else { out[0] = 2; out[1] = 4; }
     return 2;
 }
@@ -26,6 +26,7 @@ cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, 
 #define SCIVR_B(FF) case FF: return launch_group_batch_mixed_F<FF>(warps, items, work, n_work, counter, n_sm, s);
     SCIVR_B(1) SCIVR_B(2) SCIVR_B(3) SCIVR_B(4) SCIVR_B(5) SCIVR_B(6) SCIVR_B(7) SCIVR_B(8) SCIVR_B(9)
     SCIVR_B(10) SCIVR_B(11) SCIVR_B(12) SCIVR_B(13) SCIVR_B(14) SCIVR_B(15) SCIVR_B(16)
+    SCIVR_B(17) SCIVR_B(18) SCIVR_B(19) SCIVR_B(20) SCIVR_B(21) SCIVR_B(22) SCIVR_B(23) SCIVR_B(24)
 #undef SCIVR_B
     default: return cudaErrorInvalidValue;
     }
@@ -35,7 +36,7 @@ namespace {
 
 constexpr int kMaxThreadF = 9;   // thread-per-trajectory FP64 kernel
 constexpr int kMaxGroupF = 9;    // FP64 lane-group kernel
-constexpr int kMaxMixedF = 16;   // mixed lane-group kernel (2F <= 32 lanes; one trajectory per warp above F = 9)
+constexpr int kMaxMixedF = 24;   // mixed lane-group kernel (one trajectory per warp above F = 9, two columns per lane above F = 16)
 
 // Schedule choice when the caller leaves it to the library: the lane-group
 // kernel keeps every SM busy with few trajectories (it launches G lanes per
@@ -86,6 +87,14 @@ cudaError_t launch_propagate(const PropLaunch &L, cudaStream_t s, int *n_launch)
             case 14: return launch_group_mixed<14>(L, s);
             case 15: return launch_group_mixed<15>(L, s);
             case 16: return launch_group_mixed<16>(L, s);
+            case 17: return launch_group_mixed<17>(L, s);
+            case 18: return launch_group_mixed<18>(L, s);
+            case 19: return launch_group_mixed<19>(L, s);
+            case 20: return launch_group_mixed<20>(L, s);
+            case 21: return launch_group_mixed<21>(L, s);
+            case 22: return launch_group_mixed<22>(L, s);
+            case 23: return launch_group_mixed<23>(L, s);
+            case 24: return launch_group_mixed<24>(L, s);
             default: break;
         }
     } else if (kern == SCIVR_KERNEL_GROUP) {

@@ -35,6 +35,8 @@
 
 #include <math_constants.h>
 #include <cstddef>
+#include <utility>
+#include <type_traits>
 
 #include "scivr_internal.cuh"
 
@@ -67,9 +69,95 @@ __device__ __forceinline__ double recip64(double x)
 }
 
 
+// Compile-time loop: f(std::integral_constant<int, k>) for k = 0..N-1, every index a
+// constant (the unroller would leave long loops rolled, indexing register arrays).
+template <typename Fn, int... Ks>
+__device__ __forceinline__ void static_for_impl(Fn &&f, std::integer_sequence<int, Ks...>)
+{
+    (f(std::integral_constant<int, Ks>{}), ...);
+}
+template <int N, typename Fn>
+__device__ __forceinline__ void static_for(Fn &&f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 template <typename Real> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<double> { using T = double2; };
+
+// Storage of one entry of the Herman-Kluk matrix A during its elimination: FP64
+// path a double2 (re, im); mixed path a double-FP32 complex (re.hi, re.lo, im.hi,
+// im.lo) -- the entries are formed in FP32 and eliminated to FP64-class accuracy.
+template <typename Real> struct AEntry;
+template <> struct AEntry<float> { using T = float4; };
+template <> struct AEntry<double> { using T = double2; };
+
+// ---- double-FP32 arithmetic (hi + lo, |lo| <= ulp(hi)/2): error-free sum and
+// product of two floats (Knuth's TwoSum, the FMA form of Dekker's TwoProduct) and
+// the compositions the elimination needs.  Accuracy about 2^-46 relative per
+// operation, on the FP32 pipe.
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ ff ff_norm(float hi, float lo)    // |lo| well below |hi| or hi == 0
+{
+    ff r;
+    r.hi = hi + lo;
+    r.lo = lo - (r.hi - hi);
+    return r;
+}
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return ff_norm(p, e);
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    float s, e;
+    ff_two_sum(x.hi, y.hi, s, e);
+    return ff_norm(s, e + (x.lo + y.lo));
+}
+
+// a - x u + y v for double-FP32 a, x, u, y, v (one real part of a complex
+// multiply-subtract): both products exact to their double-FP32 width, both sums
+// error-free in their leading words.
+__device__ __forceinline__ ff ff_sub_mul_add_mul(ff a, ff x, ff u, ff y, ff v)
+{
+    const float p1 = x.hi * u.hi;
+    float e1 = fmaf(x.hi, u.hi, -p1);
+    e1 = fmaf(x.hi, u.lo, e1);
+    e1 = fmaf(x.lo, u.hi, e1);
+    const float p2 = y.hi * v.hi;
+    float e2 = fmaf(y.hi, v.hi, -p2);
+    e2 = fmaf(y.hi, v.lo, e2);
+    e2 = fmaf(y.lo, v.hi, e2);
+    float s1, t1, s2, t2;
+    ff_two_sum(a.hi, -p1, s1, t1);
+    ff_two_sum(s1, p2, s2, t2);
+    return ff_norm(s2, ((a.lo - e1) + e2) + (t1 + t2));
+}
+
+// 1 / m for double-FP32 m > 0: the FP32 reciprocal refined by one Newton step on
+// the exact FMA residual.
+__device__ __forceinline__ ff ff_recip(ff m)
+{
+    const float y0 = 1.0f / m.hi;
+    float r = fmaf(-m.hi, y0, 1.0f);   // 1 - m.hi y0, exact
+    r = fmaf(-m.lo, y0, r);
+    return ff_norm(y0, y0 * r);
+}
 
 // Per-mode and per-reference-state constants, staged in shared memory so that
 // lane- or chi-dependent indexing never touches the kernel-parameter space.
@@ -95,19 +183,30 @@ template <typename Real, int F> __device__ __forceinline__ Real c_w2(const CtaCo
 template <int JOBS>
 __device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & (JOBS >= 16 ? 15 : JOBS - 1)); }
 
-// Steps per chunk of a lane group.  Phases 2-4 give one job (trajectory, step) to
-// each lane: T * C jobs per warp.  Groups of 8 and 16 lanes fill all 32 lanes; the
-// one-trajectory-per-warp groups take 16 jobs (F = 9) or 8 (F > 9), so that the
-// per-job prefactor matrices (F^2 complex entries each) leave room in shared memory
-// for more warps per SM.
-template <int F, int G> __host__ __device__ constexpr int lg_chunk() { return G < 32 ? G : (F > 9 ? 8 : 16); }
+// Steps per chunk of a lane group.  Phases 2-4 work on T * C jobs (trajectory, step)
+// per warp.  FP64 path: one lane per job; groups of 8 and 16 lanes fill all 32 lanes,
+// the one-trajectory-per-warp groups take 16 jobs (F = 9) or 8 (F > 9).  Mixed path:
+// the double-FP32 elimination keeps two FP32 words per real entry, so chunks are
+// shorter (8 steps; 4 above F = 12) and 32 / (T * C) lanes share a job's elimination
+// by rows; the per-job prefactor matrices then take the same shared memory as one
+// FP32 word per entry at the FP64 path's chunk length.
+template <int F, int G, typename Real> __host__ __device__ constexpr int lg_chunk()
+{
+    if constexpr (sizeof(Real) == 4) return G == 32 && F > 16 ? 2 : ((G == 32 && F > 12) || (G == 16 && F > 8) ? 4 : 8);
+    else return G < 32 ? G : (F > 9 ? 8 : 16);
+}
 
 // Warps per CTA and the launch-bounds CTA count: the wide groups (F > 9) run one CTA per
 // SM on one copy of the coupling tensors, 8 warps up to F = 12 and 4 above (measured:
 // at F = 15 the 8-warp CTA's 216 KB of shared memory leaves too little L1 and runs 16 %
 // slower; at F = 12 8 warps are 5 % faster).
 template <int F, int G> __host__ __device__ constexpr int lg_warps() { return G < 32 ? 4 : (F <= 9 ? 2 : (F <= 12 ? 8 : 4)); }
-template <int F> __host__ __device__ constexpr int lg_min_ctas() { return F > 9 ? 1 : 4; }
+// (F > 16: 4 warps, one CTA per SM: 18 KB of per-job prefactor matrices and 9 KB of det M
+// workspace per warp at F = 24)
+template <int F, int G, typename Real> __host__ __device__ constexpr int lg_min_ctas()
+{
+    return F > 9 ? 1 : (sizeof(Real) == 4 && 2 * F > G ? 3 : 4);
+}
 
 // 16-byte vectors of Real for shared-memory loads.
 template <typename Real> struct V16;
@@ -169,16 +268,20 @@ struct TensorLayout {
     static constexpr int P = F * (F + 1) / 2;
     static constexpr int S3 = vec_len<Real>(F);   // short rows: fewer loads outweigh a 2-way conflict
     static constexpr int S4 = row_stride<Real>(P);
+    // Above F = 16 the quartic tensor (P^2 entries, 360 KB at F = 24) does not fit shared
+    // memory: both tensors are read from global memory (L2) and only the coefficients are staged.
+    static constexpr bool staged = F <= 16;
     // after the tensors: the Herman-Kluk matrix coefficients acoef[a][b][4] =
     // (1/2) {rg_a/rg_b, rg_b/rg_a, -rg_a rg_b, 1/(rg_a rg_b)}, rg = sqrt(gamma)
-    static constexpr size_t bytes = ((sizeof(Real) * (size_t)(P * S3 + P * S4 + 4 * F * F)) + 15) & ~(size_t)15;
+    static constexpr size_t bytes =
+        ((sizeof(Real) * (size_t)((staged ? P * S3 + P * S4 : 0) + 4 * F * F)) + 15) & ~(size_t)15;
 };
 
 template <int F, int G, typename Real>
 struct WarpShared {
     static constexpr int P = F * (F + 1) / 2;
     static constexpr int T = 32 / G;
-    static constexpr int JOBS = T * lg_chunk<F, G>();   // jobs per chunk (phases 2-4)
+    static constexpr int JOBS = T * lg_chunk<F, G, Real>();   // jobs per chunk (phases 2-4)
     static constexpr int S3 = TensorLayout<F, Real>::S3;   // q, zero-padded (also the Gc row stride)
     static constexpr int S4 = TensorLayout<F, Real>::S4;   // pair products q_k q_l, zero-padded
     static constexpr int SH = vec_len<Real>(F);            // row stride of H (rows read by the whole group)
@@ -186,12 +289,18 @@ struct WarpShared {
     alignas(16) Real qq[T][S4];
     alignas(16) Real Gc[T][F][S3];          // gradient coefficients, full symmetric matrix (row a read by mode lane a)
     alignas(16) Real H[T][F][SH];
-    typename Vec2<Real>::T A[F * F][JOBS]; // prefactor matrix per job, entry-major (job column swizzled)
+    typename AEntry<Real>::T A[F * F][JOBS]; // prefactor matrix per job, entry-major (job column swizzled)
     Real pj[F][JOBS], qj[F][JOBS];         // state per job, for the overlap (job column swizzled); FP32
                                            // in the mixed path, where the overlap is evaluated in FP32
     double Sj[JOBS];                        // action per job
     double lnA[JOBS];                       // log |det A|^{1/2} per job (Herman-Kluk summand only)
+    double argj[JOBS];                      // arg det A per job (mixed path: from the elimination's lanes)
+    double2 detAj[JOBS];                    // det A per job (mixed path)
     double2 ov0[SCIVR_MAX_CHI][T];          // log of the Herman-Kluk summand's divisor per trajectory
+    // above F = 16, det M eliminates rows of M^T held here (row stride 2F + 1: lanes reading
+    // the same column of different rows hit different banks) instead of in registers
+    static constexpr int WMR = F > 16 ? 2 * F : 1;
+    Real Wm[WMR][WMR + 1];
 };
 
 // One CTA's share of a propagation: trajectories (cta * WARPS + warp) * T + t.
@@ -204,18 +313,19 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     constexpr int N2 = 2 * F;
     constexpr int P = F * (F + 1) / 2;
     constexpr int T = 32 / G;
-    constexpr int C = lg_chunk<F, G>();        // steps per chunk
-    constexpr int JOBS = T * C;                // jobs per chunk: lane ln < JOBS takes job ln in phases 2-4
+    constexpr int C = lg_chunk<F, G, Real>();  // steps per chunk
+    constexpr int JOBS = T * C;                // jobs per chunk: job t * C + c is trajectory t's step c
     constexpr int EPL = (P + G - 1) / G;       // packed Hessian entries per lane
-    static_assert(N2 <= G, "group must hold all 2F columns");
+    constexpr int NCOL = (N2 + G - 1) / G;     // monodromy columns per lane: column c sits in lane c % G, slot c / G
+    static_assert(F <= G && NCOL <= 2, "a group holds every mode and at most two columns per lane");
     using Sh = WarpShared<F, G, Real>;
     using R2 = typename Vec2<Real>::T;
 
     using TL = TensorLayout<F, Real>;
     constexpr int S3 = TL::S3, S4 = TL::S4;
     Real *sT3 = reinterpret_cast<Real *>(smem_raw);
-    Real *sT4 = sT3 + P * S3;
-    Real *sAc = sT4 + P * S4;   // Herman-Kluk matrix coefficients [a][b][4] (16-byte aligned: P * (S3 + S4) is a vector multiple)
+    Real *sT4 = sT3 + (TL::staged ? P * S3 : 0);
+    Real *sAc = sT4 + (TL::staged ? P * S4 : 0);   // Herman-Kluk matrix coefficients [a][b][4] (16-byte aligned: P * (S3 + S4) is a vector multiple)
     size_t off = TL::bytes;
     CtaConst<F> &cc = *reinterpret_cast<CtaConst<F> *>(smem_raw + off);
     off += (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
@@ -225,7 +335,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     const PropArgs &A = L.args;
     const bool use3 = pes.has3, use4 = pes.has4;
     // stage the coupling tensors once per CTA
-    {
+    if constexpr (TL::staged) {
         const Real *g3 = nullptr, *g4 = nullptr;
         if constexpr (sizeof(Real) == 4) { g3 = reinterpret_cast<const Real *>(pes.T3f); g4 = reinterpret_cast<const Real *>(pes.T4f); }
         else { g3 = reinterpret_cast<const Real *>(pes.T3); g4 = reinterpret_cast<const Real *>(pes.T4); }
@@ -252,9 +362,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             cc.af[a] = pes.a_f[a];
             cc.w2f[a] = pes.omega_f[a] * pes.omega_f[a];
         }
-#pragma unroll
+        // (rolled: thread 0 alone, and unrolling F^2 iterations starves the step loop of registers)
         for (int a = 0; a < F; ++a)
-#pragma unroll
             for (int b = 0; b < F; ++b) {
                 const Real rga = (Real)A.rg[a], irga = (Real)A.irg[a], rgb = (Real)A.rg[b], irgb = (Real)A.irg[b];
                 Real *k = sAc + 4 * (a * F + b);
@@ -301,25 +410,42 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         ea[i] = a;
         eb[i] = a + e;
     }
+    // above F = 16: four consecutive entries 4 (g + i G) .. + 3 per load, (a, b) packed as a | b << 8
+    constexpr int P4 = (P + 3) & ~3;
+    constexpr int NQ = TL::staged ? 1 : (P4 / 4 + G - 1) / G;
+    int eq[TL::staged ? 1 : 4 * NQ];
+    if constexpr (!TL::staged) {
+#pragma unroll
+        for (int i = 0; i < 4 * NQ; ++i) {
+            int e = 4 * (g + (i / 4) * G) + i % 4, a = 0;
+            if (e >= P) e = 0;
+            while (e >= F - a) { e -= F - a; ++a; }
+            eq[i] = a | ((a + e) << 8);
+        }
+    }
 
     // mode state (lane g < F)
     const int mode = g < F ? g : 0;
     double p = L.p0[mode * n + jl], q = L.q0[mode * n + jl];
     Real pr = (Real)p;          // the momentum as seen by the Real-precision bulk
     double S = 0.0;             // accumulated action (lane 0 of the group holds the total)
-    // column state (lane g < 2F): column g of M = d(p,q)/d(p0,q0)
-    Real Mp[F], Mq[F];
+    // column state: slot s of lane g holds column c = g + s G of M = d(p,q)/d(p0,q0) (c < 2F;
+    // a slot past 2F holds a zero column)
+    Real Mp[NCOL][F], Mq[NCOL][F];
 #pragma unroll
-    for (int a = 0; a < F; ++a) {
-        Mp[a] = (g < F && a == g) ? Real(1) : Real(0);
-        Mq[a] = (g >= F && g < N2 && a == g - F) ? Real(1) : Real(0);
+    for (int s = 0; s < NCOL; ++s) {
+        const int col = g + s * G;
+#pragma unroll
+        for (int a = 0; a < F; ++a) {
+            Mp[s][a] = (col < F && a == col) ? Real(1) : Real(0);
+            Mq[s][a] = (col >= F && col < N2 && a == col - F) ? Real(1) : Real(0);
+        }
     }
     bool good = true;
     Real stab = Real(0);
     double detM_last = 1.0;
     double theta_last = 0.0, arg_last = 0.0;
-    double2 detA_last = make_double2(1.0, 0.0);   // FP64 path
-    double lnAbs_last = 0.0;                      // mixed path: ln |det A| of the last step
+    double2 detA_last = make_double2(1.0, 0.0);   // det A of the last step
 
     // amplitude at c = 0 (M = I, S = 0, theta = 0): lane 0 of each group
     if (g == 0 && active) {
@@ -365,7 +491,9 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         dS = fma(rt * Real(0.5) * pr, pr, dS);
                     }
 #pragma unroll
-                    for (int a = 0; a < F; ++a) Mq[a] = fma(rt, Mp[a], Mq[a]);
+                    for (int s = 0; s < NCOL; ++s)
+#pragma unroll
+                        for (int a = 0; a < F; ++a) Mq[s][a] = fma(rt, Mp[s][a], Mq[s][a]);
                 }
                 if (sub == 3) break;
                 // kick: potential at q
@@ -382,6 +510,54 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 }
                 __syncwarp();
                 Real vpart = Real(0);
+                if constexpr (!TL::staged) {
+                    // entry quads against the tensors in global memory (L2-resident; [k][e] and
+                    // [kl][e] rows padded to P4): one 16-byte load feeds four entries
+                    static_assert(sizeof(Real) == 4, "the global-tensor schedule is the mixed path's");
+                    const float4 *T3v = reinterpret_cast<const float4 *>(pes.T3p);
+                    const float4 *T4v = reinterpret_cast<const float4 *>(pes.T4p);
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) {
+                        const int q4 = g + i * G;
+                        if (4 * q4 < P) {
+                            float4 h3 = make_float4(0.f, 0.f, 0.f, 0.f), h4 = h3;
+                            if (use3) {
+#pragma unroll 8
+                                for (int k = 0; k < F; ++k) {
+                                    const float4 tv = __ldg(T3v + k * (P4 / 4) + q4);
+                                    const float x = sh.qr[t][k];
+                                    h3.x = fmaf(tv.x, x, h3.x); h3.y = fmaf(tv.y, x, h3.y);
+                                    h3.z = fmaf(tv.z, x, h3.z); h3.w = fmaf(tv.w, x, h3.w);
+                                }
+                            }
+                            if (use4) {
+#pragma unroll 4
+                                for (int kl = 0; kl < P; ++kl) {
+                                    const float4 tv = __ldg(T4v + kl * (P4 / 4) + q4);
+                                    const float x = sh.qq[t][kl];
+                                    h4.x = fmaf(tv.x, x, h4.x); h4.y = fmaf(tv.y, x, h4.y);
+                                    h4.z = fmaf(tv.z, x, h4.z); h4.w = fmaf(tv.w, x, h4.w);
+                                }
+                            }
+                            const float h3j[4] = {h3.x, h3.y, h3.z, h3.w}, h4j[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int e = 4 * q4 + j;
+                                if (e < P) {
+                                    const int a = eq[4 * i + j] & 255, b = eq[4 * i + j] >> 8;
+                                    const Real h = h3j[j] + h4j[j];
+                                    sh.H[t][a][b] = h;
+                                    sh.H[t][b][a] = h;
+                                    const Real gce = fma(Real(0.5), h3j[j], h4j[j] * Real(1.0 / 3.0));
+                                    sh.Gc[t][a][b] = gce;
+                                    sh.Gc[t][b][a] = gce;
+                                    const Real vc = fma(Real(1.0 / 6.0), h3j[j], h4j[j] * Real(1.0 / 12.0));
+                                    vpart = fma(a == b ? vc : Real(2) * vc, sh.qq[t][e], vpart);
+                                }
+                            }
+                        }
+                    }
+                } else
 #pragma unroll
                 for (int i = 0; i < EPL; ++i) {
                     const int e = g + i * G;
@@ -432,42 +608,111 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     constexpr int NV = V16<Real>::N, SH = Sh::SH;
 #pragma unroll
                     for (int a = 0; a < F; ++a) {
-                        Real acc = Real(0);
+                        Real acc[NCOL];
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s) acc[s] = Real(0);
 #pragma unroll
                         for (int b0 = 0; b0 < SH; b0 += NV) {
                             const VT v = *reinterpret_cast<const VT *>(&sh.H[t][a][b0]);
 #pragma unroll
                             for (int j = 0; j < NV; ++j)
-                                if (b0 + j < F) acc = fma(vcomp<Real>(v, j), Mq[b0 + j], acc);
+                                if (b0 + j < F) {
+#pragma unroll
+                                    for (int s = 0; s < NCOL; ++s) acc[s] = fma(vcomp<Real>(v, j), Mq[s][b0 + j], acc[s]);
+                                }
                         }
-                        Mp[a] = fma(-rtk, acc, Mp[a]);
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s) Mp[s][a] = fma(-rtk, acc[s], Mp[s][a]);
                     }
                 }
             }
             // ---- stability: det M = det M^T by Gaussian elimination of M^T with partial pivoting ----
-            // Lane c holds column c of M, i.e. row c of M^T.  Stage k picks, among the lanes not
-            // used yet, the one with the largest |M[k][c]| (an arg-max over the group by warp
-            // reduction, ties to the higher lane), and every other unused lane subtracts its multiple of
-            // the pivot lane's entries below row k.  Lanes are marked used instead of being moved;
-            // the sign of det is the parity of the order in which the lanes were picked, counted
-            // as inversions on the bitmask of unused lanes.
-            {
-                Real W[N2];
+            // Column c of M (lane c % G, slot c / G) is row c of M^T.  Stage k picks, among the rows
+            // not used yet, the one with the largest |M[k][c]| (an arg-max over the group by warp
+            // reduction, ties to the higher row), and every other unused row subtracts its multiple
+            // of the pivot row's entries below k.  Rows are marked used instead of being moved; the
+            // sign of det is the parity of the order in which they were picked, counted as
+            // inversions on the bitmask of unused rows.
+            // Cadence: the FP64 path tests every step (flags equal to the oracle's bit for bit);
+            // the mixed path tests at the last step of each chunk.  The flag is sticky and a bad
+            // trajectory is dropped whole, so the two differ only for a trajectory whose deviation
+            // crosses the threshold and falls back below it within one chunk; the FP32 threshold
+            // (537) sits far above the rounding noise, where a deviation that has grown past it
+            // keeps growing (Sec. III.A: chaotic trajectories are the ones removed).
+            if constexpr (F > 16) {
+                if (c == cnt - 1) {
+                    static_assert(T == 1, "one trajectory per warp above F = 16");
 #pragma unroll
-                for (int a = 0; a < F; ++a) { W[a] = Mp[a]; W[F + a] = Mq[a]; }
+                    for (int s = 0; s < NCOL; ++s) {
+                        const int col = g + s * G;
+                        if (col < N2) {
+#pragma unroll
+                            for (int a = 0; a < F; ++a) { sh.Wm[col][a] = Mp[s][a]; sh.Wm[col][F + a] = Mq[s][a]; }
+                        }
+                    }
+                    __syncwarp();
+                    Real det = Real(1);
+                    unsigned long long unused = (1ull << N2) - 1ull;
+                    unsigned parity = 0u;
+                    for (int k = 0; k < N2; ++k) {
+                        unsigned key = 0u;
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s) {
+                            const int col = g + s * G;
+                            if (col < N2 && ((unused >> col) & 1ull)) {
+                                const unsigned kk = (__float_as_uint(fabsf(sh.Wm[col][k])) & ~63u) | (unsigned)(col + 1);
+                                key = kk > key ? kk : key;
+                            }
+                        }
+                        const unsigned kmax = __reduce_max_sync(FULL, key);
+                        const int pc = (int)(kmax & 63u) - 1;
+                        const Real pk = sh.Wm[pc][k];
+                        const Real inv = __fdividef(1.0f, pk);
+                        parity ^= (unsigned)__popcll(unused & ((1ull << pc) - 1ull)) & 1u;
+                        unused &= ~(1ull << pc);
+                        det *= pk;
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s) {
+                            const int col = g + s * G;
+                            if (col < N2 && ((unused >> col) & 1ull)) {
+                                const Real l = sh.Wm[col][k] * inv;
+                                for (int i = k + 1; i < N2; ++i) sh.Wm[col][i] = fma(-l, sh.Wm[pc][i], sh.Wm[col][i]);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    if (parity) det = -det;
+                    const Real dev = isfinite(det) ? fabs(fma(det, det, Real(-1))) : Real(CUDART_INF);
+                    stab = dev > stab ? dev : stab;
+                    if (dev > A.stab_tol_f) good = false;
+                    detM_last = (double)det;
+                }
+            } else
+            if (sizeof(Real) == 8 || c == cnt - 1) {
+                Real W[NCOL][N2];
+#pragma unroll
+                for (int s = 0; s < NCOL; ++s)
+#pragma unroll
+                    for (int a = 0; a < F; ++a) { W[s][a] = Mp[s][a]; W[s][F + a] = Mq[s][a]; }
                 Real det = Real(1);
-                unsigned unused = N2 == 32 ? FULL : (1u << N2) - 1u;
+                unsigned long long unused = N2 == 64 ? ~0ull : (1ull << N2) - 1ull;
                 unsigned parity = 0u;
+                static_for<N2>([&](auto kc) {
+                    constexpr int k = decltype(kc)::value;
+                    // non-negative floats order like their bit patterns; the low 6 bits carry row + 1
+                    // (so a used or idle slot's key 0 never wins), at the cost of 6 mantissa bits of
+                    // the comparison
+                    unsigned key = 0u;
 #pragma unroll
-                for (int k = 0; k < N2; ++k) {
-                    const bool mine = (unused >> g) & 1u;   // false for the idle lanes g >= 2F
-                    float mag;
-                    if constexpr (sizeof(Real) == 4) mag = fabsf(W[k]); else mag = (float)fabs(W[k]);
-                    // non-negative floats order like their bit patterns; the low 6 bits carry lane + 1
-                    // (so an unused lane's key 0 never wins), at the cost of 6 mantissa bits of the
-                    // comparison
-                    const unsigned key = mine ? ((__float_as_uint(mag) & ~63u) | (unsigned)(g + 1)) : 0u;
-
+                    for (int s = 0; s < NCOL; ++s) {
+                        const int col = g + s * G;
+                        if (col < N2 && ((unused >> col) & 1ull)) {
+                            float mag;
+                            if constexpr (sizeof(Real) == 4) mag = fabsf(W[s][k]); else mag = (float)fabs(W[s][k]);
+                            const unsigned kk = (__float_as_uint(mag) & ~63u) | (unsigned)(col + 1);
+                            key = kk > key ? kk : key;
+                        }
+                    }
                     // one full-warp integer max per group (the other groups' lanes contribute 0)
                     unsigned kmax = 0u;
 #pragma unroll
@@ -475,23 +720,33 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         const unsigned r = __reduce_max_sync(FULL, t == tt ? key : 0u);
                         kmax = (t == tt) ? r : kmax;
                     }
-                    const int pl = (int)(kmax & 63u) - 1;
-                    const Real pk = __shfl_sync(FULL, W[k], base + pl);
+                    const int pc = (int)(kmax & 63u) - 1;          // pivot row of M^T
+                    const int pl = base + pc % G, ps = pc / G;     // its lane and slot
+                    auto sel = [&](int i) -> Real { if constexpr (NCOL == 1) return W[0][i]; else return ps ? W[1][i] : W[0][i]; };
+                    const Real pk = __shfl_sync(FULL, sel(k), pl);
                     // FP32: the hardware reciprocal (det M only feeds the stability test, whose FP32
                     // tolerance is far above its ulp-level error); FP64: exact division
                     Real inv;
                     if constexpr (sizeof(Real) == 4) inv = __fdividef(1.0f, pk); else inv = Real(1) / pk;
-                    parity ^= (unsigned)__popc(unused & ((1u << pl) - 1u)) & 1u;
-                    unused &= ~(1u << pl);
+                    parity ^= (unsigned)__popcll(unused & ((1ull << pc) - 1ull)) & 1u;
+                    unused &= ~(1ull << pc);
                     det *= pk;
-                    const Real l = W[k] * inv;
-                    const bool elim = mine && g != pl;
+                    Real l[NCOL];
+                    bool elim[NCOL];
+#pragma unroll
+                    for (int s = 0; s < NCOL; ++s) {
+                        const int col = g + s * G;
+                        elim[s] = col < N2 && ((unused >> col) & 1ull);
+                        l[s] = W[s][k] * inv;
+                    }
 #pragma unroll
                     for (int i = k + 1; i < N2; ++i) {
-                        const Real wp = __shfl_sync(FULL, W[i], base + pl);
-                        if (elim) W[i] = fma(-l, wp, W[i]);
+                        const Real wp = __shfl_sync(FULL, sel(i), pl);
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s)
+                            if (elim[s]) W[s][i] = fma(-l[s], wp, W[s][i]);
                     }
-                }
+                });
                 if (parity) det = -det;
                 const Real dev = isfinite(det) ? fabs(fma(det, det, Real(-1))) : Real(CUDART_INF);
                 stab = dev > stab ? dev : stab;
@@ -502,12 +757,17 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             }
             // ---- Herman-Kluk matrix column b = g (needs column F + b) ----
             {
-                const int src = base + F + (g < F ? g : 0);
+                // column F + g sits in lane (F + g) % G; a lane h sends column h (h >= F, slot 0)
+                // or column h + G (h < F, slot 1) -- the only one any mode lane asks it for
+                const int src = base + (F + (g < F ? g : 0)) % G;
                 const int job = t * C + c;
 #pragma unroll
                 for (int a = 0; a < F; ++a) {
-                    const Real mpq = __shfl_sync(FULL, Mp[a], src);
-                    const Real mqq = __shfl_sync(FULL, Mq[a], src);
+                    Real sp, sq;
+                    if constexpr (NCOL == 1) { sp = Mp[0][a]; sq = Mq[0][a]; }
+                    else { sp = g >= F ? Mp[0][a] : Mp[1][a]; sq = g >= F ? Mq[0][a] : Mq[1][a]; }
+                    const Real mpq = __shfl_sync(FULL, sp, src);
+                    const Real mqq = __shfl_sync(FULL, sq, src);
                     if (g < F) {
                         using VT = typename V16<Real>::T;
                         constexpr int NV = V16<Real>::N;
@@ -519,9 +779,12 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                             for (int j = 0; j < NV; ++j) k4[j0 + j] = vcomp<Real>(kv, j);
                         }
                         R2 v;
-                        v.x = fma(k4[0], mqq, k4[1] * Mp[a]);
-                        v.y = fma(k4[2], Mq[a], k4[3] * mpq);
-                        sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = v;
+                        v.x = fma(k4[0], mqq, k4[1] * Mp[0][a]);
+                        v.y = fma(k4[2], Mq[0][a], k4[3] * mpq);
+                        if constexpr (sizeof(Real) == 4)
+                            sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = make_float4(v.x, 0.0f, v.y, 0.0f);
+                        else
+                            sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = v;
                     }
                 }
                 if (g < F) {
@@ -545,72 +808,109 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         }
         __syncwarp();
         // ---------------- phase 2: det A per job ----------------
-        const int jc = g;                 // this lane's job: trajectory t, step step0 + jc + 1
+        const int jc = g;                 // phases 3-4: this lane's step of its trajectory (job t * C + jc)
+        const int jb = t * C + jc;
         const bool jvalid = jc < cnt;
         double argA = 0.0;                // arg det A of this lane's job (principal value)
-        double lnAbsA = 0.0;              // ln |det A| (mixed path always; FP64 path for the HK summand)
-        double2 detA = make_double2(1.0, 0.0);   // FP64 path: det A itself
-        if (ln >= JOBS) {
-            // no job for this lane (wide groups): the in-place elimination must not touch a job's storage
-        } else if constexpr (sizeof(Real) == 4) {
-            // Mixed path: the entries of A are FP32 (formed from the FP32 monodromy), so the
-            // complex LU with partial pivoting runs in FP32, in place on this job's column of
-            // the shared array (no per-lane matrix in registers).  ln|det A| = sum ln|pivot|
-            // and the unit phasor prod pivot/|pivot| (sign flipped per row exchange) keep the
-            // result free of FP32 overflow whatever the size of the entries.
-            auto at = [&](int e) -> R2 & { return sh.A[e][jswz<JOBS>(e, ln)]; };
-            float ur = 1.0f, ui = 0.0f, lsum = 0.0f;
+        double2 detA = make_double2(1.0, 0.0);
+        if constexpr (sizeof(Real) == 4) {
+            // Mixed path: the entries of A are FP32 (formed from the FP32 monodromy) and the
+            // elimination runs in double-FP32 on the FP32 pipe, so det A carries FP64-class
+            // accuracy for those entries.  LPJ lanes share a job: the rows still to be
+            // eliminated are dealt out over them through a permutation (4 bits per row,
+            // rows k.. of the permutation are the active ones), the pivot is an arg-max of
+            // |a_ik|^2 over the job's lanes, and det A is the product of the pivots in FP64,
+            // its sign flipped per exchange of the permutation.
+            constexpr int LPJ = 32 / JOBS;
+            static_assert(LPJ * JOBS == 32, "jobs must tile the warp");
+            const int job = ln / LPJ, r = ln % LPJ;
+            auto at = [&](int e) -> float4 & { return sh.A[e][jswz<JOBS>(e, job)]; };
+            unsigned long long perm = 0ull;
+#pragma unroll
+            for (int i = 0; i < F; ++i) perm |= (unsigned long long)i << (4 * i);
+            auto prow = [&](int pos) -> int { return (int)((perm >> (4 * pos)) & 15ull); };
+            double dr = 1.0, di = 0.0;
 #pragma unroll
             for (int k = 0; k < F; ++k) {
-                int piv = k;
-                float best;
-                {
-                    const R2 v = at(k * F + k);
-                    best = fmaf(v.x, v.x, v.y * v.y);
-                }
+                // pivot: the largest |a_ik|^2 (leading words) over the active rows
+                float best = -1.0f;
+                int bpos = k;
 #pragma unroll
-                for (int i = k + 1; i < F; ++i) {
-                    const R2 v = at(i * F + k);
-                    const float m = fmaf(v.x, v.x, v.y * v.y);
-                    if (m > best) { best = m; piv = i; }
-                }
-                R2 prow[F];
-#pragma unroll
-                for (int cc = k; cc < F; ++cc) prow[cc] = at(piv * F + cc);
-                if (piv != k) {
-#pragma unroll
-                    for (int cc = k; cc < F; ++cc) at(piv * F + cc) = at(k * F + cc);
-                    ur = -ur;
-                    ui = -ui;
-                }
-                const R2 pk = prow[k];
-                const float m = fmaf(pk.x, pk.x, pk.y * pk.y);
-                lsum += __logf(m);
-                const float rn = rsqrtf(m);
-                const float nr = fmaf(ur, pk.x * rn, -ui * (pk.y * rn));
-                const float ni = fmaf(ur, pk.y * rn, ui * (pk.x * rn));
-                ur = nr;
-                ui = ni;
-                const float rm = __frcp_rn(m);
-                const float ir = pk.x * rm, ii = -pk.y * rm;   // 1 / pivot
-#pragma unroll
-                for (int i = k + 1; i < F; ++i) {
-                    const R2 aik = at(i * F + k);
-                    const float lr = fmaf(aik.x, ir, -aik.y * ii);
-                    const float li = fmaf(aik.x, ii, aik.y * ir);
-#pragma unroll
-                    for (int cc = k + 1; cc < F; ++cc) {
-                        R2 a = at(i * F + cc);
-                        a.x = fmaf(-lr, prow[cc].x, fmaf(li, prow[cc].y, a.x));
-                        a.y = fmaf(-lr, prow[cc].y, fmaf(-li, prow[cc].x, a.y));
-                        at(i * F + cc) = a;
+                for (int s0 = k; s0 < F; s0 += LPJ) {
+                    const int pos = s0 + r;
+                    if (pos < F) {
+                        const float4 v = at(prow(pos) * F + k);
+                        const float m = fmaf(v.x, v.x, v.z * v.z);
+                        if (m > best) { best = m; bpos = pos; }
                     }
                 }
+#pragma unroll
+                for (int o = 1; o < LPJ; o <<= 1) {
+                    const float ob = __shfl_xor_sync(FULL, best, o);
+                    const int op = __shfl_xor_sync(FULL, bpos, o);
+                    if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; }
+                }
+                if (bpos != k) {
+                    const unsigned long long a = (perm >> (4 * k)) & 15ull, b = (perm >> (4 * bpos)) & 15ull;
+                    perm ^= ((a ^ b) << (4 * k)) | ((a ^ b) << (4 * bpos));
+                    dr = -dr;
+                    di = -di;
+                }
+                const int pr = prow(k);
+                const float4 pk4 = at(pr * F + k);
+                const ff pre = {pk4.x, pk4.y}, pim = {pk4.z, pk4.w};
+                {
+                    const double kr = (double)pre.hi + (double)pre.lo, ki = (double)pim.hi + (double)pim.lo;
+                    const double nr = fma(dr, kr, -di * ki), ni = fma(dr, ki, di * kr);
+                    dr = nr;
+                    di = ni;
+                }
+                // 1 / pivot = conj(pivot) / |pivot|^2
+                const ff m2 = ff_add(ff_mul(pre, pre), ff_mul(pim, pim));
+                const ff rm = ff_recip(m2);
+                const ff ir = ff_mul(pre, rm);
+                const ff nii = ff_mul(pim, rm);
+                const ff ii = {-nii.hi, -nii.lo};
+#pragma unroll
+                for (int s0 = k + 1; s0 < F; s0 += LPJ) {
+                    const int pos = s0 + r;
+                    if (pos < F) {
+                        const int row = prow(pos);
+                        const float4 aik = at(row * F + k);
+                        const ff ar = {aik.x, aik.y}, ai = {aik.z, aik.w};
+                        // l = a_ik / pivot
+                        const ff zero = {0.0f, 0.0f};
+                        const ff lr = ff_sub_mul_add_mul(zero, ai, ii, ar, ir);                       // ar ir - ai ii
+                        const ff li = ff_sub_mul_add_mul(zero, {-ar.hi, -ar.lo}, ii, ai, ir);         // ar ii + ai ir
+#pragma unroll
+                        for (int cc = k + 1; cc < F; ++cc) {
+                            const float4 pv = at(pr * F + cc);
+                            const ff pre_c = {pv.x, pv.y}, pim_c = {pv.z, pv.w};
+                            float4 &dst = at(row * F + cc);
+                            const float4 av = dst;
+                            // a -= l p: re = a.re - lr pr + li pi, im = a.im - lr pi - li pr
+                            const ff nre = ff_sub_mul_add_mul({av.x, av.y}, lr, pre_c, li, pim_c);
+                            const ff nim = ff_sub_mul_add_mul({av.z, av.w}, lr, pim_c, {-li.hi, -li.lo}, pre_c);
+                            dst = make_float4(nre.hi, nre.lo, nim.hi, nim.lo);
+                        }
+                    }
+                }
+                if (LPJ > 1) __syncwarp();   // rows updated by the job's other lanes feed the next pivot
             }
-            argA = (double)atan2f(ui, ur);
-            lnAbsA = 0.5 * (double)lsum;
+            if (r == 0) {
+                sh.argj[job] = atan2(di, dr);
+                sh.detAj[job] = make_double2(dr, di);
+                if (A.amplitude == SCIVR_AMP_HK) sh.lnA[job] = 0.5 * log(hypot(dr, di));
+            }
+            __syncwarp();
+            if (jvalid) {
+                argA = sh.argj[jb];
+                detA = sh.detAj[jb];
+            }
+        } else if (ln >= JOBS) {
+            // no job for this lane (wide groups): the in-place elimination must not touch a job's storage
         } else {
-            // FP64 path: the same in-place elimination in FP64, with det A as the product of
+            // FP64 path: in-place elimination in FP64, one lane per job, det A as the product of
             // the pivots (no range concern in FP64)
             auto at = [&](int e) -> R2 & { return sh.A[e][jswz<JOBS>(e, ln)]; };
             double dr = 1.0, di = 0.0;
@@ -659,10 +959,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             }
             detA = make_double2(dr, di);
             argA = atan2(di, dr);
-            if (A.amplitude == SCIVR_AMP_HK) lnAbsA = log(hypot(dr, di));
+            if (A.amplitude == SCIVR_AMP_HK) sh.lnA[ln] = 0.5 * log(hypot(dr, di));
         }
-        // Herman-Kluk summand: log |det A|^{1/2}, the only part of det A phase 4 needs
-        if (A.amplitude == SCIVR_AMP_HK && ln < JOBS) sh.lnA[ln] = 0.5 * lnAbsA;
         // ---------------- phase 3: continuous phase (segmented scan) ----------------
         const double arg = argA;
         double arg_prev = __shfl_up_sync(FULL, arg, 1, G);
@@ -676,19 +974,15 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             if (g >= o) inc += v;
         }
         const double theta = theta_last + inc;
-        const int lastlane = t * C + cnt - 1;
+        const int lastlane = base + cnt - 1;     // lane of the chunk's last step of this trajectory
         theta_last = __shfl_sync(FULL, theta, lastlane);
         arg_last = __shfl_sync(FULL, arg, lastlane);
-        if constexpr (sizeof(Real) == 4) {
-            lnAbs_last = __shfl_sync(FULL, lnAbsA, lastlane);
-        } else {
-            detA_last.x = __shfl_sync(FULL, detA.x, lastlane);
-            detA_last.y = __shfl_sync(FULL, detA.y, lastlane);
-        }
+        detA_last.x = __shfl_sync(FULL, detA.x, lastlane);
+        detA_last.y = __shfl_sync(FULL, detA.y, lastlane);
         if (!isfinite(theta_last)) good = false;
         // ---------------- phase 4: amplitudes (job-parallel) ----------------
         if (jvalid && active) {
-            const double S = sh.Sj[ln];
+            const double S = sh.Sj[jb];
             for (int x = 0; x < A.n_chi; ++x) {
                 if constexpr (sizeof(Real) == 4) {
                     // the overlap's exponent and phase are O(1)-O(10) in size: FP32 from the FP32
@@ -697,7 +991,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     float rf = 0.0f, imf = 0.0f;
 #pragma unroll
                     for (int a = 0; a < F; ++a) {
-                        const float pa = sh.pj[a][jswz<JOBS>(a, ln)], qa = sh.qj[a][jswz<JOBS>(a, ln)];
+                        const float pa = sh.pj[a][jswz<JOBS>(a, jb)], qa = sh.qj[a][jswz<JOBS>(a, jb)];
                         const float dq = cc.q_eqf[x][a] - qa, dp = cc.p_eqf[x][a] - pa;
                         rf = fmaf(-cc.qwf[a] * dq, dq, rf);
                         rf = fmaf(-cc.pwf[a] * dp, dp, rf);
@@ -708,7 +1002,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         // Herman-Kluk summand: |det A|^{1/2} and the division by the initial
                         // overlap times the sampling weight
                         const double2 o = sh.ov0[x][t];
-                        rf = (float)((double)rf - o.x + sh.lnA[ln]);
+                        rf = (float)((double)rf - o.x + sh.lnA[jb]);
                         ph -= o.y;
                     }
                     const double red = fma(-kTwoPi, rint(ph * kInvTwoPi), ph);   // FP64 reduction to [-pi, pi]
@@ -721,7 +1015,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     double re = 0.0, im = 0.0;
 #pragma unroll
                     for (int a = 0; a < F; ++a) {
-                        const double pa = sh.pj[a][jswz<JOBS>(a, ln)], qa = sh.qj[a][jswz<JOBS>(a, ln)];
+                        const double pa = sh.pj[a][jswz<JOBS>(a, jb)], qa = sh.qj[a][jswz<JOBS>(a, jb)];
                         const double dq = cc.q_eq[x][a] - qa, dp = cc.p_eq[x][a] - pa;
                         re = fma(-cc.qw[a] * dq, dq, re);
                         re = fma(-cc.pw[a] * dp, dp, re);
@@ -730,7 +1024,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     double ph = im + S + 0.5 * theta;
                     if (A.amplitude == SCIVR_AMP_HK) {
                         const double2 o = sh.ov0[x][t];
-                        re = re - o.x + sh.lnA[ln];
+                        re = re - o.x + sh.lnA[jb];
                         ph -= o.y;
                     }
                     double sn, cs;
@@ -756,21 +1050,19 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         if (fo.theta) fo.theta[jl] = theta_last;
         if (fo.detM) fo.detM[jl] = detM_last;
         if (fo.stab) fo.stab[jl] = (double)stab;
-        if constexpr (sizeof(Real) == 4) {
-            if (fo.detA) {
-                const double r = exp(lnAbs_last);
-                fo.detA[2 * jl] = r * cos(arg_last);
-                fo.detA[2 * jl + 1] = r * sin(arg_last);
-            }
-        } else {
-            if (fo.detA) { fo.detA[2 * jl] = detA_last.x; fo.detA[2 * jl + 1] = detA_last.y; }
-        }
+        if (fo.detA) { fo.detA[2 * jl] = detA_last.x; fo.detA[2 * jl + 1] = detA_last.y; }
     }
-    if (fo.M && g < N2) {
+    if (fo.M) {
 #pragma unroll
-        for (int a = 0; a < F; ++a) {
-            fo.M[jl * N2 * N2 + a * N2 + g] = (double)Mp[a];
-            fo.M[jl * N2 * N2 + (F + a) * N2 + g] = (double)Mq[a];
+        for (int s = 0; s < NCOL; ++s) {
+            const int col = g + s * G;
+            if (col < N2) {
+#pragma unroll
+                for (int a = 0; a < F; ++a) {
+                    fo.M[jl * N2 * N2 + a * N2 + col] = (double)Mp[s][a];
+                    fo.M[jl * N2 * N2 + (F + a) * N2 + col] = (double)Mq[s][a];
+                }
+            }
         }
     }
     }
@@ -778,7 +1070,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 }
 
 template <int F, int G, typename Real, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, lg_min_ctas<F>()) k_propagate_lg(const PropLaunch L)
+__global__ void __launch_bounds__(32 * WARPS, lg_min_ctas<F, G, Real>()) k_propagate_lg(const PropLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     lg_body<F, G, Real, WARPS>(L, blockIdx.x, smem_raw);
@@ -788,7 +1080,7 @@ __global__ void __launch_bounds__(32 * WARPS, lg_min_ctas<F>()) k_propagate_lg(c
 // list sorted by decreasing cost until it is exhausted.  items: device array
 // of per-molecule launches (all of this F); work: (item, tile) pairs.
 template <int F, int G, typename Real, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, lg_min_ctas<F>()) k_propagate_lg_batch(const PropLaunch *__restrict__ items,
+__global__ void __launch_bounds__(32 * WARPS, lg_min_ctas<F, G, Real>()) k_propagate_lg_batch(const PropLaunch *__restrict__ items,
                                                                        const int2 *__restrict__ work,
                                                                        int n_work, int *__restrict__ counter)
 {
@@ -863,14 +1155,15 @@ template <int F> constexpr int group_lanes() { return 2 * F <= 8 ? 8 : (2 * F <=
 
 template <int F> cudaError_t launch_group_mixed(const PropLaunch &L, cudaStream_t s)
 {
-    return launch_lg<F, group_lanes<F>(), float, lg::lg_warps<F, group_lanes<F>()>()>(L, s);
+    constexpr int G = mixed_group_lanes(F);
+    return launch_lg<F, G, float, lg::lg_warps<F, G>()>(L, s);
 }
 
 template <int F>
 cudaError_t launch_group_batch_mixed_F(int warps, const PropLaunch *items, const int2 *work, int n_work,
                                       int *counter, int n_sm, cudaStream_t s)
 {
-    constexpr int G = group_lanes<F>();
+    constexpr int G = mixed_group_lanes(F);
     if constexpr (G == 32 && F > 9) {
         constexpr int W = lg::lg_warps<F, G>();
         if (warps == W) return launch_lg_batch<F, G, float, W>(items, work, n_work, counter, n_sm, s);

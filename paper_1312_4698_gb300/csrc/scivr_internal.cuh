@@ -38,6 +38,9 @@ struct PesDev {
     const double *T3;                // [F][P]
     const double *T4;                // [P][P]
     const float *T3f, *T4f;          // FP32 copies for the mixed-precision path
+    int P4;                          // P rounded up to a multiple of 4
+    const float *T3p, *T4p;          // FP32 copies [F][P4], [P][P4] with rows padded to whole
+                                     // 16-byte vectors (read from global memory above F = 16)
     const float *omega_f, *D_f, *a_f;   // FP32 copies of the diagonal parameters
     MlpWeightsDev mlp;                  // mlp.H == 0: analytic surface only
 };
@@ -137,6 +140,11 @@ int cuda_error(cudaError_t e, const char *where);
 cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, const int2 *work, int n_work,
                                      int *counter, int n_sm, cudaStream_t s);
 int batch_warp_candidates(int F, int *out);   // returns the count (<= 2)
+
+// Lanes per trajectory of the mixed-precision lane-group kernels: every mode and at
+// most two monodromy columns per lane -- 8 lanes up to F = 4, 16 up to F = 9 (at F = 9
+// two lanes hold a second column, so a warp carries two trajectories), 32 above.
+__host__ __device__ constexpr int mixed_group_lanes(int F) { return 2 * F <= 8 ? 8 : (F <= 9 ? 16 : 32); }
 
 // log <chi_x|p0_j, q0_j> (Eq. coherent_state with unit-norm states).
 template <int F>
