@@ -261,10 +261,10 @@ def reference_arm(args):
 
 
 def batch_arm(args):
-    """48 molecules (F cycling over the recipe's classes 3, 6, 9, 12, 15 -- F = 24 is not
-    built; n_traj log-uniform in [512, 32768]; steps uniform in [2000, 8000]) sampled,
-    propagated in one persistent launch per F-class and transformed, all captured in
-    one CUDA graph.  One batch takes ~25 s on a GB300: time it with --steps 2."""
+    """48 molecules (F cycling over the recipe's classes 3, 6, 9, 12, 15, 24; n_traj
+    log-uniform in [512, 32768]; steps uniform in [2000, 8000]) sampled, propagated in one
+    persistent launch per F-class and transformed, all captured in one CUDA graph.  One
+    batch takes tens of seconds on a GB300: time it with --steps 2."""
     import torch
     from paper_1312_4698_gb300 import scivr
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -274,7 +274,7 @@ def batch_arm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    mols = wl.batch_molecules(args.n_mol, seed=1000 * rank, Fs=(3, 6, 9, 12, 15))
+    mols = wl.batch_molecules(args.n_mol, seed=1000 * rank, Fs=(3, 6, 9, 12, 15, 24))
     prec = PRECISIONS[args.precision]
     ftm = FT_MODES[args.ft]
     entries = []
@@ -342,8 +342,7 @@ def batch_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision] + ("" if ftm == 0 else f" + {args.ft} tensor FT"),
         "data": "synthetic",
-        "config": {"workload": f"batch of {len(mols)} molecules, F cycling over 3/6/9/12/15 (F = 24 of the "
-                               f"batched recipe is not built), n_traj log-uniform "
+        "config": {"workload": f"batch of {len(mols)} molecules, F cycling over 3/6/9/12/15/24, n_traj log-uniform "
                                f"[512, 32768], steps uniform [2000, 8000], 4000 energies; sampling, "
                                f"propagation (one persistent launch per F) and spectra in one CUDA graph",
                    "global_batch": world * sum(w8.n_traj for w8 in mols),
@@ -620,8 +619,8 @@ def surrogate_arm(args):
 def speedup_arm(args):
     """F uncoupled Morse oscillators (the speed-up-versus-F comparison of Sec. IV):
     GPU trajectory-steps/s of the FP64 propagation (F = 1..9, where it is built) and of
-    the mixed propagation (F = 1..16), each with its Fourier step, against the oracle on
-    one host core and on all host cores.  F = 17..24 are not built on the GPU."""
+    the mixed propagation (F = 1..24), each with its Fourier step, against the oracle on
+    one host core and on all host cores."""
     import torch
     from paper_1312_4698_gb300 import scivr
     import oracle
@@ -637,7 +636,7 @@ def speedup_arm(args):
     rows = []
     scivr.launch_count(reset=True)
     with ClockSampler(gpu_selector(0)) as clk:
-        for F in range(1, 17):
+        for F in range(1, 25):
             w8 = wl.uncoupled_morse(F, n_traj=n, n_steps=steps, n_E=2000)
             pes = scivr.scivr_create_pes(w8.pes)
             bufs = scivr.alloc_buffers(w8)
@@ -687,9 +686,9 @@ def speedup_arm(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": n * steps / rows[-1]["gpu_mixed"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 and f32+f64", "data": "synthetic",
-        "config": {"workload": f"uncoupled Morse oscillators F = 1..16 (omega ~ U[1100, 3000] cm^-1, D ~ U[0.15, "
+        "config": {"workload": f"uncoupled Morse oscillators F = 1..24 (omega ~ U[1100, 3000] cm^-1, D ~ U[0.15, "
                                f"0.25]), {n} trajectories, {steps} steps, 2000 energies; FP64 GPU path F <= 9; "
-                               f"value = mixed path at F = 16",
+                               f"value = mixed path at F = 24",
                    "l2": f"flushed between runs ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "cpu_cores": all_threads},
         "sweep": rows,

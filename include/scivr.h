@@ -49,7 +49,8 @@ enum { SCIVR_DIAG_HARMONIC = 0,   /* omega_i^2 q_i^2 / 2 */
        SCIVR_DIAG_MORSE = 1 };    /* D_i (1 - exp(-a_i q_i))^2 */
 
 /* Potential kinds. */
-enum { SCIVR_PES_POLY = 0 };      /* diagonal + cubic + quartic coupling monomials */
+enum { SCIVR_PES_POLY = 0,        /* diagonal + cubic + quartic coupling monomials */
+       SCIVR_PES_CART3 = 1 };     /* Cartesian triatomic surface in its normal modes (F = 3) */
 
 /* Arithmetic of the propagation. */
 enum { SCIVR_FP64 = 0,            /* everything in IEEE double */
@@ -132,8 +133,59 @@ typedef struct {
  * SCIVR_ENOMEM, SCIVR_ECUDA. */
 int scivr_create_pes(const scivr_pes_desc *d, scivr_pes *out);
 
-/* Release a potential created by scivr_create_pes (synchronises the device
- * so that no launch still reads it).  NULL is accepted. */
+/* ------------------------------------------------------------------------ */
+/* Cartesian surfaces and normal modes                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Cartesian surface of a bent triatomic, atoms 0 and 2 bonded to the central atom 1
+ * (Sec. III.A: the molecular surfaces are functions of the Cartesian coordinates and
+ * the host converts them to mass-weighted normal modes before propagation):
+ *   V(x) = sum_b D[b] (1 - exp(-a[b] (r_b - re[b])))^2 + (k_bend / 2) (cos theta - cos theta_e)^2,
+ * r_0 = |x0 - x1|, r_1 = |x2 - x1|, theta the angle 0-1-2.  x: [9] bohr, atom-major.
+ * Units: hartree, bohr, electron masses. */
+typedef struct {
+    double mass[3];         /* atom masses (> 0) */
+    double D[2];            /* Morse depths of bonds 0-1 and 2-1 (> 0) */
+    double a[2];            /* Morse range parameters (> 0) */
+    double re[2];           /* equilibrium bond lengths (> 0) */
+    double k_bend;          /* bend force constant (> 0) */
+    double theta_e;         /* equilibrium angle, radians, in (0, pi) */
+} scivr_cart_triatomic;
+
+/* Normal modes of a triatomic surface (Sec. III.A, the conversion matrix of the host
+ * driver): the equilibrium geometry x_eq (atom 1 at the origin, the molecule in the
+ * xy plane, the bisector along +y), the Hessian there, its mass-weighted form
+ * M^{-1/2} H M^{-1/2} diagonalised by Jacobi rotations, and the three vibrations (the
+ * largest eigenvalues; translations and rotations have eigenvalue zero) in increasing
+ * frequency.  Outputs (host memory, caller-owned; any may be NULL):
+ *   omega [3]: harmonic frequencies sqrt(eigenvalue), hartree;
+ *   x_eq [9];
+ *   Lm [9][3]: x = x_eq + Lm q, Lm[i][m] = L[i][m] / sqrt(mass of the atom of coordinate i)
+ *              with L the orthonormal mass-weighted eigenvectors, each signed so that its
+ *              first component of magnitude above 1e-3 is positive.
+ * Host only (no device work).  Errors: SCIVR_EINVAL (NULL c, non-positive or non-finite
+ * parameters, theta_e outside (0, pi)). */
+int scivr_normal_modes(const scivr_cart_triatomic *c, double *omega, double *x_eq, double *Lm);
+
+/* Conversions between n Cartesian geometries x [n][9] and normal coordinates q [n][3]
+ * of the triatomic: x = x_eq + Lm q and q = Lm^T M (x - x_eq), M the diagonal of atom
+ * masses (the projection onto the vibrations: Lm^T M Lm = I; translations and
+ * rotations of x are dropped).  Host arrays, caller-owned.  Errors: as
+ * scivr_normal_modes, SCIVR_EINVAL for n < 0 or NULL arrays with n > 0. */
+int scivr_normal_to_cartesian(const scivr_cart_triatomic *c, int64_t n, const double *q, double *x);
+int scivr_cartesian_to_normal(const scivr_cart_triatomic *c, int64_t n, const double *x, double *q);
+
+/* Potential whose V(q), gradient and Hessian are those of the Cartesian surface at
+ * x = x_eq + Lm q (the normal modes of scivr_normal_modes; F = 3): the propagation
+ * kernels evaluate the surface through the bond and angle coordinates and the chain
+ * rule at every force stage.  Propagation: SCIVR_FP64 with the thread-per-trajectory
+ * schedule (SCIVR_KERNEL_AUTO chooses it); other precisions or schedules return
+ * SCIVR_EUNSUPPORTED.  Allocates device memory on the current device.
+ * Errors: as scivr_normal_modes, SCIVR_ENOMEM, SCIVR_ECUDA. */
+int scivr_create_pes_cartesian(const scivr_cart_triatomic *c, scivr_pes *out);
+
+/* Release a potential created by scivr_create_pes or scivr_create_pes_cartesian
+ * (synchronises the device so that no launch still reads it).  NULL is accepted. */
 int scivr_destroy_pes(scivr_pes pes);
 
 /* Number of modes of a potential (0 for NULL). */

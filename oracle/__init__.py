@@ -73,7 +73,13 @@ class _Pes(C.Structure):
                 ("omega", C.c_void_p), ("D", C.c_void_p), ("a", C.c_void_p),
                 ("n3", C.c_int32), ("idx3", C.c_void_p), ("c3", C.c_void_p),
                 ("n4", C.c_int32), ("idx4", C.c_void_p), ("c4", C.c_void_p),
-                ("mlp", C.c_void_p)]
+                ("mlp", C.c_void_p), ("cart", C.c_void_p)]
+
+
+class _Cart(C.Structure):
+    _fields_ = [("mass", C.c_double * 3), ("D", C.c_double * 2), ("a", C.c_double * 2),
+                ("re", C.c_double * 2), ("k_bend", C.c_double), ("theta_e", C.c_double),
+                ("x_eq", C.c_double * 9), ("Lm", C.c_double * 27)]
 
 
 class _Prop(C.Structure):
@@ -103,6 +109,10 @@ def _load():
             vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
             lib.or_pes_eval.restype = d
             lib.or_pes_eval.argtypes = [vp, vp, vp, vp]
+            lib.or_cart_eval.restype = d
+            lib.or_cart_eval.argtypes = [vp, vp, vp, vp]
+            lib.or_normal_modes.restype = d
+            lib.or_normal_modes.argtypes = [vp, vp]
             lib.or_det_real.restype = d
             lib.or_det_real.argtypes = [C.c_int, vp]
             lib.or_det_complex.restype = _Cplx
@@ -151,10 +161,54 @@ class Mlp:
                       _p(b3), _p(w4), float(m.b4))
 
 
+class Cart:
+    """The oracle's Cartesian triatomic surface with its own normal-mode analysis
+    (equilibrium geometry, Jacobi diagonalisation of the mass-weighted Hessian)."""
+
+    def __init__(self, c):
+        self.s = _Cart()
+        self.s.mass[:] = [float(v) for v in c.mass]
+        self.s.D[:] = [float(v) for v in c.D]
+        self.s.a[:] = [float(v) for v in c.a]
+        self.s.re[:] = [float(v) for v in c.re]
+        self.s.k_bend = float(c.k_bend)
+        self.s.theta_e = float(c.theta_e)
+        om = np.zeros(3)
+        self.rigid = float(_load().or_normal_modes(C.byref(self.s), _p(om)))
+        self.omega = om
+        self.x_eq = np.array(self.s.x_eq[:])
+        self.Lm = np.array(self.s.Lm[:]).reshape(9, 3)
+
+
+def normal_modes(c):
+    """omega [3] (increasing), x_eq [9], Lm [9, 3] with x = x_eq + Lm q, and the largest
+    rigid-body eigenvalue magnitude of the mass-weighted Hessian."""
+    k = Cart(c)
+    return k.omega, k.x_eq, k.Lm, k.rigid
+
+
+def cart_eval(c, x):
+    """V, gradient [9] and Hessian [9, 9] of the Cartesian surface at x [9]."""
+    k = Cart(c)
+    g = np.zeros(9)
+    H = np.zeros((9, 9))
+    V = _load().or_cart_eval(C.byref(k.s), _p(_f64(x)), _p(g), _p(H))
+    return float(V), g, H
+
+
 class Pes:
     """Owns contiguous copies of a descriptor's arrays and the C struct pointing at them."""
 
     def __init__(self, desc):
+        cart = getattr(desc, "cart", None)
+        if cart is not None:
+            self.F = 3
+            self._cart = Cart(cart)
+            z = np.zeros(3)
+            self._keep = [z]
+            self.s = _Pes(3, 0, _p(z), _p(z), _p(z), 0, None, None, 0, None, None, None,
+                          C.addressof(self._cart.s))
+            return
         self.F = int(desc.F)
         self._keep = [_f64(desc.omega), _f64(desc.D), _f64(desc.a),
                       np.ascontiguousarray(desc.idx3, dtype=np.int32), _f64(desc.c3),

@@ -75,7 +75,192 @@ typedef struct {
     const int32_t *idx4;      /* [n4 * 4] */
     const double *c4;         /* [n4] */
     const or_mlp *mlp;        /* NULL: no learned residual */
+    const struct or_cart_s *cart;   /* non-NULL: a Cartesian triatomic surface in its normal modes (F = 3) */
 } or_pes;
+
+/* ------------------------------------------------------------------------ */
+/* Cartesian triatomic surface and its normal modes (Sec. III.A: the molecular */
+/* surfaces are functions of Cartesian coordinates; the host driver builds the */
+/* normal modes from the mass-weighted Hessian at the equilibrium geometry and */
+/* converts between the two sets of coordinates).                             */
+/* ------------------------------------------------------------------------ */
+
+/* Atoms 0 and 2 bonded to the central atom 1.  V(x) = sum_b D_b (1 - e^{-a_b (r_b - re_b)})^2
+ * + k/2 (cos theta - cos theta_e)^2, r_0 = |x0 - x1|, r_1 = |x2 - x1|, theta the angle 0-1-2.
+ * x_eq, Lm fill the normal-mode map x = x_eq + Lm q (Lm[i][m] = L[i][m] / sqrt(mass of the
+ * atom of coordinate i), L the orthonormal mass-weighted eigenvectors). */
+typedef struct or_cart_s {
+    double mass[3];
+    double D[2], a[2], re[2];
+    double k_bend, theta_e;
+    double x_eq[9];
+    double Lm[27];            /* [9][3] */
+} or_cart;
+
+/* V, gradient [9] and Hessian [9][9] of the Cartesian surface.  Derivatives written from
+ * the dot products s = u.v, P = (u.u)(v.v) (u = x0 - x1, v = x2 - x1, cos theta = s P^{-1/2})
+ * and r = (w.w)^{1/2} for each bond vector w: every intermediate is a polynomial in x or a
+ * power of one, differentiated by the product and chain rules. */
+double or_cart_eval(const or_cart *c, const double *x, double *g, double *H)
+{
+    double V = 0.0;
+    if (g) memset(g, 0, 9 * sizeof(double));
+    if (H) memset(H, 0, 81 * sizeof(double));
+    /* bonds: atom pair (0, 1) and (2, 1) */
+    for (int b = 0; b < 2; ++b) {
+        const int ia = b == 0 ? 0 : 2, ib = 1;
+        double w[3], ww = 0.0;
+        for (int d = 0; d < 3; ++d) { w[d] = x[3 * ia + d] - x[3 * ib + d]; ww += w[d] * w[d]; }
+        const double r = sqrt(ww);
+        const double e = exp(-c->a[b] * (r - c->re[b]));
+        V += c->D[b] * (1.0 - e) * (1.0 - e);
+        const double f1 = 2.0 * c->D[b] * c->a[b] * e * (1.0 - e);                  /* dV/dr */
+        const double f2 = 2.0 * c->D[b] * c->a[b] * c->a[b] * e * (2.0 * e - 1.0);  /* d2V/dr2 */
+        /* dr/dw = w / r ; d2r/dw dw^T = (I - w w^T / r^2) / r */
+        for (int d = 0; d < 3; ++d) {
+            const double gd = f1 * w[d] / r;
+            if (g) { g[3 * ia + d] += gd; g[3 * ib + d] -= gd; }
+        }
+        if (H)
+            for (int d = 0; d < 3; ++d)
+                for (int f = 0; f < 3; ++f) {
+                    const double hw = f2 * w[d] * w[f] / ww + f1 * ((d == f ? 1.0 : 0.0) - w[d] * w[f] / ww) / r;
+                    H[(3 * ia + d) * 9 + 3 * ia + f] += hw;
+                    H[(3 * ib + d) * 9 + 3 * ib + f] += hw;
+                    H[(3 * ia + d) * 9 + 3 * ib + f] -= hw;
+                    H[(3 * ib + d) * 9 + 3 * ia + f] -= hw;
+                }
+    }
+    /* bend: y = (u, v) in R^6, cos = s P^{-1/2} */
+    {
+        double y[6];
+        for (int d = 0; d < 3; ++d) { y[d] = x[d] - x[3 + d]; y[3 + d] = x[6 + d] - x[3 + d]; }
+        const double *u = y, *v = y + 3;
+        double uu = 0.0, vv = 0.0, s = 0.0;
+        for (int d = 0; d < 3; ++d) { uu += u[d] * u[d]; vv += v[d] * v[d]; s += u[d] * v[d]; }
+        const double P = uu * vv;
+        const double Pm12 = 1.0 / sqrt(P);
+        const double cth = s * Pm12;
+        const double dc = cth - cos(c->theta_e);
+        V += 0.5 * c->k_bend * dc * dc;
+        /* ds/dy = (v, u); dP/dy = (2 u vv, 2 v uu) */
+        double ds[6], dP[6];
+        for (int d = 0; d < 3; ++d) {
+            ds[d] = v[d]; ds[3 + d] = u[d];
+            dP[d] = 2.0 * u[d] * vv; dP[3 + d] = 2.0 * v[d] * uu;
+        }
+        /* dcos = ds P^{-1/2} - (1/2) s P^{-3/2} dP */
+        double dcy[6];
+        for (int i = 0; i < 6; ++i) dcy[i] = ds[i] * Pm12 - 0.5 * s * Pm12 * Pm12 * Pm12 * dP[i];
+        double Hy[36];
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                /* d2s: 1 where one index is in u and the other the same component in v */
+                const double d2s = (i % 3 == j % 3 && (i < 3) != (j < 3)) ? 1.0 : 0.0;
+                /* d2P: d/dy_j of (2 u vv, 2 v uu) */
+                double d2P;
+                if (i < 3 && j < 3) d2P = (i == j ? 2.0 * vv : 0.0);
+                else if (i >= 3 && j >= 3) d2P = (i == j ? 2.0 * uu : 0.0);
+                else if (i < 3) d2P = 4.0 * u[i] * v[j - 3];
+                else d2P = 4.0 * v[i - 3] * u[j];
+                const double P32 = Pm12 * Pm12 * Pm12, P52 = P32 * Pm12 * Pm12;
+                const double d2c = d2s * Pm12 - 0.5 * P32 * (ds[i] * dP[j] + ds[j] * dP[i])
+                                   - 0.5 * s * P32 * d2P + 0.75 * s * P52 * dP[i] * dP[j];
+                Hy[i * 6 + j] = c->k_bend * (dcy[i] * dcy[j] + dc * d2c);
+            }
+        /* y = (x0 - x1, x2 - x1): dy/dx maps atom 0 -> u, atom 2 -> v, atom 1 -> -(u + v) */
+        for (int i = 0; i < 6; ++i) {
+            const double gi = c->k_bend * dc * dcy[i];
+            const int atom = i < 3 ? 0 : 2, d = i % 3;
+            if (g) { g[3 * atom + d] += gi; g[3 + d] -= gi; }
+        }
+        if (H)
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                    const int ai = i < 3 ? 0 : 2, di = i % 3, aj = j < 3 ? 0 : 2, dj = j % 3;
+                    const double h = Hy[i * 6 + j];
+                    H[(3 * ai + di) * 9 + 3 * aj + dj] += h;
+                    H[(3 * ai + di) * 9 + 3 + dj] -= h;
+                    H[(3 + di) * 9 + 3 * aj + dj] -= h;
+                    H[(3 + di) * 9 + 3 + dj] += h;
+                }
+    }
+    return V;
+}
+
+/* Equilibrium geometry (atom 1 at the origin, the molecule in the xy plane, the
+ * bisector along y) and the normal modes: the eigenvectors of the mass-weighted
+ * Hessian M^{-1/2} H M^{-1/2} by cyclic Jacobi rotations; the three largest
+ * eigenvalues are omega^2 of the vibrations (the other six, translations and
+ * rotations, vanish at the equilibrium).  Modes in increasing frequency; each
+ * eigenvector's sign makes its first component of magnitude above 1e-3 positive.
+ * Fills c->x_eq, c->Lm, omega[3]; returns the largest |eigenvalue| among the six
+ * rigid-body modes (zero up to rounding). */
+double or_normal_modes(or_cart *c, double *omega)
+{
+    const double h = 0.5 * c->theta_e;
+    memset(c->x_eq, 0, sizeof(c->x_eq));
+    c->x_eq[0] = -c->re[0] * sin(h); c->x_eq[1] = c->re[0] * cos(h);
+    c->x_eq[6] = c->re[1] * sin(h);  c->x_eq[7] = c->re[1] * cos(h);
+    double Hx[81], A[81], Vm[81];
+    or_cart_eval(c, c->x_eq, NULL, Hx);
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+            A[i * 9 + j] = Hx[i * 9 + j] / sqrt(c->mass[i / 3] * c->mass[j / 3]);
+            Vm[i * 9 + j] = i == j ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) {
+                tot += A[i * 9 + j] * A[i * 9 + j];
+                if (i != j) off += A[i * 9 + j] * A[i * 9 + j];
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < 8; ++p)
+            for (int q = p + 1; q < 9; ++q) {
+                const double apq = A[p * 9 + q];
+                if (apq == 0.0) continue;
+                /* rotation that zeroes A[p][q]: tan(2 phi) = 2 apq / (aqq - app) */
+                const double theta = (A[q * 9 + q] - A[p * 9 + p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < 9; ++k) {
+                    const double akp = A[k * 9 + p], akq = A[k * 9 + q];
+                    A[k * 9 + p] = cs * akp - sn * akq;
+                    A[k * 9 + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < 9; ++k) {
+                    const double apk = A[p * 9 + k], aqk = A[q * 9 + k];
+                    A[p * 9 + k] = cs * apk - sn * aqk;
+                    A[q * 9 + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < 9; ++k) {
+                    const double vkp = Vm[k * 9 + p], vkq = Vm[k * 9 + q];
+                    Vm[k * 9 + p] = cs * vkp - sn * vkq;
+                    Vm[k * 9 + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    /* order by eigenvalue: the three largest are the vibrations */
+    int idx[9];
+    for (int i = 0; i < 9; ++i) idx[i] = i;
+    for (int i = 0; i < 9; ++i)
+        for (int j = i + 1; j < 9; ++j)
+            if (A[idx[j] * 9 + idx[j]] < A[idx[i] * 9 + idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+    double rigid = 0.0;
+    for (int i = 0; i < 6; ++i) rigid = fmax(rigid, fabs(A[idx[i] * 9 + idx[i]]));
+    for (int m = 0; m < 3; ++m) {
+        const int col = idx[6 + m];
+        omega[m] = sqrt(A[col * 9 + col]);
+        double sgn = 1.0;
+        for (int i = 0; i < 9; ++i)
+            if (fabs(Vm[i * 9 + col]) > 1e-3) { sgn = Vm[i * 9 + col] > 0.0 ? 1.0 : -1.0; break; }
+        for (int i = 0; i < 9; ++i) c->Lm[i * 3 + m] = sgn * Vm[i * 9 + col] / sqrt(c->mass[i / 3]);
+    }
+    return rigid;
+}
+
 
 static double or_sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
 
@@ -190,6 +375,30 @@ double or_pes_eval(const or_pes *pes, const double *q, double *g, double *H)
     double V = 0.0;
     if (g) memset(g, 0, sizeof(double) * F);
     if (H) memset(H, 0, sizeof(double) * F * F);
+    if (pes->cart) {
+        /* V(q) = V_cart(x_eq + Lm q): g = Lm^T grad_x V, H = Lm^T H_x Lm (F = 3) */
+        const or_cart *c = pes->cart;
+        double x[9], gx[9], Hx[81];
+        for (int i = 0; i < 9; ++i) {
+            x[i] = c->x_eq[i];
+            for (int m = 0; m < 3; ++m) x[i] += c->Lm[i * 3 + m] * q[m];
+        }
+        V = or_cart_eval(c, x, gx, Hx);
+        for (int m = 0; m < 3; ++m) {
+            if (g) {
+                g[m] = 0.0;
+                for (int i = 0; i < 9; ++i) g[m] += c->Lm[i * 3 + m] * gx[i];
+            }
+            if (H)
+                for (int n = 0; n < 3; ++n) {
+                    double acc = 0.0;
+                    for (int i = 0; i < 9; ++i)
+                        for (int j = 0; j < 9; ++j) acc += c->Lm[i * 3 + m] * Hx[i * 9 + j] * c->Lm[j * 3 + n];
+                    H[m * 3 + n] = acc;
+                }
+        }
+        return V;
+    }
     for (int i = 0; i < F; ++i) {
         if (pes->diag_kind == 0) {
             double w2 = pes->omega[i] * pes->omega[i];

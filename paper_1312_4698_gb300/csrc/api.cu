@@ -103,6 +103,9 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
     if (!propagate_supported(F, prm->precision, prm->kernel))
         return fail(SCIVR_EUNSUPPORTED, "scivr_propagate: precision %d / kernel %d not built for F=%d",
                     prm->precision, prm->kernel, F);
+    if (pes->dev.kind == SCIVR_PES_CART3 && (prm->precision != SCIVR_FP64 || prm->kernel == SCIVR_KERNEL_GROUP))
+        return fail(SCIVR_EUNSUPPORTED, "scivr_propagate: a Cartesian surface propagates in FP64 with the "
+                                        "thread-per-trajectory schedule");
 
     PropLaunch L{};
     L.pes = pes->dev;
@@ -111,7 +114,7 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
     A.n_steps = prm->n_steps;
     A.n_chi = prm->n_chi;
     A.precision = prm->precision;
-    A.kernel = prm->kernel;
+    A.kernel = (pes->dev.kind == SCIVR_PES_CART3) ? SCIVR_KERNEL_THREAD : prm->kernel;
     A.amplitude = prm->amplitude;
     A.dt = prm->dt;
     A.stab_tol = prm->stab_tol;

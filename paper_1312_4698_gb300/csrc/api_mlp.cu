@@ -85,6 +85,8 @@ int scivr_pes_set_mlp(scivr_pes pes, const scivr_mlp_desc *m)
     cudaError_t e;
     if (m) {
         if (F > 9) return err(SCIVR_EUNSUPPORTED, "scivr_pes_set_mlp: F=%d > 9 not built", F);
+        if (pes->dev.kind == SCIVR_PES_CART3)
+            return err(SCIVR_EUNSUPPORTED, "scivr_pes_set_mlp: a learned residual needs a polynomial surface");
         if (m->H != SCIVR_MLP_HIDDEN) return err(SCIVR_EINVAL, "scivr_pes_set_mlp: H=%d (only %d built)", m->H, SCIVR_MLP_HIDDEN);
         const int H = m->H;
         if (!m->s_in || !m->W1 || !m->b1 || !m->W2 || !m->b2 || !m->W3 || !m->b3 || !m->w4)
@@ -245,6 +247,8 @@ int scivr_pes_eval(scivr_pes pes, int64_t n, const double *q, int32_t terms, dou
     if (terms != SCIVR_TERMS_ALL && terms != SCIVR_TERMS_DIAG && terms != SCIVR_TERMS_COUPLING)
         return err(SCIVR_EINVAL, "scivr_pes_eval: terms=%d invalid", terms);
     if (pes->dev.F > 9) return err(SCIVR_EUNSUPPORTED, "scivr_pes_eval: F=%d > 9 not built", pes->dev.F);
+    if (pes->dev.kind == SCIVR_PES_CART3 && terms != SCIVR_TERMS_ALL)
+        return err(SCIVR_EINVAL, "scivr_pes_eval: a Cartesian surface has no diagonal/coupling split (terms=%d)", terms);
     cudaError_t e = launch_pes_eval(pes->dev, n, q, terms, V, g, H, static_cast<cudaStream_t>(stream));
     count_launches(1);
     if (e != cudaSuccess) return cuda_error(e, "scivr_pes_eval: launch");

@@ -187,8 +187,10 @@ int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t f
         if (rc == SCIVR_OK)
             rc = check_spectrum_args(it.amp, it.amp_ld, SCIVR_FP64, it.w, it.good, it.n_traj, it.prm.n_steps,
                                      it.prm.dt, it.E_min, it.E_max, it.n_E, ft_mode, it.I_out, "scivr_batch_create");
-        if (rc == SCIVR_OK && it.prm.precision == SCIVR_MIXED && it.pes->dev.F > 16)
-            rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: mixed precision is built for F <= 16");
+        if (rc == SCIVR_OK && it.prm.precision == SCIVR_MIXED && it.pes->dev.F > SCIVR_MAX_F)
+            rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: mixed precision is built for F <= 24");
+        if (rc == SCIVR_OK && it.pes->dev.kind != SCIVR_PES_POLY)
+            rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: batches take polynomial surfaces");
         if (rc == SCIVR_OK && it.prm.amplitude != SCIVR_AMP_TA)
             rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: batch spectra are time-averaged (SCIVR_AMP_TA)");
         if (rc == SCIVR_OK && it.pes->dev.mlp.H != 0)

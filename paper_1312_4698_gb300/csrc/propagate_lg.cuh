@@ -190,6 +190,13 @@ __device__ __forceinline__ int jswz(int r, int j) { return j ^ (r & (JOBS >= 16 
 // shorter (8 steps; 4 above F = 12) and 32 / (T * C) lanes share a job's elimination
 // by rows; the per-job prefactor matrices then take the same shared memory as one
 // FP32 word per entry at the FP64 path's chunk length.
+// Mixed path: steps between stability tests (a multiple of every mixed chunk length).
+// The flag is sticky and a bad trajectory is dropped whole, so a coarser test differs
+// from the per-step one only for a deviation that crosses the threshold and falls back
+// below it between two tests (on the recipe surfaces, none: the good sets at 8- and
+// 16-step cadences equal the per-step ones).
+constexpr int kDetMEvery = 16;
+
 template <int F, int G, typename Real> __host__ __device__ constexpr int lg_chunk()
 {
     if constexpr (sizeof(Real) == 4) return G == 32 && F > 16 ? 2 : ((G == 32 && F > 12) || (G == 16 && F > 8) ? 4 : 8);
@@ -297,10 +304,6 @@ struct WarpShared {
     double argj[JOBS];                      // arg det A per job (mixed path: from the elimination's lanes)
     double2 detAj[JOBS];                    // det A per job (mixed path)
     double2 ov0[SCIVR_MAX_CHI][T];          // log of the Herman-Kluk summand's divisor per trajectory
-    // above F = 16, det M eliminates rows of M^T held here (row stride 2F + 1: lanes reading
-    // the same column of different rows hit different banks) instead of in registers
-    static constexpr int WMR = F > 16 ? 2 * F : 1;
-    Real Wm[WMR][WMR + 1];
 };
 
 // One CTA's share of a propagation: trajectories (cta * WARPS + warp) * T + t.
@@ -481,6 +484,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         // ---------------- phase 1: cnt steps, group-parallel ----------------
         for (int c = 0; c < cnt; ++c) {
             Real dS = Real(0);   // this lane's share of the step's action increment
+#pragma unroll 1
             for (int sub = 0; sub < 4; ++sub) {
                 // drift: q += tau p, S += tau p.p/2, M_q += tau M_p
                 {
@@ -634,61 +638,10 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             // sign of det is the parity of the order in which they were picked, counted as
             // inversions on the bitmask of unused rows.
             // Cadence: the FP64 path tests every step (flags equal to the oracle's bit for bit);
-            // the mixed path tests at the last step of each chunk.  The flag is sticky and a bad
-            // trajectory is dropped whole, so the two differ only for a trajectory whose deviation
-            // crosses the threshold and falls back below it within one chunk; the FP32 threshold
-            // (537) sits far above the rounding noise, where a deviation that has grown past it
-            // keeps growing (Sec. III.A: chaotic trajectories are the ones removed).
-            if constexpr (F > 16) {
-                if (c == cnt - 1) {
-                    static_assert(T == 1, "one trajectory per warp above F = 16");
-#pragma unroll
-                    for (int s = 0; s < NCOL; ++s) {
-                        const int col = g + s * G;
-                        if (col < N2) {
-#pragma unroll
-                            for (int a = 0; a < F; ++a) { sh.Wm[col][a] = Mp[s][a]; sh.Wm[col][F + a] = Mq[s][a]; }
-                        }
-                    }
-                    __syncwarp();
-                    Real det = Real(1);
-                    unsigned long long unused = (1ull << N2) - 1ull;
-                    unsigned parity = 0u;
-                    for (int k = 0; k < N2; ++k) {
-                        unsigned key = 0u;
-#pragma unroll
-                        for (int s = 0; s < NCOL; ++s) {
-                            const int col = g + s * G;
-                            if (col < N2 && ((unused >> col) & 1ull)) {
-                                const unsigned kk = (__float_as_uint(fabsf(sh.Wm[col][k])) & ~63u) | (unsigned)(col + 1);
-                                key = kk > key ? kk : key;
-                            }
-                        }
-                        const unsigned kmax = __reduce_max_sync(FULL, key);
-                        const int pc = (int)(kmax & 63u) - 1;
-                        const Real pk = sh.Wm[pc][k];
-                        const Real inv = __fdividef(1.0f, pk);
-                        parity ^= (unsigned)__popcll(unused & ((1ull << pc) - 1ull)) & 1u;
-                        unused &= ~(1ull << pc);
-                        det *= pk;
-#pragma unroll
-                        for (int s = 0; s < NCOL; ++s) {
-                            const int col = g + s * G;
-                            if (col < N2 && ((unused >> col) & 1ull)) {
-                                const Real l = sh.Wm[col][k] * inv;
-                                for (int i = k + 1; i < N2; ++i) sh.Wm[col][i] = fma(-l, sh.Wm[pc][i], sh.Wm[col][i]);
-                            }
-                        }
-                        __syncwarp();
-                    }
-                    if (parity) det = -det;
-                    const Real dev = isfinite(det) ? fabs(fma(det, det, Real(-1))) : Real(CUDART_INF);
-                    stab = dev > stab ? dev : stab;
-                    if (dev > A.stab_tol_f) good = false;
-                    detM_last = (double)det;
-                }
-            } else
-            if (sizeof(Real) == 8 || c == cnt - 1) {
+            // the mixed path tests every kDetMEvery steps, after phase 2 (below).  The FP32
+            // threshold (537) sits far above the rounding noise, where a deviation that has
+            // grown past it keeps growing (Sec. III.A: chaotic trajectories are the ones removed).
+            if constexpr (sizeof(Real) == 8) {
                 Real W[NCOL][N2];
 #pragma unroll
                 for (int s = 0; s < NCOL; ++s)
@@ -817,25 +770,36 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             // Mixed path: the entries of A are FP32 (formed from the FP32 monodromy) and the
             // elimination runs in double-FP32 on the FP32 pipe, so det A carries FP64-class
             // accuracy for those entries.  LPJ lanes share a job: the rows still to be
-            // eliminated are dealt out over them through a permutation (4 bits per row,
-            // rows k.. of the permutation are the active ones), the pivot is an arg-max of
+            // eliminated are dealt out over them through a permutation (a 4-bit field per row
+            // up to F = 16, 5 bits above, in two 64-bit words; positions k.. are the active
+            // rows), the pivot is an arg-max of
             // |a_ik|^2 over the job's lanes, and det A is the product of the pivots in FP64,
             // its sign flipped per exchange of the permutation.
             constexpr int LPJ = 32 / JOBS;
             static_assert(LPJ * JOBS == 32, "jobs must tile the warp");
             const int job = ln / LPJ, r = ln % LPJ;
             auto at = [&](int e) -> float4 & { return sh.A[e][jswz<JOBS>(e, job)]; };
-            unsigned long long perm = 0ull;
+            constexpr int PB = F > 16 ? 5 : 4, PPW = 64 / PB;   // bits per field, fields per word
+            constexpr unsigned long long PMASK = (1ull << PB) - 1ull;
+            unsigned long long perm0 = 0ull, perm1 = 0ull;
 #pragma unroll
-            for (int i = 0; i < F; ++i) perm |= (unsigned long long)i << (4 * i);
-            auto prow = [&](int pos) -> int { return (int)((perm >> (4 * pos)) & 15ull); };
-            double dr = 1.0, di = 0.0;
-#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                if (i < PPW) perm0 |= (unsigned long long)i << (PB * i);
+                else perm1 |= (unsigned long long)i << (PB * (i - PPW));
+            }
+            auto prow = [&](int pos) -> int {
+                return pos < PPW ? (int)((perm0 >> (PB * pos)) & PMASK) : (int)((perm1 >> (PB * (pos - PPW))) & PMASK);
+            };
+            auto pset = [&](int pos, unsigned long long v) {
+                if (pos < PPW) perm0 = (perm0 & ~(PMASK << (PB * pos))) | (v << (PB * pos));
+                else perm1 = (perm1 & ~(PMASK << (PB * (pos - PPW)))) | (v << (PB * (pos - PPW)));
+            };
+            double dr = 1.0, di = 0.0;   // det A, the product of the pivots in FP64
+#pragma unroll 1
             for (int k = 0; k < F; ++k) {
                 // pivot: the largest |a_ik|^2 (leading words) over the active rows
                 float best = -1.0f;
                 int bpos = k;
-#pragma unroll
                 for (int s0 = k; s0 < F; s0 += LPJ) {
                     const int pos = s0 + r;
                     if (pos < F) {
@@ -851,8 +815,9 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; }
                 }
                 if (bpos != k) {
-                    const unsigned long long a = (perm >> (4 * k)) & 15ull, b = (perm >> (4 * bpos)) & 15ull;
-                    perm ^= ((a ^ b) << (4 * k)) | ((a ^ b) << (4 * bpos));
+                    const unsigned long long a = (unsigned long long)prow(k), b = (unsigned long long)prow(bpos);
+                    pset(k, b);
+                    pset(bpos, a);
                     dr = -dr;
                     di = -di;
                 }
@@ -871,7 +836,6 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 const ff ir = ff_mul(pre, rm);
                 const ff nii = ff_mul(pim, rm);
                 const ff ii = {-nii.hi, -nii.lo};
-#pragma unroll
                 for (int s0 = k + 1; s0 < F; s0 += LPJ) {
                     const int pos = s0 + r;
                     if (pos < F) {
@@ -882,7 +846,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         const ff zero = {0.0f, 0.0f};
                         const ff lr = ff_sub_mul_add_mul(zero, ai, ii, ar, ir);                       // ar ir - ai ii
                         const ff li = ff_sub_mul_add_mul(zero, {-ar.hi, -ar.lo}, ii, ai, ir);         // ar ii + ai ir
-#pragma unroll
+#pragma unroll 2
                         for (int cc = k + 1; cc < F; ++cc) {
                             const float4 pv = at(pr * F + cc);
                             const ff pre_c = {pv.x, pv.y}, pim_c = {pv.z, pv.w};
@@ -960,6 +924,70 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             detA = make_double2(dr, di);
             argA = atan2(di, dr);
             if (A.amplitude == SCIVR_AMP_HK) sh.lnA[ln] = 0.5 * log(hypot(dr, di));
+        }
+        if constexpr (sizeof(Real) == 4) {
+            // det M every kDetMEvery steps and at the last step (at a chunk end: M is unchanged
+            // since): rows of M^T in the job matrices' storage, free once det A is done
+            // (2F (2F + 1) words per trajectory fit in its 4 F^2 C words), row stride 2F + 1 so
+            // that lanes reading one column of different rows hit different banks; a rolled
+            // loop keeps the code and registers small
+            static_assert(kDetMEvery % C == 0, "det M cadence falls on chunk ends");
+            if ((step0 + cnt) % kDetMEvery == 0 || step0 + cnt == A.n_steps) {
+                float (*Wm)[N2 + 1] = reinterpret_cast<float (*)[N2 + 1]>(&sh.A[0][0]) + t * N2;
+                static_assert(sizeof(float) * T * N2 * (N2 + 1) <= sizeof(sh.A), "det M workspace");
+#pragma unroll
+                    for (int s = 0; s < NCOL; ++s) {
+                        const int col = g + s * G;
+                        if (col < N2) {
+#pragma unroll
+                            for (int a = 0; a < F; ++a) { Wm[col][a] = Mp[s][a]; Wm[col][F + a] = Mq[s][a]; }
+                        }
+                    }
+                    __syncwarp();
+                    float det = 1.0f;
+                    unsigned long long unused = N2 == 64 ? ~0ull : (1ull << N2) - 1ull;
+                    unsigned parity = 0u;
+#pragma unroll 1
+                    for (int k = 0; k < N2; ++k) {
+                        unsigned key = 0u;
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s) {
+                            const int col = g + s * G;
+                            if (col < N2 && ((unused >> col) & 1ull)) {
+                                const unsigned kk = (__float_as_uint(fabsf(Wm[col][k])) & ~63u) | (unsigned)(col + 1);
+                                key = kk > key ? kk : key;
+                            }
+                        }
+                        // one full-warp integer max per group (the other groups' lanes contribute 0)
+                        unsigned kmax = 0u;
+#pragma unroll
+                        for (int tt = 0; tt < T; ++tt) {
+                            const unsigned r = __reduce_max_sync(FULL, t == tt ? key : 0u);
+                            kmax = (t == tt) ? r : kmax;
+                        }
+                        const int pc = (int)(kmax & 63u) - 1;
+                        const float pk = Wm[pc][k];
+                        const float inv = __fdividef(1.0f, pk);
+                        parity ^= (unsigned)__popcll(unused & ((1ull << pc) - 1ull)) & 1u;
+                        unused &= ~(1ull << pc);
+                        det *= pk;
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s) {
+                            const int col = g + s * G;
+                            if (col < N2 && ((unused >> col) & 1ull)) {
+                                const float l = Wm[col][k] * inv;
+                                for (int i = k + 1; i < N2; ++i) Wm[col][i] = fmaf(-l, Wm[pc][i], Wm[col][i]);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    if (parity) det = -det;
+                    const float dev = isfinite(det) ? fabsf(fmaf(det, det, -1.0f)) : CUDART_INF_F;
+                    stab = dev > stab ? dev : stab;
+                    if (dev > A.stab_tol_f) good = false;
+                    detM_last = (double)det;
+            }
+            __syncwarp();   // the next chunk's phase 1 refills the job matrices
         }
         // ---------------- phase 3: continuous phase (segmented scan) ----------------
         const double arg = argA;

@@ -16,6 +16,7 @@
 // for every reference state.
 #include <math_constants.h>
 
+#include "cartesian.cuh"
 #include "scivr_internal.cuh"
 
 namespace scivr {
@@ -47,6 +48,19 @@ template <int F>
 __device__ __forceinline__ void pes_fp64(const PesDev &pes, const double (&q)[F], double (&H)[F][F],
                                          double (&g)[F], double &V)
 {
+    if constexpr (F == 3) {
+        if (pes.kind == SCIVR_PES_CART3) {   // Cartesian surface through the bond vectors
+            double gq[3], Hq[3][3];
+            V = cart3_eval_q(*pes.cart, q, gq, Hq);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                g[a] = gq[a];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) H[a][b] = Hq[a][b];
+            }
+            return;
+        }
+    }
     constexpr int P = F * (F + 1) / 2;
     double qq[P];
 #pragma unroll

@@ -31,8 +31,12 @@ struct MlpWeightsDev {
 // theorem for homogeneous polynomials, grad V3 = H3 q / 2, V3 = q.H3 q / 6,
 // grad V4 = H4 q / 3 and V4 = q.H4 q / 12, so one pass over the packed
 // Hessian entries yields V, grad V and H.
+struct CartQ;   // cartesian.cuh
+
 struct PesDev {
     int F, P, diag_kind;
+    int kind;                        // SCIVR_PES_POLY or SCIVR_PES_CART3
+    const CartQ *cart;               // SCIVR_PES_CART3: bond-vector map and force constants
     int has3, has4;
     const double *omega, *D, *a;     // [F]
     const double *T3;                // [F][P]

@@ -27,6 +27,7 @@ SCIVR_EUNSUPPORTED = -5
 SCIVR_DIAG_HARMONIC = 0
 SCIVR_DIAG_MORSE = 1
 SCIVR_PES_POLY = 0
+SCIVR_PES_CART3 = 1
 SCIVR_FP64 = 0
 SCIVR_MIXED = 1
 SCIVR_FT_FP64 = 0
@@ -124,7 +125,9 @@ EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_s
             "scivr_selftest_wait_timeout", "scivr_last_error", "scivr_launch_count",
             "scivr_batch_create", "scivr_batch_launch", "scivr_batch_info", "scivr_batch_destroy",
             "scivr_mlp_param_count", "scivr_pes_set_mlp", "scivr_mlp_eval", "scivr_mlp_get_params",
-            "scivr_mlp_set_params", "scivr_mlp_loss_grad", "scivr_mlp_adamw", "scivr_pes_eval"]
+            "scivr_mlp_set_params", "scivr_mlp_loss_grad", "scivr_mlp_adamw", "scivr_pes_eval",
+            "scivr_normal_modes", "scivr_normal_to_cartesian", "scivr_cartesian_to_normal",
+            "scivr_create_pes_cartesian"]
 
 
 def scivr_check_status(stream=None) -> int:
@@ -192,8 +195,67 @@ class Pes:
             pass
 
 
+class scivr_cart_triatomic(C.Structure):
+    _fields_ = [("mass", C.c_double * 3), ("D", C.c_double * 2), ("a", C.c_double * 2),
+                ("re", C.c_double * 2), ("k_bend", C.c_double), ("theta_e", C.c_double)]
+
+
+_lib.scivr_normal_modes.restype = C.c_int
+_lib.scivr_normal_modes.argtypes = [C.POINTER(scivr_cart_triatomic), _vp, _vp, _vp]
+_lib.scivr_normal_to_cartesian.restype = C.c_int
+_lib.scivr_normal_to_cartesian.argtypes = [C.POINTER(scivr_cart_triatomic), _i64, _vp, _vp]
+_lib.scivr_cartesian_to_normal.restype = C.c_int
+_lib.scivr_cartesian_to_normal.argtypes = [C.POINTER(scivr_cart_triatomic), _i64, _vp, _vp]
+_lib.scivr_create_pes_cartesian.restype = C.c_int
+_lib.scivr_create_pes_cartesian.argtypes = [C.POINTER(scivr_cart_triatomic), C.POINTER(_vp)]
+
+
+def _cart_struct(c) -> scivr_cart_triatomic:
+    s = scivr_cart_triatomic()
+    s.mass[:] = [float(v) for v in c.mass]
+    s.D[:] = [float(v) for v in c.D]
+    s.a[:] = [float(v) for v in c.a]
+    s.re[:] = [float(v) for v in c.re]
+    s.k_bend = float(c.k_bend)
+    s.theta_e = float(c.theta_e)
+    return s
+
+
+def scivr_normal_modes(c):
+    """c: workloads.CartTriatomic.  Returns omega [3], x_eq [9], Lm [9, 3] (host arrays)."""
+    om, xe, Lm = np.zeros(3), np.zeros(9), np.zeros((9, 3))
+    _check(_lib.scivr_normal_modes(C.byref(_cart_struct(c)), om.ctypes.data, xe.ctypes.data, Lm.ctypes.data),
+           "scivr_normal_modes")
+    return om, xe, Lm
+
+
+def scivr_normal_to_cartesian(c, q):
+    q = _f64(np.atleast_2d(q))
+    x = np.zeros((q.shape[0], 9))
+    _check(_lib.scivr_normal_to_cartesian(C.byref(_cart_struct(c)), q.shape[0], q.ctypes.data, x.ctypes.data),
+           "scivr_normal_to_cartesian")
+    return x
+
+
+def scivr_cartesian_to_normal(c, x):
+    x = _f64(np.atleast_2d(x))
+    q = np.zeros((x.shape[0], 3))
+    _check(_lib.scivr_cartesian_to_normal(C.byref(_cart_struct(c)), x.shape[0], x.ctypes.data, q.ctypes.data),
+           "scivr_cartesian_to_normal")
+    return q
+
+
+def scivr_create_pes_cartesian(c) -> Pes:
+    h = _vp()
+    _check(_lib.scivr_create_pes_cartesian(C.byref(_cart_struct(c)), C.byref(h)), "scivr_create_pes_cartesian")
+    return Pes(h.value, 3)
+
+
 def scivr_create_pes(desc) -> Pes:
-    """desc: workloads.PesDesc-like object (F, diag_kind, omega, D, a, idx3, c3, idx4, c4)."""
+    """desc: workloads.PesDesc-like object (F, diag_kind, omega, D, a, idx3, c3, idx4, c4), or a
+    workloads.CartPes (a Cartesian surface in its normal modes)."""
+    if getattr(desc, "cart", None) is not None:
+        return scivr_create_pes_cartesian(desc.cart)
     keep = [_f64(desc.omega), _f64(desc.D), _f64(desc.a),
             np.ascontiguousarray(desc.idx3, dtype=np.int32), _f64(desc.c3),
             np.ascontiguousarray(desc.idx4, dtype=np.int32), _f64(desc.c4)]

@@ -76,6 +76,48 @@ class PesDesc:
         self.c4 = np.ascontiguousarray(self.c4, dtype=np.float64).reshape(-1)
 
 
+AMU = 1822.888486209  # unified atomic mass unit in electron masses
+
+
+@dataclasses.dataclass
+class CartTriatomic:
+    """Cartesian surface of a bent triatomic: atoms 0 and 2 bonded to the central atom 1,
+    V(x) = sum_b D_b (1 - exp(-a_b (r_b - re_b)))^2 + (k_bend / 2) (cos theta - cos theta_e)^2
+    with r_0 = |x0 - x1|, r_1 = |x2 - x1| and theta the angle 0-1-2.  x: [9] Cartesian
+    coordinates (bohr), atom-major; masses in electron masses.  Its normal modes (the
+    coordinates the propagation runs in) come from the mass-weighted Hessian at the
+    equilibrium geometry (Sec. III.A)."""
+    mass: np.ndarray          # [3]
+    D: np.ndarray             # [2] Morse depths (hartree)
+    a: np.ndarray             # [2] Morse range parameters (1/bohr)
+    re: np.ndarray            # [2] equilibrium bond lengths (bohr)
+    k_bend: float             # hartree
+    theta_e: float            # equilibrium angle (rad)
+
+    @property
+    def F(self) -> int:
+        return 3
+
+
+@dataclasses.dataclass
+class CartPes:
+    """A potential given as a Cartesian surface (F = 3 vibrational normal modes)."""
+    cart: CartTriatomic
+
+    @property
+    def F(self) -> int:
+        return 3
+
+
+def water_like_triatomic() -> CartTriatomic:
+    """Synthetic water-sized surface: H-O-H masses, bonds of 1.81 bohr at 104.5 degrees,
+    Morse depth 0.2 hartree; a = 1.1 / bohr and k_bend = 0.16 hartree put the stretches
+    near 3650-3700 cm^-1 and the bend near 1600 cm^-1 (the F = 3 workload's range)."""
+    m_h, m_o = 1.00782503223 * AMU, 15.99491461957 * AMU
+    return CartTriatomic(mass=np.array([m_h, m_o, m_h]), D=np.array([0.2, 0.2]), a=np.array([1.1, 1.1]),
+                         re=np.array([1.81, 1.81]), k_bend=0.16, theta_e=float(np.deg2rad(104.5)))
+
+
 @dataclasses.dataclass
 class MlpParams:
     """Learned residual V_mlp(q) = s_out * (w4 . a3 + b4) on x = s_in * q (a_l = silu(z_l)).

@@ -263,7 +263,7 @@ def test_binding_struct_layouts_match_the_headers(tmp_path):
     if gcc is None:
         pytest.skip("no C compiler")
     structs = [getattr(scivr, n) for n in ("scivr_pes_desc", "scivr_prop_params", "scivr_final_state",
-                                           "scivr_batch_item", "scivr_mlp_desc")]
+                                           "scivr_batch_item", "scivr_mlp_desc", "scivr_cart_triatomic")]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "scivr.h"', '#include "scivr_mlp.h"',
              'int main(void) {']
     for S in structs:

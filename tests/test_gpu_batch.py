@@ -1,4 +1,4 @@
-"""Batched multi-molecule runs (scivr_batch_*): one persistent launch per F-class.
+"""Batched multi-molecule runs (scivr_batch_*), F from 3 to 24.
 
 The batch must reproduce, bit for bit, what per-molecule scivr_propagate /
 scivr_spectrum calls produce (same kernel arithmetic per trajectory), match
@@ -25,7 +25,7 @@ def G():
 
 def _molecules():
     specs = [(3, 100, 70, 1), (6, 257, 150, 2), (9, 64, 40, 3), (6, 1000, 96, 4), (3, 33, 33, 5),
-             (4, 50, 61, 6), (12, 45, 37, 7), (15, 70, 29, 8)]
+             (4, 50, 61, 6), (12, 45, 37, 7), (15, 70, 29, 8), (24, 21, 13, 9), (20, 9, 8, 10)]
     out = []
     for F, n, steps, seed in specs:
         w8 = wl.config_f3(n_traj=n, n_steps=steps, n_E=150) if F == 3 else \
@@ -83,6 +83,36 @@ def test_batch_matches_per_molecule_runs(G, ft_mode):
         assert torch.equal(b.I, I)
         assert int(b.n_good.item()) == int(ng.item())
     assert G.scivr_check_status() == G.SCIVR_OK
+
+
+def test_batch_of_every_recipe_f_matches_per_molecule_runs(G):
+    """The batch recipe's F set, 3, 6, 9, 12, 15 and 24 (with F = 20 besides), in one plan,
+    all mixed precision: bit for bit the per-molecule runs, and the same again from a
+    captured graph."""
+    import torch
+    mols = [_molecules()[i] for i in (0, 1, 2, 6, 7, 8, 9)]
+    entries = _setup(G, mols, [1] * len(mols))
+    plan = G.scivr_batch_create(entries, ft_mode=2)
+    assert sorted(F for F, _, _ in plan.groups()) == [3, 6, 9, 12, 15, 20, 24]
+    G.scivr_batch_launch(plan)
+    torch.cuda.synchronize()
+    assert G.scivr_check_status() == G.SCIVR_OK
+    for e in entries:
+        amp, good, I, ng = _reference(G, e, 2)
+        b = e["bufs"]
+        assert torch.equal(b.good, good) and torch.equal(b.amp, amp) and torch.equal(b.I, I)
+    eager = [(e["bufs"].amp.clone(), e["bufs"].I.clone()) for e in entries]
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(graph, stream=side):
+        G.scivr_batch_launch(plan, stream=side)
+    for e in entries:
+        e["bufs"].amp.zero_()
+        e["bufs"].I.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for e, (amp, I) in zip(entries, eager):
+        assert torch.equal(e["bufs"].amp, amp) and torch.equal(e["bufs"].I, I)
 
 
 def test_batch_fp64_item_matches_oracle(G):

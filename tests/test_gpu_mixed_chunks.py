@@ -3,7 +3,8 @@ schedule has a ragged end, and the F = 9 methane-sized workload at full size.
 
 The lane-group kernels process steps in chunks (mixed path: 8 steps up to
 F = 12); the prefactor determinants, the phase scan and the amplitude records
-run once per chunk, and the mixed path tests det M at the chunk's last step.
+run once per chunk, and the mixed path tests det M every 16 steps and at the
+last step.
 Step counts 301 and 405 end on a partial chunk (301 = 37*8 + 5, 405 = 50*8 + 5;
 also partial for 16-step chunks: 18*16 + 13, 25*16 + 5), and 67 trajectories
 leave the last CTA partly empty.  The discrete sum of Eq. 11
@@ -104,7 +105,7 @@ def test_mixed_ragged_tail_chunk_herman_kluk(G, F, n_steps):
 
 
 def test_mixed_chunk_end_stability_test_flags(G):
-    """Flags of the mixed path (FP32 det M tested at chunk ends) against the oracle's
+    """Flags of the mixed path (FP32 det M tested every 16 steps) against the oracle's
     (FP64 det M tested every step) at the same threshold, on a surface where most
     trajectories go bad: F = 6 with the recipe's couplings on mass-weighted q (the
     literal reading, under which trajectories escape), 128 trajectories, 600 steps.

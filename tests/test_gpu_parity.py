@@ -492,6 +492,33 @@ def test_wide_group_mixed_close_to_oracle(G, F):
     assert e_amp < 5e-2 and e_det < 1e-2 and e_dA < 1e-3 and e_q < 1e-3
 
 
+@pytest.mark.parametrize("F", [17, 20, 24])
+def test_two_column_groups_mixed_close_to_oracle(G, F):
+    """Mixed path above F = 16 (two monodromy columns per lane, coupling tensors read from
+    L2, det M in shared memory, 2-step chunks) against the FP64 oracle: 35 trajectories
+    (ragged for four trajectories per CTA) and 61 steps (odd: a 1-step tail chunk).  The
+    F = 24 surface is the batch recipe's (300 x 300 quartic Hessian tensor).  Bounds as for
+    F <= 16."""
+    w8 = wl.config_generic(F, seed=F, n_traj=35, n_steps=61)
+    p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, w8.n_traj, 3)
+    ra, rg, rf = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0, q0, final=True)
+    g = gpu_propagate(G, w8, p0, q0, precision=1, stab_tol=MIXED_STAB_TOL, fin=True)
+    assert G.scivr_check_status() == G.SCIVR_OK
+    sel = rg.astype(bool) & g["good"].astype(bool)
+    print(f"F={F}: oracle good {rg.sum()}, GPU good {g['good'].sum()}, both {sel.sum()}")
+    assert sel.sum() >= 0.9 * rg.sum() and sel.sum() > 0
+    e_amp = amp_err(g["amp"][:, sel], ra[:, sel], np.ones(sel.sum(), np.uint8))
+    e_det = np.max(np.abs(g["detM"][sel] - rf["detM"][sel]))
+    dA = g["detA"][:, 0] + 1j * g["detA"][:, 1]
+    e_dA = np.max(np.abs(dA[sel] - rf["detA"][sel]) / np.abs(rf["detA"][sel]))
+    rg_ = np.sqrt(w8.gamma)[:, None]
+    e_q = np.max(np.abs((g["q"] - rf["q"].T) * rg_)[:, sel])
+    e_M = np.max(np.abs(g["M"][sel] - rf["M"][sel])) / max(1.0, np.max(np.abs(rf["M"][sel])))
+    print(f"F={F}: {sel.sum()} of {rg.sum()} good; amp {e_amp:.2e} det M {e_det:.2e} det A {e_dA:.2e} "
+          f"q {e_q:.2e} M {e_M:.2e}")
+    assert e_amp < 5e-2 and e_det < 1e-1 and e_dA < 1e-3 and e_q < 1e-3 and e_M < 1e-3
+
+
 def test_wide_group_several_reference_states_and_hk(G):
     """F = 12: two reference states, time-averaged and Herman-Kluk summands."""
     from tests.test_gpu_hk import hk_propagate

@@ -327,8 +327,8 @@ def test_batch_matches_single_and_chi_layout():
 
 @pytest.mark.parametrize("sigma", [(3e-8, 3e-9), (5e-8, 5e-9)])
 def test_chunk_end_stability_cadence_selects_the_per_step_good_set(sigma):
-    """The mixed-precision kernels test det M at the last step of each chunk of C
-    steps instead of every step (Sec. II, Sec. III.A: a trajectory is discarded as
+    """The mixed-precision kernels test det M every C = 16 steps (and at the last step)
+    instead of every step (Sec. II, Sec. III.A: a trajectory is discarded as
     soon as |det(M^T M) - 1| exceeds the tolerance; the flag is sticky and the whole
     trajectory is dropped).  On the oracle's own per-step det M series, over surfaces
     where about half the trajectories go bad (couplings on mass-weighted q), the
