@@ -36,7 +36,7 @@ sys.path.insert(0, HERE)
 from paper_1312_4698_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "trajectory-steps/s and spectra/s at ≤1 cm⁻¹ peak error vs FP64 oracle"
-FT_MODES = {"fp64": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
+FT_MODES = {"fp64": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "czt64": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 MIXED_STAB_TOL = 1e-6 * 2.0 ** 29     # the FP64 threshold scaled by eps32 / eps64
 L2_FLUSH_BYTES = 512 << 20

@@ -67,7 +67,8 @@ enum { SCIVR_KERNEL_AUTO = 0,     /* library choice (tuned per F, precision, n_t
 enum { SCIVR_FT_FP64 = 0,         /* FP64 fused-multiply-add contraction (CUDA cores) */
        SCIVR_FT_TC_BF16 = 1,      /* tensor cores: one BF16 digit per operand, FP32 accumulation */
        SCIVR_FT_TC_BF16X3 = 2,    /* tensor cores: two BF16 digits, three digit products */
-       SCIVR_FT_TC_BF16X6 = 3 };  /* tensor cores: three BF16 digits, six products (FP32-level) */
+       SCIVR_FT_TC_BF16X6 = 3,    /* tensor cores: three BF16 digits, six products (FP32-level) */
+       SCIVR_FT_CZT64 = 4 };      /* FP64 chirp-z transform (Bluestein convolution by FFTs) */
 
 /* What scivr_propagate records per step. */
 enum { SCIVR_AMP_TA = 0,          /* time-averaged SC-IVR summand (Eq. I(E)_discreto) */
@@ -255,7 +256,13 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
  * the CUDA cores; the SCIVR_FT_TC_* modes split both operands into BF16
  * digits and contract on the tensor cores (tcgen05) with FP32 accumulation,
  * then sum tiles in FP64: their error is that of the digit count (about
- * 2^-8, 2^-16, 2^-24 relative to the largest terms).  Allocates
+ * 2^-8, 2^-16, 2^-24 relative to the largest terms).  SCIVR_FT_CZT64 evaluates the
+ * same sums in FP64 through Bluestein's identity E_k c dt = E_min c dt + w (k^2 + c^2
+ * - (k - c)^2)/2 (w = dE dt): a convolution by length-8192 FP64 FFTs per trajectory,
+ * about 10 L log2 L flops instead of 8 K n_E, with FP64 rounding; it takes
+ * n_steps + 1 <= 7169 and n_E <= 12288 (SCIVR_EUNSUPPORTED otherwise; energies beyond
+ * 8193 - (n_steps + 1) are transformed in blocks) and allocates about 200 KB plus
+ * 8 n_E bytes per SM.  Allocates
  * stream-ordered scratch (cudaMallocAsync): FP64 mode about
  * 16 (n_steps+1) n_E + 8 n_E ceil(n_traj/64) bytes; tensor-core modes about
  * 4 d (n_steps+1) (n_traj + 2 n_E) + 8 n_E ceil(n_traj/128) bytes, d digits.

@@ -170,8 +170,11 @@ int check_spectrum_args(const void *amp, int64_t amp_ld, int32_t amp_prec, const
     if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "%s: amp_ld < n_steps+1", who);
     if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "%s: amp not 16-byte aligned", who);
     if (amp_prec != SCIVR_FP64) return fail(SCIVR_EUNSUPPORTED, "%s: amp_prec %d not supported", who, amp_prec);
-    if (ft_mode != SCIVR_FT_FP64 && ft_tc_digits(ft_mode) == 0)
+    if (ft_mode != SCIVR_FT_FP64 && ft_mode != SCIVR_FT_CZT64 && ft_tc_digits(ft_mode) == 0)
         return fail(SCIVR_EUNSUPPORTED, "%s: ft_mode %d not supported", who, ft_mode);
+    if (ft_mode == SCIVR_FT_CZT64 && (n_steps + 1 > spectrum_czt_max_samples() || n_E > kCztMaxEnergies))
+        return fail(SCIVR_EUNSUPPORTED, "%s: the chirp-z mode takes n_steps + 1 <= %d and n_E <= %d", who,
+                    spectrum_czt_max_samples(), kCztMaxEnergies);
     return SCIVR_OK;
 }
 
@@ -405,6 +408,21 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
         if (rc != SCIVR_OK) return rc;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ft_mode == SCIVR_FT_CZT64) {
+        const size_t cb = spectrum_czt_scratch_bytes(n_traj, n_steps, n_E);
+        void *scr = nullptr;
+        cudaError_t e = cudaMallocAsync(&scr, cb, s);
+        if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: cudaMallocAsync");
+        int nl = 0;
+        e = launch_spectrum_czt(static_cast<const double2 *>(amp), amp_ld, w, good, n_traj, n_steps, dt, E_min,
+                                E_max, n_E, I_out, n_good_out, scr, s, &nl);
+        g_launches += nl;
+        cudaError_t e2 = cudaFreeAsync(scr, s);
+        if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: chirp-z launch");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "scivr_spectrum: cudaFreeAsync");
+        ok();
+        return SCIVR_OK;
+    }
     if (ft_mode != SCIVR_FT_FP64) {
         const size_t tb = spectrum_tc_scratch_bytes(ft_mode, n_traj, n_steps, n_E);
         void *scr = nullptr;

@@ -172,7 +172,7 @@ int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t f
 {
     if (!items || !out || n_items < 1) return set_error(SCIVR_EINVAL, "scivr_batch_create: need items and n_items >= 1");
     *out = nullptr;
-    if (ft_mode != SCIVR_FT_FP64 && ft_tc_digits(ft_mode) == 0)
+    if (ft_mode != SCIVR_FT_FP64 && ft_mode != SCIVR_FT_CZT64 && ft_tc_digits(ft_mode) == 0)
         return set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: ft_mode not supported");
     scivr_batch_s *B = new scivr_batch_s;
     B->ft_mode = ft_mode;
@@ -203,8 +203,9 @@ int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t f
         }
         B->items.push_back(it);
         B->launches.push_back(L);
-        const size_t sb = ft_mode == SCIVR_FT_FP64 ? spectrum_fp64_scratch_bytes(it.n_traj, it.prm.n_steps, it.n_E)
-                                                   : spectrum_tc_scratch_bytes(ft_mode, it.n_traj, it.prm.n_steps, it.n_E);
+        const size_t sb = ft_mode == SCIVR_FT_FP64    ? spectrum_fp64_scratch_bytes(it.n_traj, it.prm.n_steps, it.n_E)
+                          : ft_mode == SCIVR_FT_CZT64 ? spectrum_czt_scratch_bytes(it.n_traj, it.prm.n_steps, it.n_E)
+                                                      : spectrum_tc_scratch_bytes(ft_mode, it.n_traj, it.prm.n_steps, it.n_E);
         scratch = std::max(scratch, sb);
     }
     // groups
@@ -306,6 +307,9 @@ int scivr_batch_launch(scivr_batch B, void *stream)
             if (B->ft_mode == SCIVR_FT_FP64)
                 e = launch_spectrum_fp64(amp, it.amp_ld, it.w, it.good, it.n_traj, it.prm.n_steps, it.prm.dt,
                                          it.E_min, it.E_max, it.n_E, I, it.n_good_out, B->scratch, s, &nl);
+            else if (B->ft_mode == SCIVR_FT_CZT64)
+                e = launch_spectrum_czt(amp, it.amp_ld, it.w, it.good, it.n_traj, it.prm.n_steps, it.prm.dt,
+                                        it.E_min, it.E_max, it.n_E, I, it.n_good_out, B->scratch, s, &nl);
             else
                 e = launch_spectrum_tc(B->ft_mode, amp, it.amp_ld, it.w, it.good, it.n_traj, it.prm.n_steps,
                                        it.prm.dt, it.E_min, it.E_max, it.n_E, I, it.n_good_out, B->scratch, s, &nl);

@@ -267,6 +267,34 @@ __device__ __forceinline__ Real dot16(const Real *a, const Real *b)
     return r;
 }
 
+// Rows u, v against vectors x, y (all 16-byte aligned shared rows of S elements):
+// out = {u.x, u.y, v.x, v.y}.  Each loaded vector of u or v feeds two products, so a
+// warp's shared-memory wavefronts per multiply-add are half those of dot16.
+template <int S>
+__device__ __forceinline__ void dot16_2x2(const float *u, const float *v, const float *x, const float *y,
+                                          float (&out)[4])
+{
+    static_assert(S % 4 == 0, "padded length");
+    float acc[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q][0] = acc[q][1] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < S; i += 4) {
+        const float4 uu = *reinterpret_cast<const float4 *>(u + i), vv = *reinterpret_cast<const float4 *>(v + i);
+        const float4 xx = *reinterpret_cast<const float4 *>(x + i), yy = *reinterpret_cast<const float4 *>(y + i);
+        acc[0][0] = fmaf(uu.x, xx.x, acc[0][0]); acc[0][1] = fmaf(uu.y, xx.y, acc[0][1]);
+        acc[0][0] = fmaf(uu.z, xx.z, acc[0][0]); acc[0][1] = fmaf(uu.w, xx.w, acc[0][1]);
+        acc[1][0] = fmaf(uu.x, yy.x, acc[1][0]); acc[1][1] = fmaf(uu.y, yy.y, acc[1][1]);
+        acc[1][0] = fmaf(uu.z, yy.z, acc[1][0]); acc[1][1] = fmaf(uu.w, yy.w, acc[1][1]);
+        acc[2][0] = fmaf(vv.x, xx.x, acc[2][0]); acc[2][1] = fmaf(vv.y, xx.y, acc[2][1]);
+        acc[2][0] = fmaf(vv.z, xx.z, acc[2][0]); acc[2][1] = fmaf(vv.w, xx.w, acc[2][1]);
+        acc[3][0] = fmaf(vv.x, yy.x, acc[3][0]); acc[3][1] = fmaf(vv.y, yy.y, acc[3][1]);
+        acc[3][0] = fmaf(vv.z, yy.z, acc[3][0]); acc[3][1] = fmaf(vv.w, yy.w, acc[3][1]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = acc[q][0] + acc[q][1];
+}
+
 // Coupling tensors staged per CTA, transposed so that one potential entry e
 // reads one contiguous row: sT3[e][k] (k < F, stride S3), sT4[e][kl] (kl < P,
 // stride S4), zero-padded.
@@ -412,6 +440,20 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         while (e >= F - a) { e -= F - a; ++a; }
         ea[i] = a;
         eb[i] = a + e;
+    }
+    // two trajectories per warp (16-lane groups, mixed path): lane ln computes entries 2 ln and
+    // 2 ln + 1 for both trajectories (register blocking; P <= 64)
+    constexpr bool kBlocked = (T == 2) && (sizeof(Real) == 4) && TL::staged && (P <= 64) && (P > 16);
+    int ebA[2] = {0, 0}, ebB[2] = {0, 0};
+    if constexpr (kBlocked) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            int e = 2 * ln + i, a = 0;
+            if (e >= P) e = 0;
+            while (e >= F - a) { e -= F - a; ++a; }
+            ebA[i] = a;
+            ebB[i] = a + e;
+        }
     }
     // above F = 16: four consecutive entries 4 (g + i G) .. + 3 per load, (a, b) packed as a | b << 8
     constexpr int P4 = (P + 3) & ~3;
@@ -561,6 +603,33 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                             }
                         }
                     }
+                } else if constexpr (kBlocked) {
+                    const int e0 = 2 * ln, e1 = e0 + 1 < P ? e0 + 1 : e0;
+                    float v[2] = {0.0f, 0.0f};   // energy parts of trajectories 0 and 1
+                    if (e0 < P) {
+                        float h3[4] = {0.f, 0.f, 0.f, 0.f}, h4[4] = {0.f, 0.f, 0.f, 0.f};   // (e0,t0) (e0,t1) (e1,t0) (e1,t1)
+                        if (use3) dot16_2x2<S3>(sT3 + e0 * S3, sT3 + e1 * S3, sh.qr[0], sh.qr[1], h3);
+                        if (use4) dot16_2x2<S4>(sT4 + e0 * S4, sT4 + e1 * S4, sh.qq[0], sh.qq[1], h4);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int i = q >> 1, tt = q & 1, e = e0 + i;
+                            if (e < P) {
+                                const int a = ebA[i], b = ebB[i];
+                                const float h = h3[q] + h4[q];
+                                sh.H[tt][a][b] = h;
+                                sh.H[tt][b][a] = h;
+                                const float gce = fmaf(0.5f, h3[q], h4[q] * (1.0f / 3.0f));
+                                sh.Gc[tt][a][b] = gce;
+                                sh.Gc[tt][b][a] = gce;
+                                const float vc = fmaf(1.0f / 6.0f, h3[q], h4[q] * (1.0f / 12.0f));
+                                v[tt] = fmaf(a == b ? vc : 2.0f * vc, sh.qq[tt][e], v[tt]);
+                            }
+                        }
+                    }
+                    // this lane keeps its own trajectory's part and passes the other to the
+                    // matching lane of the other group, so that each group's lanes sum to its total
+                    const float mine = t == 0 ? v[0] : v[1], other = t == 0 ? v[1] : v[0];
+                    vpart = mine + __shfl_xor_sync(FULL, other, 16);
                 } else
 #pragma unroll
                 for (int i = 0; i < EPL; ++i) {

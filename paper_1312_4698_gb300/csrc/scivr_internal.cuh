@@ -102,6 +102,12 @@ size_t spectrum_hk_scratch_bytes(int64_t n_traj, int n_steps);
 cudaError_t launch_spectrum_hk(const double2 *amp, int64_t amp_ld, const uint8_t *good, int64_t n_traj, int n_steps,
                                double dt, double E_min, double E_max, int n_E, double *I_out, double2 *C_out,
                                int64_t *n_good_out, void *scratch, cudaStream_t s, int *n_launch);
+int spectrum_czt_max_samples();
+constexpr int kCztMaxEnergies = 12288;   // per-CTA weighted sums beside the 128 KB transform buffer
+size_t spectrum_czt_scratch_bytes(int64_t n_traj, int n_steps, int n_E);
+cudaError_t launch_spectrum_czt(const double2 *amp, int64_t amp_ld, const double *w, const uint8_t *good,
+                                int64_t n_traj, int n_steps, double dt, double E_min, double E_max, int n_E,
+                                double *I_out, int64_t *n_good_out, void *scratch, cudaStream_t s, int *n_launch);
 int ft_tc_digits(int ft_mode);
 size_t spectrum_tc_scratch_bytes(int ft_mode, int64_t n_traj, int n_steps, int n_E);
 cudaError_t launch_spectrum_tc(int ft_mode, const double2 *amp, int64_t amp_ld, const double *w,

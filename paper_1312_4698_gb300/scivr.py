@@ -34,6 +34,7 @@ SCIVR_FT_FP64 = 0
 SCIVR_FT_TC_BF16 = 1
 SCIVR_FT_TC_BF16X3 = 2
 SCIVR_FT_TC_BF16X6 = 3
+SCIVR_FT_CZT64 = 4
 SCIVR_KERNEL_AUTO = 0
 SCIVR_KERNEL_THREAD = 1
 SCIVR_KERNEL_GROUP = 2
