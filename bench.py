@@ -185,6 +185,28 @@ def gpu_selector(local: int) -> str:
     return str(local)
 
 
+def fma_peaks(stream=None):
+    """Attainable FP32 and FP64 FMA rates (TFLOP/s) of this GPU, measured live by the
+    library's probe (independent FMA chains on every SM, about 30 ms per launch, best of
+    three after one warm-up) -- the propagation kernels' roofline denominators."""
+    import torch
+    from paper_1312_4698_gb300 import scivr
+    out = {}
+    for name, prec, iters in (("fp32", 1, 225000), ("fp64", 0, 3750)):
+        best = 0.0
+        for rep in range(4):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = scivr.scivr_fma_probe(prec, iters, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out[name] = best
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
@@ -328,11 +350,12 @@ def batch_arm(args):
     traj_steps = sum(w8.n_traj * w8.n_steps for w8 in mols)
     flops = 0.0
     t_bound = 0.0
+    probe = fma_peaks()
     for w8 in mols:
         bulk, kept = propagate_flops_split(w8.F, w8.pes.c3.size, w8.pes.c4.size)
         flops += (bulk + kept) * w8.n_traj * w8.n_steps
-        t_bound += (bulk * w8.n_traj * w8.n_steps) / (FP32_PEAK_GFLOPS * 1e9) + \
-                   (kept * w8.n_traj * w8.n_steps) / (FP64_PEAK_GFLOPS * 1e9)
+        t_bound += (bulk * w8.n_traj * w8.n_steps) / (probe["fp32"] * 1e12) + \
+                   (kept * w8.n_traj * w8.n_steps) / (probe["fp64"] * 1e12)
     achieved = flops / (ms * 1e-3) / 1e12
     eff_peak = flops / t_bound / 1e12
     groups = plan.groups()
@@ -352,8 +375,9 @@ def batch_arm(args):
         "spectra_per_s": world * len(mols) / (ms * 1e-3),
         "roofline": {"kernel": "k_propagate_lg_batch<float> (scivr_batch_launch)", "bound": "alu",
                      "achieved": achieved, "peak": eff_peak, "unit": "TFLOP/s", "frac": achieved / eff_peak,
-                     "traffic": None, "peak_source": "two-pipe bound summed over molecules (FP32 bulk at "
-                                                     "80.5 TFLOP/s + FP64-kept at 1.25 TFLOP/s)"},
+                     "traffic": None, "peak_source": f"two-pipe bound summed over molecules (FP32 bulk at "
+                                                     f"{probe['fp32']:.1f} + FP64-kept at {probe['fp64']:.3f} "
+                                                     f"TFLOP/s, measured live by scivr_fma_probe)"},
         "cpu_baseline": None,
         "e2e": None,
         "gpu_launches": launches_per_step * args.steps,
@@ -723,6 +747,9 @@ def main(argv=None):
     ap.add_argument("--n-traj", type=int, default=None, help="override the workload's trajectory count")
     ap.add_argument("--n-steps", type=int, default=None, help="override the workload's step count")
     ap.add_argument("--n-E", type=int, default=None, help="override the workload's energy count")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="under torchrun: weak = one batch per rank (seed base + rank); strong = one batch "
+                         "split into contiguous trajectory shards, spectra combined by one all-reduce")
     ap.add_argument("--amplitude", default="ta", choices=["ta", "hk"],
                     help="ta: time-averaged spectrum (Eq. I(E)_discreto); hk: plain Herman-Kluk SC-IVR "
                          "spectrum (Eq. I(E)_SCIVR)")
@@ -752,13 +779,19 @@ def main(argv=None):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w8 = sized(workload(args.workload, seed=rank), args)   # weak scaling: one batch per rank
+    # weak scaling: one batch per rank (seed base + rank); strong scaling: one batch (seed 0)
+    # whose trajectories are split into contiguous shards, one per rank
+    strong = args.scaling == "strong" and world > 1
+    w8 = sized(workload(args.workload, seed=0 if strong else rank), args)
+    n_job = w8.n_traj
+    lo, hi = shards.shard_range(n_job, rank, world) if strong else (0, n_job)
+    n = hi - lo                                  # this rank's trajectories
     pes = scivr.scivr_create_pes(w8.pes)
-    bufs = scivr.alloc_buffers(w8, device=dev)
+    bufs = scivr.alloc_buffers(w8, device=dev, n_traj=n)
+    full = scivr.alloc_buffers(w8.with_(n_steps=1, n_E=2), device=dev) if strong else None   # the job's samples
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     K = w8.n_steps + 1
-    n = w8.n_traj
 
     prec = PRECISIONS[args.precision]
     hk = args.amplitude == "hk"
@@ -777,8 +810,17 @@ def main(argv=None):
     combined = [None]
 
     def one_step(record):
-        scivr.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], n, w8.seed, bufs.p0,
-                                   bufs.q0, bufs.w, stream)
+        if strong:
+            # the whole job's Husimi samples (the same Philox stream on every rank), then this
+            # rank's contiguous shard
+            scivr.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], n_job, w8.seed, full.p0,
+                                       full.q0, full.w, stream)
+            bufs.p0.copy_(full.p0[:, lo:hi])
+            bufs.q0.copy_(full.q0[:, lo:hi])
+            bufs.w.copy_(full.w[lo:hi])
+        else:
+            scivr.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], n, w8.seed, bufs.p0,
+                                       bufs.q0, bufs.w, stream)
         if record:
             e0 = torch.cuda.Event(enable_timing=True); e0.record(stream); ev["prop0"].append(e0)
         scivr.scivr_propagate(pes, w8.dt, w8.n_steps, w8.gamma, w8.p_eq, w8.q_eq, n, bufs.p0, bufs.q0,
@@ -855,7 +897,8 @@ def main(argv=None):
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e_ms = float(te.item()) / args.steps
-        e2e = {"value": world * n * w8.n_steps / (e2e_ms * 1e-3), "unit": "trajectory-steps/s",
+        e2e = {"value": (n_job if strong else world * n) * w8.n_steps / (e2e_ms * 1e-3),
+               "unit": "trajectory-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": e2e_ms}
 
@@ -895,7 +938,7 @@ def main(argv=None):
         }
         del ref
 
-    value = world * n * w8.n_steps / (ms_per_step * 1e-3)
+    value = (n_job if strong else world * n) * w8.n_steps / (ms_per_step * 1e-3)
     prop_avg = float(np.mean(prop_ms))
     spec_avg = float(np.mean(spec_ms))
     # time-averaged: 8 N K N_E (complex multiply-add per trajectory, sample and energy);
@@ -906,14 +949,32 @@ def main(argv=None):
     ft_tf = ft_flops / (spec_avg * 1e-3) / 1e12
     pr_tf = pr_flops / (prop_avg * 1e-3) / 1e12
     peaks = measured_peaks()
-    fp64_peak = FP64_PEAK_GFLOPS / 1e3
+    probe = fma_peaks(stream)                 # untimed: the FP32 / FP64 pipes' attainable rates
+    fp64_peak = probe["fp64"]
+    fp32_peak = probe["fp32"]
+    probe_note = (f"measured live by scivr_fma_probe (independent FMA chains on every SM): FP32 "
+                  f"{fp32_peak:.1f}, FP64 {fp64_peak:.3f} TFLOP/s of measured")
     full = args.n_traj is None and args.n_steps is None and args.n_E is None
     if spec_avg >= prop_avg:
-        if ftm == 0:
+        if ftm == 4:
+            # chirp-z: per good trajectory and energy block two length-L FFTs (5 L log2 L flops each
+            # for complex radix-2) and three complex products per point (input chirp, spectrum of
+            # the chirp, |y|^2)
+            L_czt = 8192
+            nb = L_czt - K + 1
+            n_blk = -(-w8.n_E // nb)
+            czt_flops = n_good * n_blk * (2 * 5 * L_czt * 13 + 3 * 6 * L_czt)
+            a = czt_flops / (spec_avg * 1e-3) / 1e12
+            roof = {"kernel": "k_czt (scivr_spectrum, FP64 chirp-z)", "bound": "alu", "achieved": a,
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": a / fp64_peak, "traffic": None,
+                    "peak_source": probe_note,
+                    "note": "achieved counts the transform's own FFT flops (10 L log2 L + 18 L per good "
+                            "trajectory and energy block, L = 8192), not the direct sum's 8 N K N_E"}
+        elif ftm == 0:
             roof = {"kernel": "k_ft_fp64 (scivr_spectrum)", "bound": "alu", "achieved": ft_tf,
                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": ft_tf / fp64_peak,
                     "traffic": TRAFFIC.get(("k_ft_fp64", args.workload)) if full else None,
-                    "peak_source": FP64_PEAK_NOTE}
+                    "peak_source": probe_note}
         else:
             pk = float(peaks.get("bf16_tflops", 1900.0))
             roof = {"kernel": f"k_ft_tc<{ftm}> (scivr_spectrum, {args.ft})", "bound": "tensor",
@@ -927,19 +988,20 @@ def main(argv=None):
         if prec == 0:
             roof = {"kernel": "k_propagate (scivr_propagate, fp64)", "bound": "alu", "achieved": pr_tf,
                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": pr_tf / fp64_peak, "traffic": None,
-                    "peak_source": FP64_PEAK_NOTE}
+                    "peak_source": probe_note}
         else:
             # two pipes: the FP32 bulk at the FP32 peak plus the FP64-kept part at the FP64 peak
-            t_bound = (bulk * n * w8.n_steps) / (FP32_PEAK_GFLOPS * 1e9) + \
-                      (kept * n * w8.n_steps) / (FP64_PEAK_GFLOPS * 1e9)
+            t_bound = (bulk * n * w8.n_steps) / (fp32_peak * 1e12) + \
+                      (kept * n * w8.n_steps) / (fp64_peak * 1e12)
             eff_peak = pr_flops / t_bound / 1e12
+            tr = TRAFFIC.get(("k_propagate_lg_mixed", args.workload))
             roof = {"kernel": "k_propagate_lg<float> (scivr_propagate, mixed)", "bound": "alu",
                     "achieved": pr_tf, "peak": eff_peak, "unit": "TFLOP/s", "frac": pr_tf / eff_peak,
-                    "traffic": None,
-                    "peak_source": (f"two-pipe bound: FP32 bulk {bulk:.0f} flop/step at "
-                                    f"{FP32_PEAK_GFLOPS / 1e3:.1f} TFLOP/s + FP64-kept {kept:.0f} "
-                                    f"flop/step at {fp64_peak} TFLOP/s (FP32 peak = 152 SMs x 128 "
-                                    f"lanes x 2 x 2.07 GHz; FMA probe measured 73.3)")}
+                    "traffic": tr * n * w8.n_steps if (tr is not None and full) else None,
+                    "peak_source": (f"two-pipe bound: FP32 bulk {bulk:.0f} flop/step at {fp32_peak:.1f} "
+                                    f"TFLOP/s + FP64-kept {kept:.0f} flop/step at {fp64_peak:.3f} TFLOP/s, "
+                                    f"both {probe_note.split(': ', 1)[0]}"),
+                    "nominal_fp32_peak": FP32_PEAK_GFLOPS / 1e3}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -952,18 +1014,21 @@ def main(argv=None):
     line = {
         "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision] + ("" if ftm == 0 else f" + {args.ft} tensor FT"),
+        "higher_is_better": True, "scaling": "strong" if strong else "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision] + ("" if ftm == 0 else f" + {args.ft} FT"),
         "data": "synthetic",
-        "config": {"workload": describe(w8, args.precision, args.ft, args.amplitude), "global_batch": world * n,
-                   "seed": "base 0 + rank",
+        "config": {"workload": describe(w8, args.precision, args.ft, args.amplitude),
+                   "global_batch": n_job if strong else world * n,
+                   "seed": "0, one batch split into trajectory shards" if strong else "base 0 + rank",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); amplitudes "
                          f"({n * K * 16 / 1e9:.2f} GB) exceed L2",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": (f"trajectory shards x{world} (one all-reduce of n_E + 1 numbers)" if strong
+                                   else f"replicas x{world}")},
         "spectra_per_s": world / (ms_per_step * 1e-3),
         "propagate_ms": prop_avg, "spectrum_ms": spec_avg, "n_good": n_good,
         "propagate_tflops": pr_tf, "spectrum_tflops": ft_tf,
         "roofline": roof,
+        "fma_probe_tflops": probe,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "accuracy": accuracy,

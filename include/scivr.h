@@ -380,6 +380,15 @@ int scivr_check_status(void *stream);
  * SCIVR_ETIMEOUT.  seconds must lie in (0, 10]. */
 int scivr_selftest_wait_timeout(double seconds, void *stream);
 
+/* Arithmetic-rate probe (measurement, no counterpart in the paper): launches
+ * independent fused multiply-add chains on every SM, in FP32 (precision SCIVR_MIXED)
+ * or FP64 (SCIVR_FP64), each thread iters x 16 FMAs; *flops_per_launch (host)
+ * receives 2 x the FMAs of the launch.  The caller times the launch on `stream`;
+ * flops / time is the pipe's attainable rate, the denominator of the propagation
+ * kernels' roofline.  Errors: SCIVR_EINVAL (precision, iters < 1, NULL output),
+ * SCIVR_ECUDA. */
+int scivr_fma_probe(int32_t precision, int64_t iters, double *flops_per_launch, void *stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *scivr_last_error(void);
 

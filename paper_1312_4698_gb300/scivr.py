@@ -128,7 +128,18 @@ EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_s
             "scivr_mlp_param_count", "scivr_pes_set_mlp", "scivr_mlp_eval", "scivr_mlp_get_params",
             "scivr_mlp_set_params", "scivr_mlp_loss_grad", "scivr_mlp_adamw", "scivr_pes_eval",
             "scivr_normal_modes", "scivr_normal_to_cartesian", "scivr_cartesian_to_normal",
-            "scivr_create_pes_cartesian"]
+            "scivr_create_pes_cartesian", "scivr_fma_probe"]
+
+
+_lib.scivr_fma_probe.restype = C.c_int
+_lib.scivr_fma_probe.argtypes = [_i32, _i64, C.POINTER(_d), _vp]
+
+
+def scivr_fma_probe(precision, iters, stream=None) -> float:
+    """Launch the FMA-rate probe on `stream`; returns the launch's flops."""
+    f = _d()
+    _check(_lib.scivr_fma_probe(int(precision), int(iters), C.byref(f), _stream(stream)), "scivr_fma_probe")
+    return f.value
 
 
 def scivr_check_status(stream=None) -> int:
