@@ -19,6 +19,7 @@ S = "tests/test_oracle_spectrum.py::"
 H = "tests/test_oracle_hk.py::"
 E = "tests/test_oracle_pes.py::"
 N = "tests/test_oracle_mlp.py::"
+CA = "tests/test_oracle_cartesian.py::"
 
 # name: ([(exact source text, replacement), ...], [pins that must fail])
 MUTANTS = {
@@ -125,6 +126,21 @@ MUTANTS = {
           "double complex lo = or_log_overlap(F, prm->gamma, prm->p_eq,\n"
           "                                                   prm->q_eq, p, q);")],
         [H + "test_reference_states_share_trajectories_sampled_around_the_first"]),
+    "Cartesian bend gradient with the wrong sign": (
+        [("const double gi = c->k_bend * dc * dcy[i];", "const double gi = -c->k_bend * dc * dcy[i];")],
+        [CA + "test_cartesian_derivatives_match_finite_differences"]),
+    "Cartesian bond Hessian without its transverse part": (
+        [("f1 * ((d == f ? 1.0 : 0.0) - w[d] * w[f] / ww) / r", "0.0 * f1")],
+        [CA + "test_cartesian_derivatives_match_finite_differences"]),   # zero at the minimum: FD off it
+    "normal modes of the Hessian without mass weighting": (
+        [("A[i * 9 + j] = Hx[i * 9 + j] / sqrt(c->mass[i / 3] * c->mass[j / 3]);", "A[i * 9 + j] = Hx[i * 9 + j];")],
+        [CA + "test_normal_mode_frequencies_match_the_wilson_gf_closed_form"]),
+    "mode matrix not divided by the square root of the mass": (
+        [("c->Lm[i * 3 + m] = sgn * Vm[i * 9 + col] / sqrt(c->mass[i / 3]);", "c->Lm[i * 3 + m] = sgn * Vm[i * 9 + col];")],
+        [CA + "test_mode_matrix_is_mass_orthonormal_and_free_of_rigid_motions"]),
+    "Jacobi rotation of the columns with the wrong sign": (
+        [("A[k * 9 + p] = cs * akp - sn * akq;", "A[k * 9 + p] = cs * akp + sn * akq;")],
+        [CA + "test_normal_mode_frequencies_match_the_wilson_gf_closed_form"]),
     "gradient-matching term of the training gradient halved": (
         [("u[i] = 2.0 * beta * e / (double)n;", "u[i] = beta * e / (double)n;")],
         [N + "test_training_gradient_vs_finite_differences"]),
