@@ -341,6 +341,18 @@ int scivr_batch_launch(scivr_batch b, void *stream);
 int scivr_batch_info(scivr_batch b, int32_t g, int32_t *n_groups, int32_t *F, int32_t *precision,
                      int32_t *warps);
 
+/* The plan's propagation schedule: *one_launch = 1 when every mixed-precision
+ * molecule runs in one persistent launch (the multi-F kernel: CTAs of four warps pull
+ * (molecule, trajectory tile) items of all classes from one list, costliest first, and
+ * run the body specialised for each item's F; built when every class is one of 3, 6, 9,
+ * 12, 15, 24 and there are at least two), 0 when each F-class has its own persistent
+ * launch.  scivr_batch_create picks by timing both on a probe of the plan (32 steps,
+ * up to 2048 trajectories per molecule); the environment variable SCIVR_BATCH_SCHEDULE
+ * = "one" or "per-class" forces the choice.  Above F = 9 the one launch reads the
+ * coupling tensors from L2, so those molecules' results may differ in rounding from
+ * their per-class runs.  Errors: SCIVR_EINVAL (NULL arguments). */
+int scivr_batch_schedule(scivr_batch b, int32_t *one_launch);
+
 /* Free a plan (synchronises the device).  NULL is accepted. */
 int scivr_batch_destroy(scivr_batch b);
 

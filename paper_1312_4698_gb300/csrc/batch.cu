@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <cstdint>
 #include <map>
 #include <mutex>
 #include <string>
@@ -153,6 +154,128 @@ cudaError_t choose_warps(const PropLaunch &L, int precision, int n_sm, int *warp
     return cudaSuccess;
 }
 
+// Relative cost of one trajectory-step at F (the dominant terms of the step's work: the
+// quartic Hessian contraction and the monodromy kicks), for ordering work items.
+double step_cost(int F)
+{
+    const double P = F * (F + 1) / 2.0;
+    return 6.0 * P * P + 12.0 * F * F * (double)F;
+}
+
+// (record, tile) items of the one-launch schedule, the costliest tiles first.
+std::vector<int2> multi_work(const std::vector<PropLaunch> &recs)
+{
+    std::vector<int2> w;
+    for (int k = 0; k < (int)recs.size(); ++k) {
+        const int per_tile = multi_launch_tile(recs[k].args.F);
+        const int tiles = (int)((recs[k].n_traj + per_tile - 1) / per_tile);
+        for (int t = 0; t < tiles; ++t) w.push_back(make_int2(k, t));
+    }
+    std::stable_sort(w.begin(), w.end(), [&](const int2 &a, const int2 &b) {
+        const PropLaunch &A = recs[a.x], &Bm = recs[b.x];
+        return A.args.n_steps * step_cost(A.args.F) * multi_launch_tile(A.args.F) >
+               Bm.args.n_steps * step_cost(Bm.args.F) * multi_launch_tile(Bm.args.F);
+    });
+    return w;
+}
+
+// Time the two schedules of a plan's mixed molecules on a probe (at most 32 steps and
+// 2048 trajectories per molecule, amplitudes into a probe buffer): the per-class
+// persistent launches one after the other, and the one-launch schedule.  true if the
+// one launch is faster.
+cudaError_t one_launch_is_faster(const std::vector<PropLaunch> &recs, const std::vector<int> &warps_of_rec,
+                                 int n_sm, bool *faster)
+{
+    std::vector<PropLaunch> P = recs;
+    size_t amp_bytes = 0;
+    for (auto &L : P) {
+        L.args.n_steps = std::min(L.args.n_steps, 32);
+        L.n_traj = std::min<int64_t>(L.n_traj, 2048);
+        L.amp_ld = L.args.n_steps + 1;
+        L.chi_stride = L.n_traj * L.amp_ld;
+        L.fin = FinalDev{};
+        amp_bytes += ((sizeof(double2) * (size_t)L.args.n_chi * L.chi_stride + (size_t)L.n_traj) + 255) & ~(size_t)255;
+    }
+    // per-class work lists of the probe
+    std::map<int, std::vector<int>> cls;
+    for (int k = 0; k < (int)P.size(); ++k) cls[P[k].args.F].push_back(k);
+    std::vector<int2> mw = multi_work(P);
+    size_t bytes = amp_bytes + sizeof(PropLaunch) * P.size() + sizeof(int2) * (mw.size() + 16) * 2 + 4096 +
+                   256 * cls.size();
+    for (auto &c : cls) {
+        const int per_tile = warps_of_rec[c.second[0]] * (32 / mixed_group_lanes(c.first));
+        size_t n = 0;
+        for (int k : c.second) n += (P[k].n_traj + per_tile - 1) / per_tile;
+        bytes += sizeof(int2) * n + sizeof(PropLaunch) * c.second.size() + 512;
+    }
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, bytes);
+    if (e != cudaSuccess) return e;
+    char *b = static_cast<char *>(mem);
+    for (auto &L : P) {
+        L.amp = reinterpret_cast<double2 *>(b);
+        b += sizeof(double2) * (size_t)L.args.n_chi * L.chi_stride;
+        L.good = reinterpret_cast<uint8_t *>(b);
+        b += ((size_t)L.n_traj + 255) & ~(size_t)255;
+        b = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(b) + 255) & ~(uintptr_t)255);
+    }
+    auto put = [&](const void *src, size_t n) -> void * {
+        void *dst = b;
+        b = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(b + n) + 255) & ~(uintptr_t)255);
+        if (e == cudaSuccess) e = cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+        return dst;
+    };
+    auto *d_all = static_cast<PropLaunch *>(put(P.data(), sizeof(PropLaunch) * P.size()));
+    auto *d_mw = static_cast<int2 *>(put(mw.data(), sizeof(int2) * mw.size()));
+    struct ClassProbe { PropLaunch *items; int2 *work; int n_work; int warps; int F; };
+    std::vector<ClassProbe> cps;
+    for (auto &c : cls) {
+        std::vector<PropLaunch> rr;
+        for (int k : c.second) rr.push_back(P[k]);
+        const int warps = warps_of_rec[c.second[0]];
+        const int per_tile = warps * (32 / mixed_group_lanes(c.first));
+        std::vector<int2> w;
+        for (int k = 0; k < (int)rr.size(); ++k)
+            for (int t = 0; t < (int)((rr[k].n_traj + per_tile - 1) / per_tile); ++t) w.push_back(make_int2(k, t));
+        ClassProbe cp;
+        cp.items = static_cast<PropLaunch *>(put(rr.data(), sizeof(PropLaunch) * rr.size()));
+        cp.work = static_cast<int2 *>(put(w.data(), sizeof(int2) * w.size()));
+        cp.n_work = (int)w.size();
+        cp.warps = warps;
+        cp.F = c.first;
+        cps.push_back(cp);
+    }
+    int *counters = reinterpret_cast<int *>(b);   // one per class + one for the one launch
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float t_class = 1e30f, t_one = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        float t = 0.0f;
+        e = cudaMemset(counters, 0, sizeof(int) * (cps.size() + 1));
+        if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+        for (size_t i = 0; i < cps.size() && e == cudaSuccess; ++i)
+            e = launch_group_batch_mixed(cps[i].F, cps[i].warps, cps[i].items, cps[i].work, cps[i].n_work,
+                                         counters + i, n_sm, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && rep > 0) t_class = std::min(t_class, t);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+        if (e == cudaSuccess)
+            e = launch_group_batch_multi(d_all, d_mw, (int)mw.size(), counters + cps.size(), n_sm, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && rep > 0) t_one = std::min(t_one, t);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(mem);
+    *faster = t_one < t_class;
+    return e;
+}
+
 }  // namespace
 
 struct scivr_batch_s {
@@ -164,6 +287,13 @@ struct scivr_batch_s {
     int n_sm = 0;
     void *blob = nullptr;                 // work lists, launch records, counters
     void *scratch = nullptr;              // Fourier scratch for the largest molecule
+    // one persistent launch for every mixed molecule (when their F classes allow it)
+    bool one_launch = false;
+    PropLaunch *m_items = nullptr;
+    int2 *m_work = nullptr;
+    int m_n_work = 0;
+    int *m_counter = nullptr;
+    void *m_blob = nullptr;
 };
 
 extern "C" {
@@ -267,10 +397,48 @@ int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t f
         if (e == cudaSuccess)
             e = cudaMemcpy(g.d_work, works[gi].data(), sizeof(int2) * works[gi].size(), cudaMemcpyHostToDevice);
     }
+    // one persistent launch for every mixed molecule: built when every mixed class is one the
+    // multi-F kernel holds; taken when SCIVR_BATCH_SCHEDULE says "one", or, unless it says
+    // "per-class", when the probe finds it faster
+    bool multi_ok = B->groups.size() > 1;
+    for (const Group &g : B->groups) multi_ok = multi_ok && multi_launch_holds(g.F);
+    if (e == cudaSuccess && multi_ok) {
+        std::vector<PropLaunch> recs;
+        std::vector<int> warps_of_rec;
+        for (const Group &g : B->groups)
+            for (int m : g.members) {
+                recs.push_back(B->launches[m]);
+                warps_of_rec.push_back(g.warps);
+            }
+        const char *sched = std::getenv("SCIVR_BATCH_SCHEDULE");
+        bool one = false;
+        if (sched && std::strcmp(sched, "one") == 0) one = true;
+        else if (!(sched && std::strcmp(sched, "per-class") == 0)) e = one_launch_is_faster(recs, warps_of_rec, B->n_sm, &one);
+        if (e == cudaSuccess && one) {
+            std::vector<int2> mw = multi_work(recs);
+            const size_t nb = ((sizeof(PropLaunch) * recs.size() + 255) & ~(size_t)255) +
+                              ((sizeof(int2) * mw.size() + 255) & ~(size_t)255) + 256;
+            e = cudaMalloc(&B->m_blob, nb);
+            if (e == cudaSuccess) {
+                char *mb = static_cast<char *>(B->m_blob);
+                B->m_items = reinterpret_cast<PropLaunch *>(mb);
+                mb += (sizeof(PropLaunch) * recs.size() + 255) & ~(size_t)255;
+                B->m_work = reinterpret_cast<int2 *>(mb);
+                mb += (sizeof(int2) * mw.size() + 255) & ~(size_t)255;
+                B->m_counter = reinterpret_cast<int *>(mb);
+                B->m_n_work = (int)mw.size();
+                e = cudaMemcpy(B->m_items, recs.data(), sizeof(PropLaunch) * recs.size(), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(B->m_work, mw.data(), sizeof(int2) * mw.size(), cudaMemcpyHostToDevice);
+                B->one_launch = e == cudaSuccess;
+            }
+        }
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         if (B->blob) cudaFree(B->blob);
         if (B->scratch) cudaFree(B->scratch);
+        if (B->m_blob) cudaFree(B->m_blob);
         delete B;
         return cuda_error(e, "scivr_batch_create: device setup");
     }
@@ -285,7 +453,15 @@ int scivr_batch_launch(scivr_batch B, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     int launches = 0;
+    if (B->one_launch) {
+        e = cudaMemsetAsync(B->m_counter, 0, sizeof(int), s);
+        if (e == cudaSuccess)
+            e = launch_group_batch_multi(B->m_items, B->m_work, B->m_n_work, B->m_counter, B->n_sm, s);
+        if (e != cudaSuccess) return cuda_error(e, "scivr_batch_launch: one-launch propagation");
+        ++launches;
+    }
     for (const Group &g : B->groups) {
+        if (B->one_launch) break;
         e = cudaMemsetAsync(g.d_counter, 0, sizeof(int), s);
         if (e == cudaSuccess)
             e = launch_group_batch_mixed(g.F, g.warps, g.d_items, g.d_work, g.n_work, g.d_counter, B->n_sm, s);
@@ -337,12 +513,21 @@ int scivr_batch_info(scivr_batch B, int32_t g, int32_t *n_groups, int32_t *F, in
     return SCIVR_OK;
 }
 
+int scivr_batch_schedule(scivr_batch B, int32_t *one_launch)
+{
+    if (!B || !one_launch) return set_error(SCIVR_EINVAL, "scivr_batch_schedule: NULL argument");
+    *one_launch = B->one_launch ? 1 : 0;
+    clear_error();
+    return SCIVR_OK;
+}
+
 int scivr_batch_destroy(scivr_batch B)
 {
     if (!B) { clear_error(); return SCIVR_OK; }
     cudaError_t e = cudaDeviceSynchronize();
     if (B->blob) cudaFree(B->blob);
     if (B->scratch) cudaFree(B->scratch);
+    if (B->m_blob) cudaFree(B->m_blob);
     delete B;
     if (e != cudaSuccess) return cuda_error(e, "scivr_batch_destroy: synchronize");
     clear_error();

@@ -35,6 +35,7 @@
 
 #include <math_constants.h>
 #include <cstddef>
+#include <algorithm>
 #include <utility>
 #include <type_traits>
 
@@ -298,14 +299,14 @@ __device__ __forceinline__ void dot16_2x2(const float *u, const float *v, const 
 // Coupling tensors staged per CTA, transposed so that one potential entry e
 // reads one contiguous row: sT3[e][k] (k < F, stride S3), sT4[e][kl] (kl < P,
 // stride S4), zero-padded.
-template <int F, typename Real>
+template <int F, typename Real, bool STAGED = (F <= 16)>
 struct TensorLayout {
     static constexpr int P = F * (F + 1) / 2;
     static constexpr int S3 = vec_len<Real>(F);   // short rows: fewer loads outweigh a 2-way conflict
     static constexpr int S4 = row_stride<Real>(P);
     // Above F = 16 the quartic tensor (P^2 entries, 360 KB at F = 24) does not fit shared
     // memory: both tensors are read from global memory (L2) and only the coefficients are staged.
-    static constexpr bool staged = F <= 16;
+    static constexpr bool staged = STAGED;
     // after the tensors: the Herman-Kluk matrix coefficients acoef[a][b][4] =
     // (1/2) {rg_a/rg_b, rg_b/rg_a, -rg_a rg_b, 1/(rg_a rg_b)}, rg = sqrt(gamma)
     static constexpr size_t bytes =
@@ -338,7 +339,7 @@ struct WarpShared {
 // Called by the per-molecule kernel (cta = blockIdx.x) and by the batched
 // persistent kernel (cta = the work item's tile).  Stages the molecule's
 // constants itself and leaves shared memory free for the next call.
-template <int F, int G, typename Real, int WARPS>
+template <int F, int G, typename Real, int WARPS, bool STAGED = (F <= 16)>
 __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsigned char *smem_raw)
 {
     constexpr int N2 = 2 * F;
@@ -352,7 +353,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     using Sh = WarpShared<F, G, Real>;
     using R2 = typename Vec2<Real>::T;
 
-    using TL = TensorLayout<F, Real>;
+    using TL = TensorLayout<F, Real, STAGED>;
     constexpr int S3 = TL::S3, S4 = TL::S4;
     Real *sT3 = reinterpret_cast<Real *>(smem_raw);
     Real *sT4 = sT3 + (TL::staged ? P * S3 : 0);
@@ -441,14 +442,15 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         ea[i] = a;
         eb[i] = a + e;
     }
-    // two trajectories per warp (16-lane groups, mixed path): lane ln computes entries 2 ln and
-    // 2 ln + 1 for both trajectories (register blocking; P <= 64)
+    // two trajectories per warp (16-lane groups, mixed path): lane ln computes entries ln and
+    // ln + 32 for both trajectories (register blocking; P <= 64).  Consecutive lanes read
+    // consecutive tensor rows, whose odd vector stride keeps them in different banks.
     constexpr bool kBlocked = (T == 2) && (sizeof(Real) == 4) && TL::staged && (P <= 64) && (P > 16);
     int ebA[2] = {0, 0}, ebB[2] = {0, 0};
     if constexpr (kBlocked) {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-            int e = 2 * ln + i, a = 0;
+            int e = ln + 32 * i, a = 0;
             if (e >= P) e = 0;
             while (e >= F - a) { e -= F - a; ++a; }
             ebA[i] = a;
@@ -604,7 +606,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         }
                     }
                 } else if constexpr (kBlocked) {
-                    const int e0 = 2 * ln, e1 = e0 + 1 < P ? e0 + 1 : e0;
+                    const int e0 = ln, e1 = ln + 32 < P ? ln + 32 : ln;
                     float v[2] = {0.0f, 0.0f};   // energy parts of trajectories 0 and 1
                     if (e0 < P) {
                         float h3[4] = {0.f, 0.f, 0.f, 0.f}, h4[4] = {0.f, 0.f, 0.f, 0.f};   // (e0,t0) (e0,t1) (e1,t0) (e1,t1)
@@ -612,7 +614,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         if (use4) dot16_2x2<S4>(sT4 + e0 * S4, sT4 + e1 * S4, sh.qq[0], sh.qq[1], h4);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const int i = q >> 1, tt = q & 1, e = e0 + i;
+                            const int i = q >> 1, tt = q & 1, e = ln + 32 * i;
                             if (e < P) {
                                 const int a = ebA[i], b = ebB[i];
                                 const float h = h3[q] + h4[q];
@@ -1194,13 +1196,40 @@ __global__ void __launch_bounds__(32 * WARPS, lg_min_ctas<F, G, Real>()) k_propa
     }
 }
 
+// One persistent launch for molecules of several F: CTAs of four warps pull (molecule,
+// tile) work items from one list (all molecules, sorted by decreasing cost) and run the
+// body specialised for each item's F.  Above F = 9 the coupling tensors are read from L2
+// here, so that no class's shared memory sets the whole launch's occupancy.
+template <int... Fs>
+__global__ void __launch_bounds__(128, 1) k_propagate_lg_multi(const PropLaunch *__restrict__ items,
+                                                               const int2 *__restrict__ work, int n_work,
+                                                               int *__restrict__ counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int next;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = next;
+        __syncthreads();
+        if (w >= n_work) break;
+        const int2 it = work[w];
+        const int F = items[it.x].args.F;
+        const bool ran = ((F == Fs ? (lg_body<Fs, mixed_group_lanes(Fs), float, 4, (Fs <= 9)>(items[it.x], it.y, smem_raw),
+                                      true)
+                                   : false) ||
+                          ...);
+        (void)ran;
+    }
+}
+
 }  // namespace lg
 
-template <int F, int G, typename Real, int WARPS>
+template <int F, int G, typename Real, int WARPS, bool STAGED = (F <= 16)>
 size_t lg_smem_bytes()
 {
     using namespace lg;
-    const size_t tensors = TensorLayout<F, Real>::bytes;
+    const size_t tensors = TensorLayout<F, Real, STAGED>::bytes;
     const size_t consts = (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
     return tensors + consts + WARPS * sizeof(WarpShared<F, G, Real>);
 }
@@ -1273,6 +1302,37 @@ cudaError_t launch_group_batch_mixed_F(int warps, const PropLaunch *items, const
     }
     return cudaErrorInvalidValue;
 }
+
+// The classes one persistent launch can hold, and the trajectories per work tile of each.
+template <int... Fs>
+struct MultiLaunch {
+    static constexpr bool holds(int F) { return ((F == Fs) || ...); }
+    static size_t smem_bytes()
+    {
+        size_t m = 0;
+        ((m = std::max(m, lg_smem_bytes<Fs, mixed_group_lanes(Fs), float, 4, (Fs <= 9)>())), ...);
+        return m;
+    }
+    static cudaError_t launch(const PropLaunch *items, const int2 *work, int n_work, int *counter, int n_sm,
+                              cudaStream_t s)
+    {
+        const size_t bytes = smem_bytes();
+        auto kern = lg::k_propagate_lg_multi<Fs...>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, bytes);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        int grid = n_sm * per_sm;
+        if (grid > n_work) grid = n_work;
+        if (grid < 1) return cudaSuccess;
+        kern<<<grid, 128, bytes, s>>>(items, work, n_work, counter);
+        return cudaGetLastError();
+    }
+};
 
 template <int F> cudaError_t launch_group_fp64(const PropLaunch &L, cudaStream_t s)
 {

@@ -150,6 +150,11 @@ int cuda_error(cudaError_t e, const char *where);
 cudaError_t launch_group_batch_mixed(int F, int warps, const PropLaunch *items, const int2 *work, int n_work,
                                      int *counter, int n_sm, cudaStream_t s);
 int batch_warp_candidates(int F, int *out);   // returns the count (<= 2)
+// One persistent launch for molecules of several F (the batch recipe's classes).
+bool multi_launch_holds(int F);
+int multi_launch_tile(int F);                  // trajectories per work item
+cudaError_t launch_group_batch_multi(const PropLaunch *items, const int2 *work, int n_work, int *counter, int n_sm,
+                                     cudaStream_t s);
 
 // Lanes per trajectory of the mixed-precision lane-group kernels: every mode and at
 // most two monodromy columns per lane -- 8 lanes up to F = 4, 16 up to F = 9 (at F = 9

@@ -110,6 +110,8 @@ _lib.scivr_batch_launch.argtypes = [_vp, _vp]
 _lib.scivr_batch_launch.restype = C.c_int
 _lib.scivr_batch_info.argtypes = [_vp, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)]
 _lib.scivr_batch_info.restype = C.c_int
+_lib.scivr_batch_schedule.argtypes = [_vp, C.POINTER(_i32)]
+_lib.scivr_batch_schedule.restype = C.c_int
 _lib.scivr_batch_destroy.argtypes = [_vp]
 _lib.scivr_batch_destroy.restype = C.c_int
 _lib.scivr_check_status.argtypes = [_vp]
@@ -128,7 +130,7 @@ EXPORTED = ["scivr_create_pes", "scivr_destroy_pes", "scivr_pes_modes", "scivr_s
             "scivr_mlp_param_count", "scivr_pes_set_mlp", "scivr_mlp_eval", "scivr_mlp_get_params",
             "scivr_mlp_set_params", "scivr_mlp_loss_grad", "scivr_mlp_adamw", "scivr_pes_eval",
             "scivr_normal_modes", "scivr_normal_to_cartesian", "scivr_cartesian_to_normal",
-            "scivr_create_pes_cartesian", "scivr_fma_probe"]
+            "scivr_create_pes_cartesian", "scivr_fma_probe", "scivr_batch_schedule"]
 
 
 _lib.scivr_fma_probe.restype = C.c_int
@@ -404,6 +406,12 @@ class Batch:
     def __init__(self, handle, keep):
         self.handle = handle
         self._keep = keep
+
+    def one_launch(self) -> bool:
+        """True when every mixed-precision molecule runs in one persistent launch."""
+        v = _i32()
+        _check(_lib.scivr_batch_schedule(self.handle, C.byref(v)), "scivr_batch_schedule")
+        return bool(v.value)
 
     def groups(self):
         n = _i32()

@@ -115,6 +115,53 @@ def test_batch_of_every_recipe_f_matches_per_molecule_runs(G):
         assert torch.equal(e["bufs"].amp, amp) and torch.equal(e["bufs"].I, I)
 
 
+def test_batch_one_persistent_launch_across_f_classes(G, monkeypatch):
+    """The one-launch schedule (SCIVR_BATCH_SCHEDULE=one): every molecule of F = 3..24 in one
+    persistent kernel that dispatches on each work item's F.  Up to F = 9 (coupling tensors
+    in shared memory in both schedules) and at F = 24 (in L2 in both) the results equal the
+    per-molecule runs bit for bit; at F = 12 and 15 the one launch reads the tensors from
+    L2, so amplitudes agree to rounding (within 1e-5 of each row's largest) and spectra to
+    1e-6.  A captured graph replays the plan bit for bit."""
+    import torch
+    mols = [_molecules()[i] for i in (0, 1, 2, 6, 7, 8)]
+    entries = _setup(G, mols, [1] * len(mols))
+    monkeypatch.setenv("SCIVR_BATCH_SCHEDULE", "one")
+    plan = G.scivr_batch_create(entries, ft_mode=2)
+    assert plan.one_launch()
+    G.scivr_batch_launch(plan)
+    torch.cuda.synchronize()
+    assert G.scivr_check_status() == G.SCIVR_OK
+    for e in entries:
+        amp, good, I, ng = _reference(G, e, 2)
+        b = e["bufs"]
+        F = e["wl"].F
+        if F <= 9 or F == 24:
+            assert torch.equal(b.good, good) and torch.equal(b.amp, amp) and torch.equal(b.I, I), F
+        else:
+            assert torch.equal(b.good, good), F
+            a1 = b.amp[0].cpu().numpy()
+            a0 = amp[0].cpu().numpy()
+            z1, z0 = a1[..., 0] + 1j * a1[..., 1], a0[..., 0] + 1j * a0[..., 1]
+            sel = good.cpu().numpy().astype(bool)
+            err = np.max(np.abs(z1[sel] - z0[sel]) / np.max(np.abs(z0[sel]), axis=-1, keepdims=True))
+            eI = float(torch.max(torch.abs(b.I - I)) / torch.max(torch.abs(I)))
+            print(f"F={F}: one launch vs per-class amplitudes {err:.2e}, spectrum {eI:.2e}")
+            assert err < 1e-5 and eI < 1e-6
+    eager = [(e["bufs"].amp.clone(), e["bufs"].I.clone()) for e in entries]
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(graph, stream=side):
+        G.scivr_batch_launch(plan, stream=side)
+    for e in entries:
+        e["bufs"].amp.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for e, (amp, I) in zip(entries, eager):
+        assert torch.equal(e["bufs"].amp, amp) and torch.equal(e["bufs"].I, I)
+    monkeypatch.setenv("SCIVR_BATCH_SCHEDULE", "per-class")
+    assert not G.scivr_batch_create(entries, ft_mode=2).one_launch()
+
+
 def test_batch_fp64_item_matches_oracle(G):
     import torch
     mols = _molecules()[:3]
