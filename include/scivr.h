@@ -233,11 +233,16 @@ int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
  * p0, q0: device [F][n_traj].  amp: device complex double (re, im interleaved)
  * [n_chi][n_traj][amp_ld], amp_ld >= n_steps + 1, 16-byte aligned.  good:
  * device [n_traj].  fin: host struct of optional device outputs (NULL = none).
- * Precision SCIVR_MIXED keeps the monodromy, the potential, det M and the
- * elimination that gives det A in FP32 (positions, momenta, action and phase in
- * FP64), so its det M deviation is FP32 rounding: give it a stab_tol scaled
- * accordingly.  Built: SCIVR_FP64 for F <= 9 (both schedules), SCIVR_MIXED for
- * F <= 16 (lane-group schedule; one trajectory per warp above F = 9).
+ * Precision SCIVR_MIXED keeps the monodromy, the potential and det M in FP32
+ * (positions, momenta, action and phase in FP64; the elimination that gives
+ * det A in double-FP32 pairs, pivot product and argument in FP64), so its det M
+ * deviation is FP32 rounding: give it a stab_tol scaled accordingly.  The mixed
+ * path tests det M every 16 steps and at the last step (FP64: every step).
+ * Built: SCIVR_FP64 for F <= 9 (both schedules), SCIVR_MIXED for F <= 24
+ * (lane-group schedule; one trajectory per warp above F = 9, two column
+ * groups per trajectory and tensors read from L2 above F = 16).  A surface of
+ * kind SCIVR_PES_CART3 (scivr_create_pes_cartesian) runs on SCIVR_FP64 with the
+ * thread schedule only.
  * Errors: SCIVR_EINVAL (NULL pointers, n_traj < 1, n_steps < 1, dt <= 0,
  * gamma <= 0, amp_ld too small, F mismatch, n_chi out of range),
  * SCIVR_EUNSUPPORTED (precision or kernel not built for this F). */
@@ -326,7 +331,7 @@ typedef struct scivr_batch_s *scivr_batch;   /* opaque plan, library-owned */
  * buffers are not touched until scivr_batch_launch.  ft_mode as for
  * scivr_spectrum.  Synchronises the device.  Errors: SCIVR_EINVAL (any item
  * invalid; the message names it), SCIVR_EUNSUPPORTED (precision not built
- * for the item's F: mixed above F = 16, FP64 above F = 9), SCIVR_ENOMEM, SCIVR_ECUDA. */
+ * for the item's F: mixed above F = 24, FP64 above F = 9), SCIVR_ENOMEM, SCIVR_ECUDA. */
 int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t ft_mode,
                        scivr_batch *out);
 
