@@ -47,7 +47,10 @@ FP64_PEAK_NOTE = ("GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table
 # dram read+write bytes per launch from ncu captures (profiles/), keyed by (kernel, workload);
 # scaled to the full launch where the capture used fewer trajectories
 TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9, ("k_ft_tc2", "f6"): 7.98e9,
-           ("k_mlp_fused", "f9mlp"): 0.914e6 * 8}
+           ("k_mlp_fused", "f9mlp"): 0.914e6 * 8,
+           # per trajectory-step (the bench multiplies by trajectories x steps): one launch of
+           # 65536 trajectories x 400 steps read 17.06 MB and wrote 364.34 MB
+           ("k_propagate_lg_mixed", "f9"): (17.06e6 + 364.34e6) / (65536 * 400)}
 
 
 # trajectories of the oracle's timed sample per workload (10-30 s of host work on 16 cores),
@@ -84,32 +87,40 @@ def describe(w8, precision="fp64", ft="fp64", amplitude="ta"):
             f"{w8.n_E} energies, propagation {precision}, {spec}")
 
 
-def propagate_flops_per_traj_step(F: int, n3: int, n4: int) -> float:
+def propagate_flops_per_traj_step(F: int, n3: int, n4: int, mixed: bool = False) -> float:
     """Algorithmic flops of one trajectory step (multiply-add = 2 flops).
 
     3 kicks: potential (pair products P, cubic Hessian P*F and quartic
     Hessian P*P multiply-adds, gradient and energy 2P each, Morse diagonal ~6F)
     and the monodromy kick M_p -= tau H M_q (2F * F * F multiply-adds);
     4 drifts: q and M_q (F + 2F*F multiply-adds) and the kinetic action (F);
-    det M by LU of 2F x 2F ((2/3)(2F)^3 flops), det A by complex LU of F x F
+    det M by LU of 2F x 2F ((2/3)(2F)^3 flops; the mixed path does it every
+    16 steps, the FP64 path every step), det A by complex LU of F x F
     (8/3 F^3 real flops) plus building A (6 F^2), phase (~30) and the
     amplitude per reference state (~10 F + 30)."""
-    fp32, fp64 = propagate_flops_split(F, n3, n4)
+    fp32, fp64 = propagate_flops_split(F, n3, n4, mixed)
     return fp32 + fp64
 
 
-def propagate_flops_split(F: int, n3: int, n4: int):
-    """(bulk, fp64-kept) split of propagate_flops_per_traj_step: in the mixed path
-    the bulk runs on the FP32 pipe -- potential, monodromy, det M, building A, the
-    elimination that gives det A, the overlap and the kinetic action increments --
-    and the p and q updates (3 kicks x 2F + 4 drifts x 2F flops), the action sum,
-    the continuous-phase scan and the phase sum with its reduction modulo 2 pi
-    (~11 flops) stay FP64."""
+DET_M_EVERY_MIXED = 16   # stability-test cadence of the mixed path (steps)
+
+
+def propagate_flops_split(F: int, n3: int, n4: int, mixed: bool = False):
+    """(bulk, fp64-kept) split of propagate_flops_per_traj_step.  Mixed path:
+    everything runs on the FP32 pipe -- in FP32 the potential, monodromy, det M,
+    building A, the overlap and the kinetic action increments; in double-FP32
+    pairs the elimination that gives det A and the p, q and action updates,
+    counted here at their algorithmic flops (the FP32 instructions that emulate
+    FP64-class arithmetic show up as lost efficiency) -- except the
+    continuous-phase scan and the phase sum with its reduction modulo 2 pi
+    (~11 flops), which stay FP64.  FP64 path: all of it is FP64 (the split is
+    then only informative)."""
     P = F * (F + 1) // 2
     pes = 2 * (P + (P * F if n3 else 0) + (P * P if n4 else 0) + 4 * P) + 6 * F
-    total = (3 * (pes + 2 * (2 * F * F * F)) + 4 * (2 * 2 * F * F) + (2.0 / 3.0) * (2 * F) ** 3 + 6 * F * F
+    det_m = (2.0 / 3.0) * (2 * F) ** 3 / (DET_M_EVERY_MIXED if mixed else 1)
+    total = (3 * (pes + 2 * (2 * F * F * F)) + 4 * (2 * 2 * F * F) + det_m + 6 * F * F
              + (8.0 / 3.0) * F ** 3 + 3 * (2 * F + 2) + 4 * (2 * F + 2 * F) + 30 + 10 * F + 30)
-    kept = 14.0 * F + 11.0
+    kept = 11.0 if mixed else 14.0 * F + 11.0
     return total - kept, kept
 
 
@@ -352,7 +363,7 @@ def batch_arm(args):
     t_bound = 0.0
     probe = fma_peaks()
     for w8 in mols:
-        bulk, kept = propagate_flops_split(w8.F, w8.pes.c3.size, w8.pes.c4.size)
+        bulk, kept = propagate_flops_split(w8.F, w8.pes.c3.size, w8.pes.c4.size, mixed=(prec != 0))
         flops += (bulk + kept) * w8.n_traj * w8.n_steps
         t_bound += (bulk * w8.n_traj * w8.n_steps) / (probe["fp32"] * 1e12) + \
                    (kept * w8.n_traj * w8.n_steps) / (probe["fp64"] * 1e12)
@@ -944,7 +955,7 @@ def main(argv=None):
     # time-averaged: 8 N K N_E (complex multiply-add per trajectory, sample and energy);
     # plain HK: the column sum (2 N K) and the transform of the mean (8 K N_E)
     ft_flops = (2.0 * n * K + 8.0 * K * w8.n_E) if hk else 8.0 * n * K * w8.n_E
-    bulk, kept = propagate_flops_split(w8.F, w8.pes.c3.size, w8.pes.c4.size)
+    bulk, kept = propagate_flops_split(w8.F, w8.pes.c3.size, w8.pes.c4.size, mixed=(prec != 0))
     pr_flops = (bulk + kept) * n * w8.n_steps
     ft_tf = ft_flops / (spec_avg * 1e-3) / 1e12
     pr_tf = pr_flops / (prop_avg * 1e-3) / 1e12

@@ -122,10 +122,12 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
     for (int i = 0; i < 4; ++i) {
         A.tdrift[i] = A.cdrift[i] * prm->dt;
         A.tdrift_f[i] = (float)A.tdrift[i];
+        A.tdrift_lo[i] = (float)(A.tdrift[i] - (double)A.tdrift_f[i]);
     }
     for (int i = 0; i < 3; ++i) {
         A.tkick[i] = A.dkick[i] * prm->dt;
         A.tkick_f[i] = (float)A.tkick[i];
+        A.tkick_lo[i] = (float)(A.tkick[i] - (double)A.tkick_f[i]);
     }
     A.stab_tol_f = prm->stab_tol > 3.0e38 ? 3.0e38f : (float)prm->stab_tol;
     double ref = 0.0;

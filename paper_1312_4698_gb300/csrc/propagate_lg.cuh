@@ -160,6 +160,53 @@ __device__ __forceinline__ ff ff_recip(ff m)
     return ff_norm(y0, y0 * r);
 }
 
+// Positions, momenta and the action: FP64 in the FP64 path, double-FP32 pairs in the
+// mixed path (FP64-class accuracy, about 2^-46 relative per operation, on the FP32 pipe:
+// on this GPU an FP64 instruction or conversion costs the FP64 pipe ~70 times the issue
+// of an FP32 one).  coord_axpy: c + t x; coord_kick: c - t g for an FP32 force g; t is
+// given as FP64 (td) and as FP32 leading and trailing words (th, tl).
+__device__ __forceinline__ void coord_set(double &c, double x) { c = x; }
+__device__ __forceinline__ void coord_set(ff &c, double x)
+{
+    c.hi = (float)x;
+    c.lo = (float)(x - (double)c.hi);
+}
+__device__ __forceinline__ double coord_get(double c) { return c; }
+__device__ __forceinline__ double coord_get(ff c) { return (double)c.hi + (double)c.lo; }
+__device__ __forceinline__ double coord_f(double c) { return c; }
+__device__ __forceinline__ float coord_f(ff c) { return c.hi; }
+__device__ __forceinline__ bool coord_finite(double c) { return isfinite(c); }
+__device__ __forceinline__ bool coord_finite(ff c) { return isfinite(c.hi) && isfinite(c.lo); }
+__device__ __forceinline__ double coord_axpy(double c, double td, float, float, double x) { return fma(td, x, c); }
+__device__ __forceinline__ ff coord_axpy(ff c, double, float th, float tl, ff x)
+{
+    const float p = th * x.hi;
+    float e = fmaf(th, x.hi, -p);   // th x.hi - p, exact
+    e = fmaf(th, x.lo, e);
+    e = fmaf(tl, x.hi, e);
+    float s, e2;
+    ff_two_sum(c.hi, p, s, e2);
+    return ff_norm(s, e2 + (c.lo + e));
+}
+__device__ __forceinline__ double coord_kick(double c, double td, float, float, double g) { return fma(-td, g, c); }
+__device__ __forceinline__ ff coord_kick(ff c, double, float th, float tl, float g)
+{
+    const float p = -th * g;
+    float e = fmaf(-th, g, -p);
+    e = fmaf(-tl, g, e);
+    float s, e2;
+    ff_two_sum(c.hi, p, s, e2);
+    return ff_norm(s, e2 + (c.lo + e));
+}
+// the action increment (FP32 partial sums) joins the running action
+__device__ __forceinline__ double coord_add(double c, double d) { return c + d; }
+__device__ __forceinline__ ff coord_add(ff c, float d)
+{
+    float s, e;
+    ff_two_sum(c.hi, d, s, e);
+    return ff_norm(s, e + c.lo);
+}
+
 // Per-mode and per-reference-state constants, staged in shared memory so that
 // lane- or chi-dependent indexing never touches the kernel-parameter space.
 template <int F>
@@ -211,8 +258,18 @@ template <int F, int G, typename Real> __host__ __device__ constexpr int lg_chun
 template <int F, int G> __host__ __device__ constexpr int lg_warps() { return G < 32 ? 4 : (F <= 9 ? 2 : (F <= 12 ? 8 : 4)); }
 // (F > 16: 4 warps, one CTA per SM: 18 KB of per-job prefactor matrices and 9 KB of det M
 // workspace per warp at F = 24)
+// Two-trajectory mixed warps (F = 6..9) hold the coupling tensors in registers (fewer
+// shared-memory wavefronts, more registers: lg_min_ctas) or read them from shared memory.
+// Measured on the recipe surfaces: registers win at F = 7 (6 %) and F = 8 (13 %: the
+// shared-memory schedule there is held to 128 registers by its four CTAs per SM and spills;
+// at three CTAs it is still 15 % slower); shared memory wins at F = 6 (5 %, four CTAs per SM
+// against three) and at F = 9 (5 %, three against two).
+template <int F> __host__ __device__ constexpr bool lg_tensor_regs() { return F == 7 || F == 8; }
+
 template <int F, int G, typename Real> __host__ __device__ constexpr int lg_min_ctas()
 {
+    // register-held tensors: two CTAs per SM at F = 8, 9 (up to 255 registers), three at F = 6, 7
+    if constexpr (sizeof(Real) == 4 && G == 16 && F >= 6 && lg_tensor_regs<F>()) return F >= 8 ? 2 : 3;
     return F > 9 ? 1 : (sizeof(Real) == 4 && 2 * F > G ? 3 : 4);
 }
 
@@ -244,14 +301,30 @@ __host__ __device__ constexpr int row_stride(int n)
     return (vec_len<Real>(n) / V16<Real>::N) % 2 == 0 ? vec_len<Real>(n) + V16<Real>::N : vec_len<Real>(n);
 }
 
+// Packed FP32 multiply-add on register pairs (one instruction, two lanes of work).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+
 // sum_{i < S} a[i] b[i] over 16-byte aligned shared rows (S a multiple of the
-// vector length) with one partial sum per vector lane.
+// vector length) with one partial sum per vector lane (FP32: packed pairs).
 template <typename Real, int S>
 __device__ __forceinline__ Real dot16(const Real *a, const Real *b)
 {
     using VT = typename V16<Real>::T;
     constexpr int N = V16<Real>::N;
     static_assert(S % N == 0, "padded length");
+    if constexpr (sizeof(Real) == 4) {
+        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
+#pragma unroll
+        for (int i = 0; i < S; i += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(a + i);
+            const float4 y = *reinterpret_cast<const float4 *>(b + i);
+            a0 = ffma2(lo2(x), lo2(y), a0);
+            a1 = ffma2(hi2(x), hi2(y), a1);
+        }
+        return (a0.x + a1.x) + (a0.y + a1.y);
+    }
     Real acc[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) acc[j] = Real(0);
@@ -276,24 +349,20 @@ __device__ __forceinline__ void dot16_2x2(const float *u, const float *v, const 
                                           float (&out)[4])
 {
     static_assert(S % 4 == 0, "padded length");
-    float acc[4][2];
+    float2 acc[4];   // packed partial sums: even and odd elements
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q][0] = acc[q][1] = 0.0f;
+    for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int i = 0; i < S; i += 4) {
         const float4 uu = *reinterpret_cast<const float4 *>(u + i), vv = *reinterpret_cast<const float4 *>(v + i);
         const float4 xx = *reinterpret_cast<const float4 *>(x + i), yy = *reinterpret_cast<const float4 *>(y + i);
-        acc[0][0] = fmaf(uu.x, xx.x, acc[0][0]); acc[0][1] = fmaf(uu.y, xx.y, acc[0][1]);
-        acc[0][0] = fmaf(uu.z, xx.z, acc[0][0]); acc[0][1] = fmaf(uu.w, xx.w, acc[0][1]);
-        acc[1][0] = fmaf(uu.x, yy.x, acc[1][0]); acc[1][1] = fmaf(uu.y, yy.y, acc[1][1]);
-        acc[1][0] = fmaf(uu.z, yy.z, acc[1][0]); acc[1][1] = fmaf(uu.w, yy.w, acc[1][1]);
-        acc[2][0] = fmaf(vv.x, xx.x, acc[2][0]); acc[2][1] = fmaf(vv.y, xx.y, acc[2][1]);
-        acc[2][0] = fmaf(vv.z, xx.z, acc[2][0]); acc[2][1] = fmaf(vv.w, xx.w, acc[2][1]);
-        acc[3][0] = fmaf(vv.x, yy.x, acc[3][0]); acc[3][1] = fmaf(vv.y, yy.y, acc[3][1]);
-        acc[3][0] = fmaf(vv.z, yy.z, acc[3][0]); acc[3][1] = fmaf(vv.w, yy.w, acc[3][1]);
+        acc[0] = ffma2(lo2(uu), lo2(xx), acc[0]); acc[0] = ffma2(hi2(uu), hi2(xx), acc[0]);
+        acc[1] = ffma2(lo2(uu), lo2(yy), acc[1]); acc[1] = ffma2(hi2(uu), hi2(yy), acc[1]);
+        acc[2] = ffma2(lo2(vv), lo2(xx), acc[2]); acc[2] = ffma2(hi2(vv), hi2(xx), acc[2]);
+        acc[3] = ffma2(lo2(vv), lo2(yy), acc[3]); acc[3] = ffma2(hi2(vv), hi2(yy), acc[3]);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = acc[q][0] + acc[q][1];
+    for (int q = 0; q < 4; ++q) out[q] = acc[q].x + acc[q].y;
 }
 
 // Coupling tensors staged per CTA, transposed so that one potential entry e
@@ -323,6 +392,11 @@ struct WarpShared {
     static constexpr int SH = vec_len<Real>(F);            // row stride of H (rows read by the whole group)
     alignas(16) Real qr[T][S3];
     alignas(16) Real qq[T][S4];
+    // x = (q, zero pad to an even length, pair products, zero pad) in two halves of KH for the
+    // register-held tensor rows of two-trajectory warps (see lg_body)
+    static constexpr int F3E = (F + 1) & ~1;
+    static constexpr int KH = (((F3E + P + 1) / 2) + 3) & ~3;
+    alignas(16) Real xs[T][2 * KH];
     alignas(16) Real Gc[T][F][S3];          // gradient coefficients, full symmetric matrix (row a read by mode lane a)
     alignas(16) Real H[T][F][SH];
     typename AEntry<Real>::T A[F * F][JOBS]; // prefactor matrix per job, entry-major (job column swizzled)
@@ -442,19 +516,57 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         ea[i] = a;
         eb[i] = a + e;
     }
-    // two trajectories per warp (16-lane groups, mixed path): lane ln computes entries ln and
-    // ln + 32 for both trajectories (register blocking; P <= 64).  Consecutive lanes read
-    // consecutive tensor rows, whose odd vector stride keeps them in different banks.
-    constexpr bool kBlocked = (T == 2) && (sizeof(Real) == 4) && TL::staged && (P <= 64) && (P > 16);
-    int ebA[2] = {0, 0}, ebB[2] = {0, 0};
+    // two trajectories per warp (16-lane groups, mixed path, P <= 64): the coupling tensors
+    // live in registers.  x = (q, qq) is cut into two halves of KH elements; lane ln holds,
+    // for its half hx = ln / 16, the matching parts of the tensor rows of the entries
+    // jx + 16 i (jx = ln % 16, i < EPH), and multiplies them by both trajectories' halves of
+    // x (read as warp-broadcast 16-byte loads).  Lanes ln and ln ^ 16 then exchange partial
+    // sums so that each ends with whole entries of its own trajectory.
+    constexpr bool kPair = (T == 2) && (sizeof(Real) == 4) && TL::staged && (P <= 64) && (P > 16);
+    constexpr bool kTreg = kPair && lg_tensor_regs<F>();
+    // otherwise (kBlocked) lane ln computes entries ln and ln + 32 for both trajectories from
+    // the staged rows (register blocking: each loaded row element feeds two products);
+    // consecutive lanes read consecutive rows, whose odd vector stride keeps them in
+    // different banks
+    constexpr bool kBlocked = kPair && !kTreg;
+    int bA[2] = {0, 0}, bB[2] = {0, 0};
     if constexpr (kBlocked) {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             int e = ln + 32 * i, a = 0;
             if (e >= P) e = 0;
             while (e >= F - a) { e -= F - a; ++a; }
+            bA[i] = a;
+            bB[i] = a + e;
+        }
+    }
+    constexpr int F3E = Sh::F3E, KH = Sh::KH;
+    constexpr int EPH = kTreg ? (P + 15) / 16 : 1;
+    const int hx = ln >> 4, jx = ln & 15;
+    int ebA[EPH], ebB[EPH];
+    float2 Tr[EPH][kTreg ? KH / 2 : 1];
+    if constexpr (kTreg) {
+#pragma unroll
+        for (int i = 0; i < EPH; ++i) {
+            const int e0 = jx + 16 * i;
+            int e = e0 < P ? e0 : 0, a = 0;
+            while (e >= F - a) { e -= F - a; ++a; }
             ebA[i] = a;
             ebB[i] = a + e;
+#pragma unroll
+            for (int k2 = 0; k2 < KH / 2; ++k2) {
+                float v[2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int gk = hx * KH + 2 * k2 + c;   // position in x
+                    v[c] = 0.0f;
+                    if (e0 < P) {
+                        if (gk < F) v[c] = sT3[e0 * S3 + gk];
+                        else if (gk >= F3E && gk - F3E < P) v[c] = sT4[e0 * S4 + gk - F3E];
+                    }
+                }
+                Tr[i][k2] = make_float2(v[0], v[1]);
+            }
         }
     }
     // above F = 16: four consecutive entries 4 (g + i G) .. + 3 per load, (a, b) packed as a | b << 8
@@ -473,9 +585,26 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 
     // mode state (lane g < F)
     const int mode = g < F ? g : 0;
-    double p = L.p0[mode * n + jl], q = L.q0[mode * n + jl];
-    Real pr = (Real)p;          // the momentum as seen by the Real-precision bulk
-    double S = 0.0;             // accumulated action (lane 0 of the group holds the total)
+    using Coord = std::conditional_t<sizeof(Real) == 4, ff, double>;
+    Coord p, q;
+    coord_set(p, L.p0[mode * n + jl]);
+    coord_set(q, L.q0[mode * n + jl]);
+    Real pr = (Real)coord_get(p);   // the momentum as seen by the Real-precision bulk
+    Coord S;                        // accumulated action (lane 0 of the group holds the total)
+    coord_set(S, 0.0);
+    // per-job action in the job table: FP64, or the double-FP32 pair in the same 8 bytes
+    auto sj_put = [&](int j, Coord v) {
+        if constexpr (sizeof(Real) == 4) reinterpret_cast<float2 *>(sh.Sj)[j] = make_float2(v.hi, v.lo);
+        else sh.Sj[j] = v;
+    };
+    auto sj_get = [&](int j) -> double {
+        if constexpr (sizeof(Real) == 4) {
+            const float2 v = reinterpret_cast<const float2 *>(sh.Sj)[j];
+            return (double)v.x + (double)v.y;
+        } else {
+            return sh.Sj[j];
+        }
+    };
     // column state: slot s of lane g holds column c = g + s G of M = d(p,q)/d(p0,q0) (c < 2F;
     // a slot past 2F holds a zero column)
     Real Mp[NCOL][F], Mq[NCOL][F];
@@ -535,13 +664,27 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     Real rt;
                     if constexpr (sizeof(Real) == 4) rt = A.tdrift_f[sub]; else rt = A.tdrift[sub];
                     if (g < F) {
-                        q = fma(A.tdrift[sub], p, q);
+                        q = coord_axpy(q, A.tdrift[sub], A.tdrift_f[sub], A.tdrift_lo[sub], p);
                         dS = fma(rt * Real(0.5) * pr, pr, dS);
                     }
+                    if constexpr (sizeof(Real) == 4) {
+                        const float2 rt2 = make_float2(rt, rt);
 #pragma unroll
-                    for (int s = 0; s < NCOL; ++s)
+                        for (int s = 0; s < NCOL; ++s) {
 #pragma unroll
-                        for (int a = 0; a < F; ++a) Mq[s][a] = fma(rt, Mp[s][a], Mq[s][a]);
+                            for (int a = 0; a + 1 < F; a += 2) {
+                                const float2 r = ffma2(rt2, make_float2(Mp[s][a], Mp[s][a + 1]), make_float2(Mq[s][a], Mq[s][a + 1]));
+                                Mq[s][a] = r.x;
+                                Mq[s][a + 1] = r.y;
+                            }
+                            if constexpr (F % 2) Mq[s][F - 1] = fmaf(rt, Mp[s][F - 1], Mq[s][F - 1]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s)
+#pragma unroll
+                            for (int a = 0; a < F; ++a) Mq[s][a] = fma(rt, Mp[s][a], Mq[s][a]);
+                    }
                 }
                 if (sub == 3) break;
                 // kick: potential at q
@@ -549,12 +692,19 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 Real rtk;
                 if constexpr (sizeof(Real) == 4) rtk = A.tkick_f[sub]; else rtk = tk;
                 __syncwarp();   // previous kick's readers of qr/H are done
-                if (g < F) sh.qr[t][g] = (Real)q;
+                if (g < F) {
+                    sh.qr[t][g] = (Real)coord_f(q);
+                    if constexpr (kTreg) sh.xs[t][g] = (Real)coord_f(q);
+                }
                 __syncwarp();
 #pragma unroll
                 for (int i = 0; i < EPL; ++i) {
                     const int e = g + i * G;
-                    if (e < P) sh.qq[t][e] = sh.qr[t][ea[i]] * sh.qr[t][eb[i]];
+                    if (e < P) {
+                        const Real v = sh.qr[t][ea[i]] * sh.qr[t][eb[i]];
+                        sh.qq[t][e] = v;
+                        if constexpr (kTreg) sh.xs[t][F3E + e] = v;
+                    }
                 }
                 __syncwarp();
                 Real vpart = Real(0);
@@ -568,14 +718,15 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     for (int i = 0; i < NQ; ++i) {
                         const int q4 = g + i * G;
                         if (4 * q4 < P) {
-                            float4 h3 = make_float4(0.f, 0.f, 0.f, 0.f), h4 = h3;
+                            float2 h3a = make_float2(0.f, 0.f), h3b = h3a, h4a = h3a, h4b = h3a;
                             if (use3) {
 #pragma unroll 8
                                 for (int k = 0; k < F; ++k) {
                                     const float4 tv = __ldg(T3v + k * (P4 / 4) + q4);
                                     const float x = sh.qr[t][k];
-                                    h3.x = fmaf(tv.x, x, h3.x); h3.y = fmaf(tv.y, x, h3.y);
-                                    h3.z = fmaf(tv.z, x, h3.z); h3.w = fmaf(tv.w, x, h3.w);
+                                    const float2 x2 = make_float2(x, x);
+                                    h3a = ffma2(lo2(tv), x2, h3a);
+                                    h3b = ffma2(hi2(tv), x2, h3b);
                                 }
                             }
                             if (use4) {
@@ -583,10 +734,12 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                                 for (int kl = 0; kl < P; ++kl) {
                                     const float4 tv = __ldg(T4v + kl * (P4 / 4) + q4);
                                     const float x = sh.qq[t][kl];
-                                    h4.x = fmaf(tv.x, x, h4.x); h4.y = fmaf(tv.y, x, h4.y);
-                                    h4.z = fmaf(tv.z, x, h4.z); h4.w = fmaf(tv.w, x, h4.w);
+                                    const float2 x2 = make_float2(x, x);
+                                    h4a = ffma2(lo2(tv), x2, h4a);
+                                    h4b = ffma2(hi2(tv), x2, h4b);
                                 }
                             }
+                            const float4 h3 = make_float4(h3a.x, h3a.y, h3b.x, h3b.y), h4 = make_float4(h4a.x, h4a.y, h4b.x, h4b.y);
                             const float h3j[4] = {h3.x, h3.y, h3.z, h3.w}, h4j[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
@@ -605,6 +758,69 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                             }
                         }
                     }
+                } else if constexpr (kTreg) {
+                    float2 aF[EPH][2], a4[EPH][2];   // packed partial sums per entry and trajectory
+                    float sF[EPH][2];                // the first F3E elements of x (q in half 0)
+#pragma unroll
+                    for (int i = 0; i < EPH; ++i)
+#pragma unroll
+                        for (int tt = 0; tt < 2; ++tt) aF[i][tt] = a4[i][tt] = make_float2(0.0f, 0.0f);
+                    const float *x0 = &sh.xs[0][hx * KH], *x1 = &sh.xs[1][hx * KH];
+#pragma unroll
+                    for (int c = 0; c < KH; c += 4) {
+                        const float4 u = *reinterpret_cast<const float4 *>(x0 + c);
+                        const float4 w = *reinterpret_cast<const float4 *>(x1 + c);
+#pragma unroll
+                        for (int hp = 0; hp < 2; ++hp) {
+                            const int kk = c + 2 * hp;
+                            const float2 xu = hp ? hi2(u) : lo2(u), xw = hp ? hi2(w) : lo2(w);
+#pragma unroll
+                            for (int i = 0; i < EPH; ++i) {
+                                if (kk < F3E) {
+                                    aF[i][0] = ffma2(Tr[i][kk / 2], xu, aF[i][0]);
+                                    aF[i][1] = ffma2(Tr[i][kk / 2], xw, aF[i][1]);
+                                } else {
+                                    a4[i][0] = ffma2(Tr[i][kk / 2], xu, a4[i][0]);
+                                    a4[i][1] = ffma2(Tr[i][kk / 2], xw, a4[i][1]);
+                                }
+                            }
+                            if (kk + 2 == F3E) {
+#pragma unroll
+                                for (int i = 0; i < EPH; ++i)
+#pragma unroll
+                                    for (int tt = 0; tt < 2; ++tt) sF[i][tt] = aF[i][tt].x + aF[i][tt].y;
+                            }
+                        }
+                    }
+                    // half 0 holds the cubic rows (h3) and the first pair products; half 1 only
+                    // pair products.  Keep trajectory hx, pass the partner its trajectory's sums.
+                    float vp = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < EPH; ++i) {
+                        float s3[2], s4[2];
+#pragma unroll
+                        for (int tt = 0; tt < 2; ++tt) {
+                            const float r = a4[i][tt].x + a4[i][tt].y;
+                            s3[tt] = hx == 0 ? sF[i][tt] : 0.0f;
+                            s4[tt] = hx == 0 ? r : sF[i][tt] + r;
+                        }
+                        const float o3 = __shfl_xor_sync(FULL, hx ? s3[0] : s3[1], 16);
+                        const float o4 = __shfl_xor_sync(FULL, hx ? s4[0] : s4[1], 16);
+                        const float h3 = (hx ? s3[1] : s3[0]) + o3, h4 = (hx ? s4[1] : s4[0]) + o4;
+                        const int e = jx + 16 * i;
+                        if (e < P) {
+                            const int a = ebA[i], b = ebB[i];
+                            const float h = h3 + h4;
+                            sh.H[hx][a][b] = h;
+                            sh.H[hx][b][a] = h;
+                            const float gce = fmaf(0.5f, h3, h4 * (1.0f / 3.0f));
+                            sh.Gc[hx][a][b] = gce;
+                            sh.Gc[hx][b][a] = gce;
+                            const float vc = fmaf(1.0f / 6.0f, h3, h4 * (1.0f / 12.0f));
+                            vp = fmaf(a == b ? vc : 2.0f * vc, sh.qq[hx][e], vp);
+                        }
+                    }
+                    vpart = vp;   // lane ln belongs to group hx = t
                 } else if constexpr (kBlocked) {
                     const int e0 = ln, e1 = ln + 32 < P ? ln + 32 : ln;
                     float v[2] = {0.0f, 0.0f};   // energy parts of trajectories 0 and 1
@@ -616,7 +832,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         for (int q = 0; q < 4; ++q) {
                             const int i = q >> 1, tt = q & 1, e = ln + 32 * i;
                             if (e < P) {
-                                const int a = ebA[i], b = ebB[i];
+                                const int a = bA[i], b = bB[i];
                                 const float h = h3[q] + h4[q];
                                 sh.H[tt][a][b] = h;
                                 sh.H[tt][b][a] = h;
@@ -671,14 +887,39 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         hd = w2;
                     }
                     sh.H[t][g][g] += hd;
-                    p = fma(-tk, (double)(gr + gd), p);
-                    pr = (Real)p;
+                    p = coord_kick(p, tk, A.tkick_f[sub], A.tkick_lo[sub], gr + gd);
+                    pr = (Real)coord_f(p);
                     vlane += Vd;
                 }
                 __syncwarp();   // H complete before the monodromy kick reads it
                 dS = fma(-rtk, vlane, dS);
                 // monodromy kick: M_p -= tau H M_q (column lanes; rows of H by 16-byte broadcast loads)
-                {
+                if constexpr (sizeof(Real) == 4) {
+                    // packed pairs of H's row entries against pairs of the column's entries
+                    constexpr int SH = Sh::SH;
+#pragma unroll
+                    for (int a = 0; a < F; ++a) {
+                        float2 acc[NCOL];
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s) acc[s] = make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int b0 = 0; b0 < SH; b0 += 4) {
+                            const float4 v = *reinterpret_cast<const float4 *>(&sh.H[t][a][b0]);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int b = b0 + 2 * h;
+                                const float2 hv = h ? hi2(v) : lo2(v);
+#pragma unroll
+                                for (int s = 0; s < NCOL; ++s) {
+                                    if (b + 1 < F) acc[s] = ffma2(hv, make_float2(Mq[s][b], Mq[s][b + 1]), acc[s]);
+                                    else if (b < F) acc[s].x = fmaf(hv.x, Mq[s][b], acc[s].x);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int s = 0; s < NCOL; ++s) Mp[s][a] = fmaf(-rtk, acc[s].x + acc[s].y, Mp[s][a]);
+                    }
+                } else {
                     using VT = typename V16<Real>::T;
                     constexpr int NV = V16<Real>::N, SH = Sh::SH;
 #pragma unroll
@@ -813,20 +1054,20 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 }
                 if (g < F) {
                     sh.pj[g][jswz<JOBS>(g, job)] = pr;   // p did not change since the last kick set pr
-                    sh.qj[g][jswz<JOBS>(g, job)] = (Real)q;
+                    sh.qj[g][jswz<JOBS>(g, job)] = (Real)coord_f(q);
                 }
                 // the step's action increment, summed over the group, joins the FP64 action
 #pragma unroll
                 for (int o = G / 2; o > 0; o >>= 1) dS += __shfl_xor_sync(FULL, dS, o, G);
                 if (g == 0) {
-                    S += (double)dS;
-                    sh.Sj[job] = S;
+                    S = coord_add(S, dS);
+                    sj_put(job, S);
                 }
             }
         }
         {
             // non-finite state persists, so testing once per chunk marks the same trajectories
-            const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(isfinite(p) && isfinite(q)));
+            const unsigned bad_bits = __ballot_sync(FULL, (g < F) && !(coord_finite(p) && coord_finite(q)));
             const unsigned gmask = (G == 32 ? FULL : (((1u << G) - 1u) << base));
             if (bad_bits & gmask) good = false;
         }
@@ -865,7 +1106,10 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 if (pos < PPW) perm0 = (perm0 & ~(PMASK << (PB * pos))) | (v << (PB * pos));
                 else perm1 = (perm1 & ~(PMASK << (PB * (pos - PPW)))) | (v << (PB * (pos - PPW)));
             };
-            double dr = 1.0, di = 0.0;   // det A, the product of the pivots in FP64
+            // det A, the product of the pivots: double-FP32 (re, im) times 2^dexp, renormalised by
+            // an exact power of two after every factor (the FP32 exponent range alone could overflow)
+            ff dr = {1.0f, 0.0f}, di = {0.0f, 0.0f};
+            int dexp = 0;
 #pragma unroll 1
             for (int k = 0; k < F; ++k) {
                 // pivot: the largest |a_ik|^2 (leading words) over the active rows
@@ -889,17 +1133,23 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     const unsigned long long a = (unsigned long long)prow(k), b = (unsigned long long)prow(bpos);
                     pset(k, b);
                     pset(bpos, a);
-                    dr = -dr;
-                    di = -di;
+                    dr = {-dr.hi, -dr.lo};
+                    di = {-di.hi, -di.lo};
                 }
                 const int pr = prow(k);
                 const float4 pk4 = at(pr * F + k);
                 const ff pre = {pk4.x, pk4.y}, pim = {pk4.z, pk4.w};
                 {
-                    const double kr = (double)pre.hi + (double)pre.lo, ki = (double)pim.hi + (double)pim.lo;
-                    const double nr = fma(dr, kr, -di * ki), ni = fma(dr, ki, di * kr);
-                    dr = nr;
-                    di = ni;
+                    const ff a1 = ff_mul(dr, pre), a2 = ff_mul(di, pim), b1 = ff_mul(dr, pim), b2 = ff_mul(di, pre);
+                    dr = ff_add(a1, {-a2.hi, -a2.lo});
+                    di = ff_add(b1, b2);
+                    const float m = fmaxf(fabsf(dr.hi), fabsf(di.hi));
+                    const int eb = (__float_as_int(m) >> 23) & 255;   // biased exponent of the larger part
+                    if (eb > 0 && eb < 255) {
+                        const float sc = __int_as_float((254 - eb) << 23);   // 2^(127 - eb): the larger part to [1, 2)
+                        dr.hi *= sc; dr.lo *= sc; di.hi *= sc; di.lo *= sc;
+                        dexp += eb - 127;
+                    }
                 }
                 // 1 / pivot = conj(pivot) / |pivot|^2
                 const ff m2 = ff_add(ff_mul(pre, pre), ff_mul(pim, pim));
@@ -933,9 +1183,10 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 if (LPJ > 1) __syncwarp();   // rows updated by the job's other lanes feed the next pivot
             }
             if (r == 0) {
-                sh.argj[job] = atan2(di, dr);
-                sh.detAj[job] = make_double2(dr, di);
-                if (A.amplitude == SCIVR_AMP_HK) sh.lnA[job] = 0.5 * log(hypot(dr, di));
+                const double mr = (double)dr.hi + (double)dr.lo, mi = (double)di.hi + (double)di.lo;
+                sh.argj[job] = atan2(mi, mr);   // the power of two does not change the argument
+                sh.detAj[job] = make_double2(ldexp(mr, dexp), ldexp(mi, dexp));
+                if (A.amplitude == SCIVR_AMP_HK) sh.lnA[job] = 0.5 * (log(hypot(mr, mi)) + dexp * 0.69314718055994530942);
             }
             __syncwarp();
             if (jvalid) {
@@ -1081,7 +1332,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         if (!isfinite(theta_last)) good = false;
         // ---------------- phase 4: amplitudes (job-parallel) ----------------
         if (jvalid && active) {
-            const double S = sh.Sj[jb];
+            const double S = sj_get(jb);
             for (int x = 0; x < A.n_chi; ++x) {
                 if constexpr (sizeof(Real) == 4) {
                     // the overlap's exponent and phase are O(1)-O(10) in size: FP32 from the FP32
@@ -1133,7 +1384,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 }
             }
         }
-        if (!isfinite(sh.Sj[t * C + cnt - 1])) good = false;
+        if (!isfinite(sj_get(t * C + cnt - 1))) good = false;
         __syncwarp();
     }
 
@@ -1141,11 +1392,11 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     if (g == 0) L.good[jl] = good ? 1 : 0;
     const FinalDev &fo = L.fin;
     if (g < F) {
-        if (fo.p) fo.p[g * n + jl] = p;
-        if (fo.q) fo.q[g * n + jl] = q;
+        if (fo.p) fo.p[g * n + jl] = coord_get(p);
+        if (fo.q) fo.q[g * n + jl] = coord_get(q);
     }
     if (g == 0) {
-        if (fo.S) fo.S[jl] = sh.Sj[t * C + ((A.n_steps - 1) % C)];
+        if (fo.S) fo.S[jl] = sj_get(t * C + ((A.n_steps - 1) % C));
         if (fo.theta) fo.theta[jl] = theta_last;
         if (fo.detM) fo.detM[jl] = detM_last;
         if (fo.stab) fo.stab[jl] = (double)stab;

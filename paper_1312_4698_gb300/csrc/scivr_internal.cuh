@@ -57,6 +57,7 @@ struct PropArgs {
     double cdrift[4], dkick[3];      // triple-jump fractions of dt
     double tdrift[4], tkick[3];      // the sub-step lengths themselves (fraction x dt)
     float tdrift_f[4], tkick_f[3];   // FP32 copies (conversions run on the FP64 pipe on GB300)
+    float tdrift_lo[4], tkick_lo[3]; // their remainders (tdrift - tdrift_f ...): double-FP32 sub-steps
     float stab_tol_f;
     double gamma[SCIVR_MAX_F];
     double rg[SCIVR_MAX_F];          // sqrt(gamma)
