@@ -48,9 +48,12 @@ FP64_PEAK_NOTE = ("GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table
 # scaled to the full launch where the capture used fewer trajectories
 TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9, ("k_ft_tc2", "f6"): 7.98e9,
            ("k_mlp_fused", "f9mlp"): 0.914e6 * 8,
-           # per trajectory-step (the bench multiplies by trajectories x steps): one launch of
-           # 65536 trajectories x 400 steps read 17.06 MB and wrote 364.34 MB
-           ("k_propagate_lg_mixed", "f9"): (17.06e6 + 364.34e6) / (65536 * 400)}
+           # per trajectory-step (the bench multiplies by trajectories x steps), by amplitude
+           # storage: one launch of 65536 trajectories x 400 steps with complex-double rows
+           # read 17.06 MB and wrote 364.34 MB
+           ("k_propagate_lg_mixed", "f9", "f64"): (17.06e6 + 364.34e6) / (65536 * 400),
+           # complex-float rows (the default mixed line): 14.30 MB read, 152.72 MB written
+           ("k_propagate_lg_mixed", "f9", "f32"): (14.30e6 + 152.72e6) / (65536 * 400)}
 
 
 # trajectories of the oracle's timed sample per workload (10-30 s of host work on 16 cores),
@@ -755,6 +758,8 @@ def main(argv=None):
                     help="propagation arithmetic (mixed: FP32 monodromy, potential and determinants; FP64 p, q, S, phase)")
     ap.add_argument("--ft", default="bf16x3", choices=list(FT_MODES),
                     help="Fourier step: fp64 CUDA cores or tensor-core BF16 digit splits")
+    ap.add_argument("--amp-storage", default="auto", choices=["auto", "fp32", "fp64"],
+                    help="amplitude rows: auto = complex float for mixed time-averaged runs, else double")
     ap.add_argument("--n-traj", type=int, default=None, help="override the workload's trajectory count")
     ap.add_argument("--n-steps", type=int, default=None, help="override the workload's step count")
     ap.add_argument("--n-E", type=int, default=None, help="override the workload's energy count")
@@ -798,7 +803,11 @@ def main(argv=None):
     lo, hi = shards.shard_range(n_job, rank, world) if strong else (0, n_job)
     n = hi - lo                                  # this rank's trajectories
     pes = scivr.scivr_create_pes(w8.pes)
-    bufs = scivr.alloc_buffers(w8, device=dev, n_traj=n)
+    # amplitude rows: complex float for the mixed path's time-averaged amplitudes (it forms
+    # them in FP32), complex double otherwise
+    amp_f32 = (args.amp_storage == "fp32" or
+               (args.amp_storage == "auto" and args.precision == "mixed" and args.amplitude == "ta"))
+    bufs = scivr.alloc_buffers(w8, device=dev, n_traj=n, amp_f32=amp_f32)
     full = scivr.alloc_buffers(w8.with_(n_steps=1, n_E=2), device=dev) if strong else None   # the job's samples
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -1005,7 +1014,7 @@ def main(argv=None):
             t_bound = (bulk * n * w8.n_steps) / (fp32_peak * 1e12) + \
                       (kept * n * w8.n_steps) / (fp64_peak * 1e12)
             eff_peak = pr_flops / t_bound / 1e12
-            tr = TRAFFIC.get(("k_propagate_lg_mixed", args.workload))
+            tr = TRAFFIC.get(("k_propagate_lg_mixed", args.workload, "f32" if amp_f32 else "f64"))
             roof = {"kernel": "k_propagate_lg<float> (scivr_propagate, mixed)", "bound": "alu",
                     "achieved": pr_tf, "peak": eff_peak, "unit": "TFLOP/s", "frac": pr_tf / eff_peak,
                     "traffic": tr * n * w8.n_steps if (tr is not None and full) else None,
@@ -1031,8 +1040,9 @@ def main(argv=None):
         "config": {"workload": describe(w8, args.precision, args.ft, args.amplitude),
                    "global_batch": n_job if strong else world * n,
                    "seed": "0, one batch split into trajectory shards" if strong else "base 0 + rank",
+                   "amplitude_storage": "complex float (8 B a sample)" if amp_f32 else "complex double (16 B)",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); amplitudes "
-                         f"({n * K * 16 / 1e9:.2f} GB) exceed L2",
+                         f"({n * K * (8 if amp_f32 else 16) / 1e9:.2f} GB) exceed L2",
                    "parallelism": (f"trajectory shards x{world} (one all-reduce of n_E + 1 numbers)" if strong
                                    else f"replicas x{world}")},
         "spectra_per_s": world / (ms_per_step * 1e-3),

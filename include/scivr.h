@@ -112,6 +112,9 @@ typedef struct {
     int32_t n_chi;          /* number of reference states, 1..SCIVR_MAX_CHI */
     int32_t kernel;         /* SCIVR_KERNEL_AUTO / _THREAD / _GROUP */
     int32_t amplitude;      /* SCIVR_AMP_TA (0) or SCIVR_AMP_HK */
+    int32_t amp_prec;       /* amplitude storage: SCIVR_FP64 (0, complex double) or SCIVR_MIXED
+                               (complex float, 8 bytes a sample; precision SCIVR_MIXED and
+                               amplitude SCIVR_AMP_TA only) */
 } scivr_prop_params;
 
 /* Optional final-state outputs of scivr_propagate (device pointers, each may be NULL). */
@@ -231,7 +234,10 @@ int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
  * common to all x, so its spectrum is scivr_spectrum of those combined rows with the same
  * weights.  The Herman-Kluk summand is bilinear in chi and has no such form.
  * p0, q0: device [F][n_traj].  amp: device complex double (re, im interleaved)
- * [n_chi][n_traj][amp_ld], amp_ld >= n_steps + 1, 16-byte aligned.  good:
+ * [n_chi][n_traj][amp_ld], amp_ld >= n_steps + 1, 16-byte aligned; with
+ * prm->amp_prec = SCIVR_MIXED complex float (re, im) of the same shape, 8-byte
+ * aligned (the mixed path forms each amplitude sample in FP32, so nothing is lost
+ * but the sample at c = 0, rounded from FP64).  good:
  * device [n_traj].  fin: host struct of optional device outputs (NULL = none).
  * Precision SCIVR_MIXED keeps the monodromy, the potential and det M in FP32
  * (positions, momenta, action and phase in FP64; the elimination that gives
@@ -244,7 +250,8 @@ int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
  * kind SCIVR_PES_CART3 (scivr_create_pes_cartesian) runs on SCIVR_FP64 with the
  * thread schedule only.
  * Errors: SCIVR_EINVAL (NULL pointers, n_traj < 1, n_steps < 1, dt <= 0,
- * gamma <= 0, amp_ld too small, F mismatch, n_chi out of range),
+ * gamma <= 0, amp_ld too small, F mismatch, n_chi out of range, amp_prec
+ * not SCIVR_FP64 or SCIVR_MIXED, or SCIVR_MIXED with FP64 precision or HK amplitudes),
  * SCIVR_EUNSUPPORTED (precision or kernel not built for this F). */
 int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
                     const double *p0, const double *q0, void *amp, int64_t amp_ld,
@@ -255,7 +262,9 @@ int scivr_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_traj,
  * with E_k = E_min + k (E_max - E_min) / (n_E - 1), k = 0..n_E-1 (endpoints
  * included, Sec. III.A) and T = n_steps dt.  Bad trajectories contribute
  * nothing, whatever their amplitudes hold.  If n_good = 0, I is all zeros.
- * amp: device complex double [n_traj][amp_ld] (amp_prec = SCIVR_FP64).  w:
+ * amp: device complex double [n_traj][amp_ld] (amp_prec = SCIVR_FP64, 16-byte
+ * aligned) or complex float (amp_prec = SCIVR_MIXED, 8-byte aligned; every
+ * Fourier mode reads it, widening to FP64 where the mode computes in FP64).  w:
  * device [n_traj].  good: device [n_traj].  I_out: device [n_E].  n_good_out:
  * device int64 (may be NULL).  ft_mode SCIVR_FT_FP64 contracts in FP64 on
  * the CUDA cores; the SCIVR_FT_TC_* modes split both operands into BF16

@@ -93,7 +93,13 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
         return fail(SCIVR_EINVAL, "scivr_propagate: chi not finite");
     if (amp_ld < (int64_t)prm->n_steps + 1)
         return fail(SCIVR_EINVAL, "scivr_propagate: amp_ld=%lld < n_steps+1", (long long)amp_ld);
-    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "scivr_propagate: amp not 16-byte aligned");
+    if (prm->amp_prec != SCIVR_FP64 && prm->amp_prec != SCIVR_MIXED)
+        return fail(SCIVR_EINVAL, "scivr_propagate: amp_prec %d invalid", prm->amp_prec);
+    if (prm->amp_prec == SCIVR_MIXED && (prm->precision != SCIVR_MIXED || prm->amplitude != SCIVR_AMP_TA))
+        return fail(SCIVR_EINVAL, "scivr_propagate: FP32 amplitude storage takes mixed precision and "
+                                  "time-averaged amplitudes");
+    if (reinterpret_cast<uintptr_t>(amp) % (prm->amp_prec == SCIVR_MIXED ? 8 : 16) != 0)
+        return fail(SCIVR_EINVAL, "scivr_propagate: amp not aligned to its element (16 bytes, 8 for FP32)");
     if (prm->precision != SCIVR_FP64 && prm->precision != SCIVR_MIXED)
         return fail(SCIVR_EINVAL, "scivr_propagate: precision %d invalid", prm->precision);
     if (prm->kernel < SCIVR_KERNEL_AUTO || prm->kernel > SCIVR_KERNEL_GROUP)
@@ -149,6 +155,7 @@ int prepare_propagate(scivr_pes pes, const scivr_prop_params *prm, int64_t n_tra
     L.p0 = p0;
     L.q0 = q0;
     L.amp = static_cast<double2 *>(amp);
+    L.amp_f32 = prm->amp_prec == SCIVR_MIXED;
     L.amp_ld = amp_ld;
     L.chi_stride = n_traj * amp_ld;
     L.good = good;
@@ -170,8 +177,10 @@ int check_spectrum_args(const void *amp, int64_t amp_ld, int32_t amp_prec, const
     if (!std::isfinite(E_min) || !std::isfinite(E_max) || !(E_max > E_min))
         return fail(SCIVR_EINVAL, "%s: need finite E_min < E_max", who);
     if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "%s: amp_ld < n_steps+1", who);
-    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0) return fail(SCIVR_EINVAL, "%s: amp not 16-byte aligned", who);
-    if (amp_prec != SCIVR_FP64) return fail(SCIVR_EUNSUPPORTED, "%s: amp_prec %d not supported", who, amp_prec);
+    if (amp_prec != SCIVR_FP64 && amp_prec != SCIVR_MIXED)
+        return fail(SCIVR_EINVAL, "%s: amp_prec %d invalid", who, amp_prec);
+    if (reinterpret_cast<uintptr_t>(amp) % (amp_prec == SCIVR_MIXED ? 8 : 16) != 0)
+        return fail(SCIVR_EINVAL, "%s: amp not aligned to its element (16 bytes, 8 for FP32)", who);
     if (ft_mode != SCIVR_FT_FP64 && ft_mode != SCIVR_FT_CZT64 && ft_tc_digits(ft_mode) == 0)
         return fail(SCIVR_EUNSUPPORTED, "%s: ft_mode %d not supported", who, ft_mode);
     if (ft_mode == SCIVR_FT_CZT64 && (n_steps + 1 > spectrum_czt_max_samples() || n_E > kCztMaxEnergies))
@@ -416,7 +425,7 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
         cudaError_t e = cudaMallocAsync(&scr, cb, s);
         if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: cudaMallocAsync");
         int nl = 0;
-        e = launch_spectrum_czt(static_cast<const double2 *>(amp), amp_ld, w, good, n_traj, n_steps, dt, E_min,
+        e = launch_spectrum_czt(AmpRef{amp, amp_prec == SCIVR_MIXED}, amp_ld, w, good, n_traj, n_steps, dt, E_min,
                                 E_max, n_E, I_out, n_good_out, scr, s, &nl);
         g_launches += nl;
         cudaError_t e2 = cudaFreeAsync(scr, s);
@@ -431,7 +440,7 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
         cudaError_t e = cudaMallocAsync(&scr, tb, s);
         if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: cudaMallocAsync");
         int nl = 0;
-        e = launch_spectrum_tc(ft_mode, static_cast<const double2 *>(amp), amp_ld, w, good, n_traj, n_steps,
+        e = launch_spectrum_tc(ft_mode, AmpRef{amp, amp_prec == SCIVR_MIXED}, amp_ld, w, good, n_traj, n_steps,
                                dt, E_min, E_max, n_E, I_out, n_good_out, scr, s, &nl);
         g_launches += nl;
         cudaError_t e2 = cudaFreeAsync(scr, s);
@@ -445,7 +454,7 @@ int scivr_spectrum(const void *amp, int64_t amp_ld, int32_t amp_prec, const doub
     cudaError_t e = cudaMallocAsync(&scratch, bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "scivr_spectrum: cudaMallocAsync");
     int nl = 0;
-    e = launch_spectrum_fp64(static_cast<const double2 *>(amp), amp_ld, w, good, n_traj, n_steps, dt,
+    e = launch_spectrum_fp64(AmpRef{amp, amp_prec == SCIVR_MIXED}, amp_ld, w, good, n_traj, n_steps, dt,
                              E_min, E_max, n_E, I_out, n_good_out, scratch, s, &nl);
     g_launches += nl;
     cudaError_t e2 = cudaFreeAsync(scratch, s);
@@ -523,14 +532,14 @@ int scivr_spectrum_noalloc(const void *amp, int64_t amp_ld, int32_t amp_prec, co
     if (!std::isfinite(E_min) || !std::isfinite(E_max) || !(E_max > E_min))
         return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: need finite E_min < E_max");
     if (amp_ld < (int64_t)n_steps + 1) return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: amp_ld < n_steps+1");
-    if (reinterpret_cast<uintptr_t>(amp) % 16 != 0)
-        return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: amp not 16-byte aligned");
-    if (amp_prec != SCIVR_FP64)
-        return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum_noalloc: amp_prec %d not supported", amp_prec);
+    if (amp_prec != SCIVR_FP64 && amp_prec != SCIVR_MIXED)
+        return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: amp_prec %d invalid", amp_prec);
+    if (reinterpret_cast<uintptr_t>(amp) % (amp_prec == SCIVR_MIXED ? 8 : 16) != 0)
+        return fail(SCIVR_EINVAL, "scivr_spectrum_noalloc: amp not aligned to its element (16 bytes, 8 for FP32)");
     if (ft_mode != SCIVR_FT_FP64)
         return fail(SCIVR_EUNSUPPORTED, "scivr_spectrum_noalloc: ft_mode %d not supported", ft_mode);
     int nl = 0;
-    cudaError_t e = launch_spectrum_noalloc(static_cast<const double2 *>(amp), amp_ld, w, good, n_traj,
+    cudaError_t e = launch_spectrum_noalloc(AmpRef{amp, amp_prec == SCIVR_MIXED}, amp_ld, w, good, n_traj,
                                             n_steps, dt, E_min, E_max, n_E, I_out, n_good_out,
                                             static_cast<cudaStream_t>(stream), &nl);
     g_launches += nl;

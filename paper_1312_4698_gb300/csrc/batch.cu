@@ -315,7 +315,7 @@ int scivr_batch_create(const scivr_batch_item *items, int32_t n_items, int32_t f
         PropLaunch L{};
         int rc = prepare_propagate(it.pes, &it.prm, it.n_traj, it.p0, it.q0, it.amp, it.amp_ld, it.good, nullptr, &L);
         if (rc == SCIVR_OK)
-            rc = check_spectrum_args(it.amp, it.amp_ld, SCIVR_FP64, it.w, it.good, it.n_traj, it.prm.n_steps,
+            rc = check_spectrum_args(it.amp, it.amp_ld, it.prm.amp_prec, it.w, it.good, it.n_traj, it.prm.n_steps,
                                      it.prm.dt, it.E_min, it.E_max, it.n_E, ft_mode, it.I_out, "scivr_batch_create");
         if (rc == SCIVR_OK && it.prm.precision == SCIVR_MIXED && it.pes->dev.F > SCIVR_MAX_F)
             rc = set_error(SCIVR_EUNSUPPORTED, "scivr_batch_create: mixed precision is built for F <= 24");
@@ -477,7 +477,7 @@ int scivr_batch_launch(scivr_batch B, void *stream)
     for (size_t i = 0; i < B->items.size(); ++i) {
         const scivr_batch_item &it = B->items[i];
         for (int x = 0; x < it.prm.n_chi; ++x) {
-            const double2 *amp = static_cast<const double2 *>(it.amp) + (int64_t)x * it.n_traj * it.amp_ld;
+            const AmpRef amp = AmpRef{it.amp, it.prm.amp_prec == SCIVR_MIXED}.offset((int64_t)x * it.n_traj * it.amp_ld);
             double *I = it.I_out + (int64_t)x * it.n_E;
             int nl = 0;
             if (B->ft_mode == SCIVR_FT_FP64)

@@ -57,7 +57,7 @@ __device__ __forceinline__ void record(const PropLaunch &L, int64_t j, int step,
         double sn, cs;
         sincos(ph, &sn, &cs);
         const double mag = exp(re);
-        L.amp[x * L.chi_stride + j * L.amp_ld + step] = make_double2(mag * cs, mag * sn);
+        amp_store(L, x * L.chi_stride + j * L.amp_ld + step, mag * cs, mag * sn);
     }
 }
 

@@ -646,9 +646,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             const double mag = exp(re);
             // the Herman-Kluk summand at t = 0 (C = 1, S = 0) is |<chi_x|p0 q0>|^2 / |<chi_0|p0 q0>|^2,
             // exactly 1 for x = 0
-            L.amp[x * L.chi_stride + jl * L.amp_ld] =
-                A.amplitude == SCIVR_AMP_HK ? make_double2(x == 0 ? 1.0 : exp(re - rdiv), 0.0)
-                                            : make_double2(mag * cs, mag * sn);
+            if (A.amplitude == SCIVR_AMP_HK) amp_store(L, x * L.chi_stride + jl * L.amp_ld, x == 0 ? 1.0 : exp(re - rdiv), 0.0);
+            else amp_store(L, x * L.chi_stride + jl * L.amp_ld, mag * cs, mag * sn);
         }
     }
 
@@ -1359,8 +1358,9 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     float sf, cf;
                     sincosf((float)red, &sf, &cf);
                     const float mag = expf(rf);
-                    L.amp[x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1] =
-                        make_double2((double)(mag * cf), (double)(mag * sf));
+                    const int64_t ia = x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1;
+                    if (L.amp_f32) reinterpret_cast<float2 *>(L.amp)[ia] = make_float2(mag * cf, mag * sf);
+                    else L.amp[ia] = make_double2((double)(mag * cf), (double)(mag * sf));
                 } else {
                     double re = 0.0, im = 0.0;
 #pragma unroll
@@ -1380,7 +1380,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     double sn, cs;
                     sincos(ph, &sn, &cs);
                     const double mag = exp(re);
-                    L.amp[x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1] = make_double2(mag * cs, mag * sn);
+                    amp_store(L, x * L.chi_stride + jl * L.amp_ld + step0 + jc + 1, mag * cs, mag * sn);
                 }
             }
         }

@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(64) k_propagate_tpt_fp64(const PropLaunch L)
             double sn, cs;
             sincos(ph, &sn, &cs);
             const double mag = exp(re);
-            L.amp[x * L.chi_stride + j * L.amp_ld + step] = make_double2(mag * cs, mag * sn);
+            amp_store(L, x * L.chi_stride + j * L.amp_ld + step, mag * cs, mag * sn);
         }
     }
     L.good[j] = good ? 1 : 0;

@@ -77,10 +77,48 @@ struct PropLaunch {
     PropArgs args;
     int64_t n_traj;
     const double *p0, *q0;
-    double2 *amp;
+    double2 *amp;                 // complex double rows, or complex float rows when amp_f32
     int64_t amp_ld, chi_stride;
+    int amp_f32;
     uint8_t *good;
     FinalDev fin;
+};
+
+// Amplitude sample i of a launch, stored at its precision.
+__device__ __forceinline__ void amp_store(const PropLaunch &L, int64_t i, double re, double im)
+{
+    if (L.amp_f32) reinterpret_cast<float2 *>(L.amp)[i] = make_float2((float)re, (float)im);
+    else L.amp[i] = make_double2(re, im);
+}
+
+// Amplitude rows as the Fourier steps read them: complex double, or complex float
+// (the mixed path's storage).  amp[i] widens to FP64; re_f, im_f narrow one part to FP32.
+struct AmpRef {
+    const void *p;
+    int f32;
+    __host__ __device__ AmpRef offset(int64_t i) const
+    {
+        return AmpRef{f32 ? (const void *)(static_cast<const float2 *>(p) + i)
+                          : (const void *)(static_cast<const double2 *>(p) + i), f32};
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ double2 operator[](int64_t i) const
+    {
+        if (f32) {
+            const float2 v = static_cast<const float2 *>(p)[i];
+            return make_double2((double)v.x, (double)v.y);
+        }
+        return static_cast<const double2 *>(p)[i];
+    }
+    __device__ __forceinline__ float re_f(int64_t i) const
+    {
+        return f32 ? static_cast<const float2 *>(p)[i].x : (float)static_cast<const double2 *>(p)[i].x;
+    }
+    __device__ __forceinline__ float im_f(int64_t i) const
+    {
+        return f32 ? static_cast<const float2 *>(p)[i].y : (float)static_cast<const double2 *>(p)[i].y;
+    }
+#endif
 };
 
 // Launchers (return cudaError_t of the launch).
@@ -88,13 +126,13 @@ cudaError_t launch_propagate(const PropLaunch &L, cudaStream_t s, int *n_launch)
 cudaError_t launch_sample(int F, const double *gamma, const double *p_eq, const double *q_eq,
                           int64_t n_traj, uint64_t seed, double *p0, double *q0, double *w,
                           cudaStream_t s, int *n_launch);
-cudaError_t launch_spectrum_fp64(const double2 *amp, int64_t amp_ld, const double *w,
+cudaError_t launch_spectrum_fp64(AmpRef amp, int64_t amp_ld, const double *w,
                                  const uint8_t *good, int64_t n_traj, int n_steps, double dt,
                                  double E_min, double E_max, int n_E, double *I_out,
                                  int64_t *n_good_out, void *scratch, cudaStream_t s,
                                  int *n_launch);
 size_t spectrum_fp64_scratch_bytes(int64_t n_traj, int n_steps, int n_E);
-cudaError_t launch_spectrum_noalloc(const double2 *amp, int64_t amp_ld, const double *w,
+cudaError_t launch_spectrum_noalloc(AmpRef amp, int64_t amp_ld, const double *w,
                                     const uint8_t *good, int64_t n_traj, int n_steps, double dt,
                                     double E_min, double E_max, int n_E, double *I_out,
                                     int64_t *n_good_out, cudaStream_t s, int *n_launch);
@@ -106,12 +144,12 @@ cudaError_t launch_spectrum_hk(const double2 *amp, int64_t amp_ld, const uint8_t
 int spectrum_czt_max_samples();
 constexpr int kCztMaxEnergies = 12288;   // per-CTA weighted sums beside the 128 KB transform buffer
 size_t spectrum_czt_scratch_bytes(int64_t n_traj, int n_steps, int n_E);
-cudaError_t launch_spectrum_czt(const double2 *amp, int64_t amp_ld, const double *w, const uint8_t *good,
+cudaError_t launch_spectrum_czt(AmpRef amp, int64_t amp_ld, const double *w, const uint8_t *good,
                                 int64_t n_traj, int n_steps, double dt, double E_min, double E_max, int n_E,
                                 double *I_out, int64_t *n_good_out, void *scratch, cudaStream_t s, int *n_launch);
 int ft_tc_digits(int ft_mode);
 size_t spectrum_tc_scratch_bytes(int ft_mode, int64_t n_traj, int n_steps, int n_E);
-cudaError_t launch_spectrum_tc(int ft_mode, const double2 *amp, int64_t amp_ld, const double *w,
+cudaError_t launch_spectrum_tc(int ft_mode, AmpRef amp, int64_t amp_ld, const double *w,
                                const uint8_t *good, int64_t n_traj, int n_steps, double dt, double E_min,
                                double E_max, int n_E, double *I_out, int64_t *n_good_out, void *scratch,
                                cudaStream_t s, int *n_launch);

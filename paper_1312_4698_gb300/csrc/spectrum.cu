@@ -46,7 +46,7 @@ __global__ void k_twiddles(double2 *__restrict__ tw, int K, int n_E, double E_mi
     tw[idx] = make_double2(cs, sn);
 }
 
-__global__ void __launch_bounds__(256) k_ft_fp64(const double2 *__restrict__ amp, int64_t amp_ld,
+__global__ void __launch_bounds__(256) k_ft_fp64(const AmpRef amp, int64_t amp_ld,
                                                  const double2 *__restrict__ tw, const double *__restrict__ w,
                                                  const uint8_t *__restrict__ good, int64_t n_traj, int K,
                                                  int n_E, double *__restrict__ part)
@@ -154,7 +154,7 @@ size_t spectrum_fp64_scratch_bytes(int64_t n_traj, int n_steps, int n_E)
            align256(sizeof(double) * n_mt * n_E);
 }
 
-cudaError_t launch_spectrum_fp64(const double2 *amp, int64_t amp_ld, const double *w,
+cudaError_t launch_spectrum_fp64(AmpRef amp, int64_t amp_ld, const double *w,
                                  const uint8_t *good, int64_t n_traj, int n_steps, double dt,
                                  double E_min, double E_max, int n_E, double *I_out,
                                  int64_t *n_good_out, void *scratch, cudaStream_t s, int *n_launch)

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_czt_kernel_fft(const double2 *__re
 }
 
 // Weighted |X|^2 of the CTA's good trajectories for every energy block; per-CTA sums.
-__global__ void __launch_bounds__(kThreads) k_czt(const double2 *__restrict__ amp, int64_t amp_ld,
+__global__ void __launch_bounds__(kThreads) k_czt(const AmpRef amp, int64_t amp_ld,
                                                   const double *__restrict__ w, const uint8_t *__restrict__ good,
                                                   int64_t n_traj, int K, int n_E, int n_blk, int nb,
                                                   const double2 *__restrict__ chirp, const double2 *__restrict__ V,
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_czt(const double2 *__restrict__ am
     const double inv_L2 = 1.0 / ((double)kL * (double)kL);
     for (int64_t j = blockIdx.x; j < n_traj; j += gridDim.x) {
         if (!good[j]) continue;                       // uniform over the CTA
-        const double2 *a = amp + j * amp_ld;
+        const AmpRef a = amp.offset(j * amp_ld);
         const double wj = w[j] * inv_L2;
         for (int b = 0; b < n_blk; ++b) {
             const double2 *ch = chirp + (int64_t)b * K;
@@ -223,7 +223,7 @@ size_t spectrum_czt_scratch_bytes(int64_t n_traj, int n_steps, int n_E)
     return czt_layout(n_steps, n_E, sm_count()).total;
 }
 
-cudaError_t launch_spectrum_czt(const double2 *amp, int64_t amp_ld, const double *w, const uint8_t *good,
+cudaError_t launch_spectrum_czt(AmpRef amp, int64_t amp_ld, const double *w, const uint8_t *good,
                                 int64_t n_traj, int n_steps, double dt, double E_min, double E_max, int n_E,
                                 double *I_out, int64_t *n_good_out, void *scratch, cudaStream_t s, int *n_launch)
 {

@@ -46,7 +46,7 @@ __global__ void k_na_count_good(const uint8_t *__restrict__ good, int64_t n, dou
 
 // grid.x: energy strips of NB columns; grid.y: row slices.  Each CTA walks the
 // row tiles m = slice, slice + n_slices, ... and keeps its column sums on chip.
-__global__ void __launch_bounds__(256) k_na_ft(const double2 *__restrict__ amp, int64_t amp_ld,
+__global__ void __launch_bounds__(256) k_na_ft(const AmpRef amp, int64_t amp_ld,
                                                const double *__restrict__ w, const uint8_t *__restrict__ good,
                                                int64_t n_traj, int K, int n_E, double E_min, double dE,
                                                double dt, int n_slices, double *__restrict__ part)
@@ -187,7 +187,7 @@ cudaError_t scratch_address(cudaStream_t s, double **out)
 
 int spectrum_noalloc_max_energies() { return kScratchDoubles - kHeaderDoubles; }
 
-cudaError_t launch_spectrum_noalloc(const double2 *amp, int64_t amp_ld, const double *w,
+cudaError_t launch_spectrum_noalloc(AmpRef amp, int64_t amp_ld, const double *w,
                                     const uint8_t *good, int64_t n_traj, int n_steps, double dt,
                                     double E_min, double E_max, int n_E, double *I_out,
                                     int64_t *n_good_out, cudaStream_t s, int *n_launch)

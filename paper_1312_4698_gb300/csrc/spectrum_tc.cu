@@ -41,7 +41,7 @@ __device__ __forceinline__ void split_digits(float x, __nv_bfloat16 (&d)[ND])
 // A' rows: [Re a(0..K-1), Im a(0..K-1), 0 ...]; rows of bad or missing trajectories are zero.
 // One thread: one row, one 8-column chunk, all digits.
 template <int ND>
-__global__ void k_split_amp(const double2 *__restrict__ amp, int64_t amp_ld, const uint8_t *__restrict__ good,
+__global__ void k_split_amp(const AmpRef amp, int64_t amp_ld, const uint8_t *__restrict__ good,
                             int64_t n_traj, int K, int n_kt, int64_t rows_pad, uint8_t *__restrict__ At)
 {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -60,8 +60,8 @@ __global__ void k_split_amp(const double2 *__restrict__ amp, int64_t amp_ld, con
         const int kp = k0 + i;
         float x = 0.0f;
         if (ok) {
-            if (kp < K) x = (float)amp[r * amp_ld + kp].x;
-            else if (kp < 2 * K) x = (float)amp[r * amp_ld + (kp - K)].y;
+            if (kp < K) x = amp.re_f(r * amp_ld + kp);
+            else if (kp < 2 * K) x = amp.im_f(r * amp_ld + (kp - K));
         }
         __nv_bfloat16 d[ND];
         split_digits<ND>(x, d);
@@ -318,7 +318,7 @@ inline TcLayout tc_layout(int nd, int64_t n_traj, int n_steps, int n_E)
 }
 
 template <int ND>
-cudaError_t run(const double2 *amp, int64_t amp_ld, const double *w, const uint8_t *good, int64_t n_traj,
+cudaError_t run(AmpRef amp, int64_t amp_ld, const double *w, const uint8_t *good, int64_t n_traj,
                 int n_steps, double dt, double E_min, double E_max, int n_E, double *I_out,
                 int64_t *n_good_out, void *scratch, cudaStream_t s, int *n_launch)
 {
@@ -370,7 +370,7 @@ size_t spectrum_tc_scratch_bytes(int ft_mode, int64_t n_traj, int n_steps, int n
     return tc::tc_layout(ft_tc_digits(ft_mode), n_traj, n_steps, n_E).total;
 }
 
-cudaError_t launch_spectrum_tc(int ft_mode, const double2 *amp, int64_t amp_ld, const double *w,
+cudaError_t launch_spectrum_tc(int ft_mode, AmpRef amp, int64_t amp_ld, const double *w,
                                const uint8_t *good, int64_t n_traj, int n_steps, double dt, double E_min,
                                double E_max, int n_E, double *I_out, int64_t *n_good_out, void *scratch,
                                cudaStream_t s, int *n_launch)

@@ -68,7 +68,7 @@ class scivr_prop_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_steps", C.c_int32), ("precision", C.c_int32),
                 ("stab_tol", C.c_double), ("gamma", C.c_void_p), ("p_eq", C.c_void_p),
                 ("q_eq", C.c_void_p), ("n_chi", C.c_int32), ("kernel", C.c_int32),
-                ("amplitude", C.c_int32)]
+                ("amplitude", C.c_int32), ("amp_prec", C.c_int32)]
 
 
 class scivr_final_state(C.Structure):
@@ -301,16 +301,18 @@ sample_initial = scivr_sample_initial
 
 def scivr_propagate(pes: Pes, dt, n_steps, gamma, p_eq, q_eq, n_traj, p0, q0, amp, amp_ld, good,
                     precision=SCIVR_FP64, stab_tol=1e-6, fin: Optional[dict] = None, stream=None,
-                    kernel=SCIVR_KERNEL_AUTO, amplitude=SCIVR_AMP_TA):
+                    kernel=SCIVR_KERNEL_AUTO, amplitude=SCIVR_AMP_TA, amp_prec=None):
     """p_eq, q_eq: [n_chi, F] host arrays.  fin: optional dict of device tensors.
     amplitude: SCIVR_AMP_TA (time-averaging integrand) or SCIVR_AMP_HK (plain
-    Herman-Kluk summand)."""
+    Herman-Kluk summand).  amp_prec: SCIVR_FP64 (complex double) or SCIVR_MIXED
+    (complex float); None takes it from amp's dtype (float32 -> SCIVR_MIXED)."""
+    amp_prec = _amp_prec_of(amp, amp_prec)
     g = _f64(gamma)
     pe = _f64(np.atleast_2d(p_eq))
     qe = _f64(np.atleast_2d(q_eq))
     prm = scivr_prop_params(float(dt), int(n_steps), int(precision), float(stab_tol),
                             g.ctypes.data, pe.ctypes.data, qe.ctypes.data, pe.shape[0], int(kernel),
-                            int(amplitude))
+                            int(amplitude), int(amp_prec))
     fs = None
     if fin:
         fs = scivr_final_state(*[_ptr(fin.get(k)) for k in ("p", "q", "S", "theta", "detM", "detA", "M",
@@ -323,8 +325,16 @@ def scivr_propagate(pes: Pes, dt, n_steps, gamma, p_eq, q_eq, n_traj, p0, q0, am
 propagate = scivr_propagate
 
 
+def _amp_prec_of(amp, amp_prec):
+    if amp_prec is None:
+        return SCIVR_MIXED if str(getattr(amp, "dtype", "")).endswith("float32") else SCIVR_FP64
+    return amp_prec
+
+
 def scivr_spectrum(amp, amp_ld, w, good, n_traj, n_steps, dt, E_min, E_max, n_E, I_out,
-                   n_good_out=None, amp_prec=SCIVR_FP64, ft_mode=SCIVR_FT_FP64, stream=None):
+                   n_good_out=None, amp_prec=None, ft_mode=SCIVR_FT_FP64, stream=None):
+    """amp_prec None: from amp's dtype (float32 rows are the FP32 storage)."""
+    amp_prec = _amp_prec_of(amp, amp_prec)
     _check(_lib.scivr_spectrum(_ptr(amp), int(amp_ld), int(amp_prec), _ptr(w), _ptr(good),
                                int(n_traj), int(n_steps), float(dt), float(E_min), float(E_max),
                                int(n_E), int(ft_mode), _ptr(I_out), _ptr(n_good_out),
@@ -343,8 +353,9 @@ def scivr_spectrum_hk(amp, amp_ld, good, n_traj, n_steps, dt, E_min, E_max, n_E,
 
 
 def scivr_spectrum_noalloc(amp, amp_ld, w, good, n_traj, n_steps, dt, E_min, E_max, n_E, I_out,
-                           n_good_out=None, amp_prec=SCIVR_FP64, ft_mode=SCIVR_FT_FP64, stream=None):
+                           n_good_out=None, amp_prec=None, ft_mode=SCIVR_FT_FP64, stream=None):
     """scivr_spectrum without device allocations (library-owned fixed scratch; calls must not overlap)."""
+    amp_prec = _amp_prec_of(amp, amp_prec)
     _check(_lib.scivr_spectrum_noalloc(_ptr(amp), int(amp_ld), int(amp_prec), _ptr(w), _ptr(good),
                                        int(n_traj), int(n_steps), float(dt), float(E_min),
                                        float(E_max), int(n_E), int(ft_mode), _ptr(I_out),
@@ -366,7 +377,8 @@ class Buffers:
     n_good: "object"
 
 
-def alloc_buffers(wl, device="cuda", n_traj=None):
+def alloc_buffers(wl, device="cuda", n_traj=None, amp_f32=False):
+    """amp_f32: complex-float amplitude rows (the mixed path's 8-byte storage)."""
     import torch
     n = wl.n_traj if n_traj is None else n_traj
     K = wl.n_steps + 1
@@ -374,7 +386,7 @@ def alloc_buffers(wl, device="cuda", n_traj=None):
         p0=torch.empty((wl.F, n), dtype=torch.float64, device=device),
         q0=torch.empty((wl.F, n), dtype=torch.float64, device=device),
         w=torch.empty(n, dtype=torch.float64, device=device),
-        amp=torch.empty((wl.n_chi, n, K, 2), dtype=torch.float64, device=device),
+        amp=torch.empty((wl.n_chi, n, K, 2), dtype=torch.float32 if amp_f32 else torch.float64, device=device),
         good=torch.empty(n, dtype=torch.uint8, device=device),
         I=torch.empty((wl.n_chi, wl.n_E), dtype=torch.float64, device=device),
         n_good=torch.zeros(1, dtype=torch.int64, device=device),

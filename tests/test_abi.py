@@ -97,6 +97,11 @@ def test_invalid_propagate_and_spectrum_arguments(lib):
     assert rc == scivr.SCIVR_EUNSUPPORTED
     rc = scivr._lib.scivr_spectrum(fake + 8, 11, 0, fake, fake, 4, 10, 10.0, 0.0, 0.1, 16, 0, fake, None, None)
     assert rc == scivr.SCIVR_EINVAL   # misaligned amplitudes
+    # amplitude storage: only FP64 (complex double) and SCIVR_MIXED (complex float, 8-byte aligned)
+    rc = scivr._lib.scivr_spectrum(fake, 11, 7, fake, fake, 4, 10, 10.0, 0.0, 0.1, 16, 0, fake, None, None)
+    assert rc == scivr.SCIVR_EINVAL and "amp_prec" in scivr.last_error()
+    rc = scivr._lib.scivr_spectrum(fake + 4, 11, 1, fake, fake, 4, 10, 10.0, 0.0, 0.1, 16, 0, fake, None, None)
+    assert rc == scivr.SCIVR_EINVAL and "aligned" in scivr.last_error()
 
 
 def test_learned_residual_entry_points_validate_before_any_launch(lib):
@@ -141,7 +146,8 @@ def test_remaining_entry_points_validate_before_any_launch(lib):
     base = dict(amp=fake, amp_ld=11, prec=0, n_traj=4, n_steps=10, dt=10.0, E_min=0.0, E_max=0.1, n_E=16, ft=0)
     for over, code in ((dict(n_E=1 << 20), scivr.SCIVR_EINVAL), (dict(n_E=1), scivr.SCIVR_EINVAL),
                        (dict(amp=fake + 8), scivr.SCIVR_EINVAL), (dict(E_max=float("inf")), scivr.SCIVR_EINVAL),
-                       (dict(prec=1), scivr.SCIVR_EUNSUPPORTED), (dict(ft=2), scivr.SCIVR_EUNSUPPORTED)):
+                       (dict(prec=7), scivr.SCIVR_EINVAL), (dict(prec=1, amp=fake + 4), scivr.SCIVR_EINVAL),
+                       (dict(ft=2), scivr.SCIVR_EUNSUPPORTED)):
         a = dict(base, **over)
         rc = L.scivr_spectrum_noalloc(a["amp"], a["amp_ld"], a["prec"], fake, fake, a["n_traj"], a["n_steps"],
                                       a["dt"], a["E_min"], a["E_max"], a["n_E"], a["ft"], fake, None, None)

@@ -128,9 +128,10 @@ def test_mixed_chunk_end_stability_test_flags(G):
 
 def test_config_f9_full_size_sampled(G):
     """The methane-sized workload (F = 9, 65536 trajectories, 5000 steps, 4000
-    energies) at its full size and launch shape: mixed propagation and the
-    tensor-core bf16x3 Fourier step.  (5000 steps are whole 8-step chunks here;
-    the tests above cover the ragged tail.)
+    energies) at its full size and launch shape: mixed propagation with FP32
+    amplitude storage and the tensor-core bf16x3 Fourier step.  (5000 steps are
+    whole 4-step chunks here, and the det M test falls every 16 steps and at the
+    last step; the tests above cover the ragged tail.)
 
     * 24 sampled amplitude rows, the last trajectory included, against the FP64
       oracle within the mixed bound;
@@ -144,7 +145,7 @@ def test_config_f9_full_size_sampled(G):
     n, K = w8.n_traj, w8.n_steps + 1
     p0, q0, w = oracle.sample_initial(w8.gamma, w8.p_eq, w8.q_eq, n, w8.seed)
     pes = G.scivr_create_pes(w8.pes)
-    bufs = G.alloc_buffers(w8, n_traj=n)
+    bufs = G.alloc_buffers(w8, n_traj=n, amp_f32=True)
     bufs.p0.copy_(_t(p0))
     bufs.q0.copy_(_t(q0))
     bufs.w.copy_(_t(w))
@@ -168,7 +169,7 @@ def test_config_f9_full_size_sampled(G):
     idx = np.sort(np.random.default_rng(2).choice(n, 24, replace=False))
     idx[-1] = n - 1
     ra, rg = oracle.propagate(w8.pes, w8.gamma, w8.p_eq, w8.q_eq, w8.dt, w8.n_steps, p0[:, idx], q0[:, idx])
-    ga = bufs.amp[0, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    ga = bufs.amp[0, torch.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.float64)
     ga = ga[..., 0] + 1j * ga[..., 1]
     sel = rg.astype(bool) & gg[idx].astype(bool)
     assert sel.sum() >= 22
