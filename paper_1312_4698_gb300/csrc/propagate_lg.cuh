@@ -258,12 +258,12 @@ template <int F, int G, typename Real> __host__ __device__ constexpr int lg_chun
 template <int F, int G> __host__ __device__ constexpr int lg_warps() { return G < 32 ? 4 : (F <= 9 ? 2 : (F <= 12 ? 8 : 4)); }
 // (F > 16: 4 warps, one CTA per SM: 18 KB of per-job prefactor matrices and 9 KB of det M
 // workspace per warp at F = 24)
-// Two-trajectory mixed warps (F = 6..9) hold the coupling tensors in registers (fewer
-// shared-memory wavefronts, more registers: lg_min_ctas) or read them from shared memory.
-// Measured on the recipe surfaces: registers win at F = 7 (6 %) and F = 8 (13 %: the
-// shared-memory schedule there is held to 128 registers by its four CTAs per SM and spills;
-// at three CTAs it is still 15 % slower); shared memory wins at F = 6 (5 %, four CTAs per SM
-// against three) and at F = 9 (5 %, three against two).
+// Two-trajectory mixed warps (F = 6..9) hold the coupling tensors in registers (no
+// shared-memory reads of them, more registers: lg_min_ctas) or read them from shared
+// memory in the same half-split layout (TensorLayout::split).  Measured on the recipe
+// surfaces: registers win at F = 7 (7 %) and F = 8 (10 %: the shared-memory schedule there
+// is held to 128 registers by its four CTAs per SM); shared memory wins at F = 6 (6 %, four
+// CTAs per SM against three) and at F = 9 (12 %, three against two).
 template <int F> __host__ __device__ constexpr bool lg_tensor_regs() { return F == 7 || F == 8; }
 
 template <int F, int G, typename Real> __host__ __device__ constexpr int lg_min_ctas()
@@ -341,30 +341,6 @@ __device__ __forceinline__ Real dot16(const Real *a, const Real *b)
     return r;
 }
 
-// Rows u, v against vectors x, y (all 16-byte aligned shared rows of S elements):
-// out = {u.x, u.y, v.x, v.y}.  Each loaded vector of u or v feeds two products, so a
-// warp's shared-memory wavefronts per multiply-add are half those of dot16.
-template <int S>
-__device__ __forceinline__ void dot16_2x2(const float *u, const float *v, const float *x, const float *y,
-                                          float (&out)[4])
-{
-    static_assert(S % 4 == 0, "padded length");
-    float2 acc[4];   // packed partial sums: even and odd elements
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int i = 0; i < S; i += 4) {
-        const float4 uu = *reinterpret_cast<const float4 *>(u + i), vv = *reinterpret_cast<const float4 *>(v + i);
-        const float4 xx = *reinterpret_cast<const float4 *>(x + i), yy = *reinterpret_cast<const float4 *>(y + i);
-        acc[0] = ffma2(lo2(uu), lo2(xx), acc[0]); acc[0] = ffma2(hi2(uu), hi2(xx), acc[0]);
-        acc[1] = ffma2(lo2(uu), lo2(yy), acc[1]); acc[1] = ffma2(hi2(uu), hi2(yy), acc[1]);
-        acc[2] = ffma2(lo2(vv), lo2(xx), acc[2]); acc[2] = ffma2(hi2(vv), hi2(xx), acc[2]);
-        acc[3] = ffma2(lo2(vv), lo2(yy), acc[3]); acc[3] = ffma2(hi2(vv), hi2(yy), acc[3]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = acc[q].x + acc[q].y;
-}
-
 // Coupling tensors staged per CTA, transposed so that one potential entry e
 // reads one contiguous row: sT3[e][k] (k < F, stride S3), sT4[e][kl] (kl < P,
 // stride S4), zero-padded.
@@ -376,10 +352,19 @@ struct TensorLayout {
     // Above F = 16 the quartic tensor (P^2 entries, 360 KB at F = 24) does not fit shared
     // memory: both tensors are read from global memory (L2) and only the coefficients are staged.
     static constexpr bool staged = STAGED;
+    // Two-trajectory mixed warps (F = 6..9) cut x = (q, zero pad to an even length F3E, the
+    // pair products, zero pad) into two halves of KH elements; those that do not hold the
+    // tensors in registers read them from shared memory cut the same way ("split"):
+    // sTh[h][e][KHS] = the tensor row of entry e over half h of x, KHS an odd number of
+    // 16-byte vectors so that 8 lanes reading 8 consecutive entries hit disjoint banks.
+    static constexpr int F3E = (F + 1) & ~1;
+    static constexpr int KH = (((F3E + P + 1) / 2) + 3) & ~3;
+    static constexpr int KHS = (KH / 4) % 2 ? KH : KH + 4;
+    static constexpr bool split = sizeof(Real) == 4 && STAGED && F >= 6 && F <= 9 && !lg_tensor_regs<F>();
+    static constexpr size_t tensor_elems = !staged ? 0 : (split ? (size_t)2 * P * KHS : (size_t)P * S3 + (size_t)P * S4);
     // after the tensors: the Herman-Kluk matrix coefficients acoef[a][b][4] =
     // (1/2) {rg_a/rg_b, rg_b/rg_a, -rg_a rg_b, 1/(rg_a rg_b)}, rg = sqrt(gamma)
-    static constexpr size_t bytes =
-        ((sizeof(Real) * (size_t)((staged ? P * S3 + P * S4 : 0) + 4 * F * F)) + 15) & ~(size_t)15;
+    static constexpr size_t bytes = ((sizeof(Real) * (tensor_elems + (size_t)4 * F * F)) + 15) & ~(size_t)15;
 };
 
 template <int F, int G, typename Real>
@@ -393,9 +378,9 @@ struct WarpShared {
     alignas(16) Real qr[T][S3];
     alignas(16) Real qq[T][S4];
     // x = (q, zero pad to an even length, pair products, zero pad) in two halves of KH for the
-    // register-held tensor rows of two-trajectory warps (see lg_body)
-    static constexpr int F3E = (F + 1) & ~1;
-    static constexpr int KH = (((F3E + P + 1) / 2) + 3) & ~3;
+    // half-split Hessian of two-trajectory warps (see TensorLayout and lg_body)
+    static constexpr int F3E = TensorLayout<F, Real>::F3E;
+    static constexpr int KH = TensorLayout<F, Real>::KH;
     alignas(16) Real xs[T][2 * KH];
     alignas(16) Real Gc[T][F][S3];          // gradient coefficients, full symmetric matrix (row a read by mode lane a)
     alignas(16) Real H[T][F][SH];
@@ -430,8 +415,9 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     using TL = TensorLayout<F, Real, STAGED>;
     constexpr int S3 = TL::S3, S4 = TL::S4;
     Real *sT3 = reinterpret_cast<Real *>(smem_raw);
-    Real *sT4 = sT3 + (TL::staged ? P * S3 : 0);
-    Real *sAc = sT4 + (TL::staged ? P * S4 : 0);   // Herman-Kluk matrix coefficients [a][b][4] (16-byte aligned: P * (S3 + S4) is a vector multiple)
+    Real *sT4 = sT3 + ((TL::staged && !TL::split) ? P * S3 : 0);
+    Real *sTh = sT3;                                  // the half-split layout (TL::split)
+    Real *sAc = sT3 + TL::tensor_elems;   // Herman-Kluk matrix coefficients [a][b][4] (16-byte aligned: the tensor block is a vector multiple)
     size_t off = TL::bytes;
     CtaConst<F> &cc = *reinterpret_cast<CtaConst<F> *>(smem_raw + off);
     off += (sizeof(CtaConst<F>) + 15) & ~(size_t)15;
@@ -445,13 +431,26 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         const Real *g3 = nullptr, *g4 = nullptr;
         if constexpr (sizeof(Real) == 4) { g3 = reinterpret_cast<const Real *>(pes.T3f); g4 = reinterpret_cast<const Real *>(pes.T4f); }
         else { g3 = reinterpret_cast<const Real *>(pes.T3); g4 = reinterpret_cast<const Real *>(pes.T4); }
-        for (int i = threadIdx.x; i < P * S3; i += blockDim.x) {
-            const int e = i / S3, k = i % S3;
-            sT3[i] = (use3 && k < F) ? g3[k * P + e] : Real(0);
-        }
-        for (int i = threadIdx.x; i < P * S4; i += blockDim.x) {
-            const int e = i / S4, kl = i % S4;
-            sT4[i] = (use4 && kl < P) ? g4[kl * P + e] : Real(0);
+        if constexpr (TL::split) {
+            constexpr int KH = TL::KH, KHS = TL::KHS, F3E = TL::F3E;
+            for (int i = threadIdx.x; i < 2 * P * KHS; i += blockDim.x) {
+                const int h = i / (P * KHS), e = (i / KHS) % P, kk = i % KHS, gk = h * KH + kk;
+                Real v = Real(0);
+                if (kk < KH) {
+                    if (gk < F) v = use3 ? g3[gk * P + e] : Real(0);
+                    else if (gk >= F3E && gk - F3E < P) v = use4 ? g4[(gk - F3E) * P + e] : Real(0);
+                }
+                sTh[i] = v;
+            }
+        } else {
+            for (int i = threadIdx.x; i < P * S3; i += blockDim.x) {
+                const int e = i / S3, k = i % S3;
+                sT3[i] = (use3 && k < F) ? g3[k * P + e] : Real(0);
+            }
+            for (int i = threadIdx.x; i < P * S4; i += blockDim.x) {
+                const int e = i / S4, kl = i % S4;
+                sT4[i] = (use4 && kl < P) ? g4[kl * P + e] : Real(0);
+            }
         }
     }
     if (threadIdx.x == 0) {
@@ -524,27 +523,24 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     // sums so that each ends with whole entries of its own trajectory.
     constexpr bool kPair = (T == 2) && (sizeof(Real) == 4) && TL::staged && (P <= 64) && (P > 16);
     constexpr bool kTreg = kPair && lg_tensor_regs<F>();
-    // otherwise (kBlocked) lane ln computes entries ln and ln + 32 for both trajectories from
-    // the staged rows (register blocking: each loaded row element feeds two products);
-    // consecutive lanes read consecutive rows, whose odd vector stride keeps them in
-    // different banks
-    constexpr bool kBlocked = kPair && !kTreg;
-    int bA[2] = {0, 0}, bB[2] = {0, 0};
-    if constexpr (kBlocked) {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            int e = ln + 32 * i, a = 0;
-            if (e >= P) e = 0;
-            while (e >= F - a) { e -= F - a; ++a; }
-            bA[i] = a;
-            bB[i] = a + e;
-        }
-    }
-    constexpr int F3E = Sh::F3E, KH = Sh::KH;
-    constexpr int EPH = kTreg ? (P + 15) / 16 : 1;
+    // or the same cut with the tensor rows read from shared memory (TL::split)
+    constexpr bool kSplit = kPair && !kTreg && TL::split;
+    static_assert(kPair == (kTreg || kSplit), "two-trajectory warps take one of the two half-split schedules");
+    constexpr int F3E = Sh::F3E, KH = Sh::KH, KHS = TL::KHS;
+    constexpr int EPH = (kTreg || kSplit) ? (P + 15) / 16 : 1;
     const int hx = ln >> 4, jx = ln & 15;
     int ebA[EPH], ebB[EPH];
     float2 Tr[EPH][kTreg ? KH / 2 : 1];
+    if constexpr (kSplit) {
+#pragma unroll
+        for (int i = 0; i < EPH; ++i) {
+            const int e0 = jx + 16 * i;
+            int e = e0 < P ? e0 : 0, a = 0;
+            while (e >= F - a) { e -= F - a; ++a; }
+            ebA[i] = a;
+            ebB[i] = a + e;
+        }
+    }
     if constexpr (kTreg) {
 #pragma unroll
         for (int i = 0; i < EPH; ++i) {
@@ -693,7 +689,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 __syncwarp();   // previous kick's readers of qr/H are done
                 if (g < F) {
                     sh.qr[t][g] = (Real)coord_f(q);
-                    if constexpr (kTreg) sh.xs[t][g] = (Real)coord_f(q);
+                    if constexpr (kTreg || kSplit) sh.xs[t][g] = (Real)coord_f(q);
                 }
                 __syncwarp();
 #pragma unroll
@@ -702,7 +698,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     if (e < P) {
                         const Real v = sh.qr[t][ea[i]] * sh.qr[t][eb[i]];
                         sh.qq[t][e] = v;
-                        if constexpr (kTreg) sh.xs[t][F3E + e] = v;
+                        if constexpr (kTreg || kSplit) sh.xs[t][F3E + e] = v;
                     }
                 }
                 __syncwarp();
@@ -757,7 +753,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                             }
                         }
                     }
-                } else if constexpr (kTreg) {
+                } else if constexpr (kTreg || kSplit) {
                     float2 aF[EPH][2], a4[EPH][2];   // packed partial sums per entry and trajectory
                     float sF[EPH][2];                // the first F3E elements of x (q in half 0)
 #pragma unroll
@@ -765,22 +761,36 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 #pragma unroll
                         for (int tt = 0; tt < 2; ++tt) aF[i][tt] = a4[i][tt] = make_float2(0.0f, 0.0f);
                     const float *x0 = &sh.xs[0][hx * KH], *x1 = &sh.xs[1][hx * KH];
+                    const float *trow[EPH];          // kSplit: this lane's rows (entries past P read row 0)
+#pragma unroll
+                    for (int i = 0; i < EPH; ++i) {
+                        const int e = jx + 16 * i;
+                        trow[i] = sTh + (hx * P + (e < P ? e : 0)) * KHS;
+                    }
 #pragma unroll
                     for (int c = 0; c < KH; c += 4) {
                         const float4 u = *reinterpret_cast<const float4 *>(x0 + c);
                         const float4 w = *reinterpret_cast<const float4 *>(x1 + c);
+                        float4 tv[EPH];
+                        if constexpr (kSplit) {
+#pragma unroll
+                            for (int i = 0; i < EPH; ++i) tv[i] = *reinterpret_cast<const float4 *>(trow[i] + c);
+                        }
 #pragma unroll
                         for (int hp = 0; hp < 2; ++hp) {
                             const int kk = c + 2 * hp;
                             const float2 xu = hp ? hi2(u) : lo2(u), xw = hp ? hi2(w) : lo2(w);
 #pragma unroll
                             for (int i = 0; i < EPH; ++i) {
+                                float2 t2;
+                                if constexpr (kSplit) t2 = hp ? hi2(tv[i]) : lo2(tv[i]);
+                                else t2 = Tr[i][kk / 2];
                                 if (kk < F3E) {
-                                    aF[i][0] = ffma2(Tr[i][kk / 2], xu, aF[i][0]);
-                                    aF[i][1] = ffma2(Tr[i][kk / 2], xw, aF[i][1]);
+                                    aF[i][0] = ffma2(t2, xu, aF[i][0]);
+                                    aF[i][1] = ffma2(t2, xw, aF[i][1]);
                                 } else {
-                                    a4[i][0] = ffma2(Tr[i][kk / 2], xu, a4[i][0]);
-                                    a4[i][1] = ffma2(Tr[i][kk / 2], xw, a4[i][1]);
+                                    a4[i][0] = ffma2(t2, xu, a4[i][0]);
+                                    a4[i][1] = ffma2(t2, xw, a4[i][1]);
                                 }
                             }
                             if (kk + 2 == F3E) {
@@ -820,33 +830,6 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         }
                     }
                     vpart = vp;   // lane ln belongs to group hx = t
-                } else if constexpr (kBlocked) {
-                    const int e0 = ln, e1 = ln + 32 < P ? ln + 32 : ln;
-                    float v[2] = {0.0f, 0.0f};   // energy parts of trajectories 0 and 1
-                    if (e0 < P) {
-                        float h3[4] = {0.f, 0.f, 0.f, 0.f}, h4[4] = {0.f, 0.f, 0.f, 0.f};   // (e0,t0) (e0,t1) (e1,t0) (e1,t1)
-                        if (use3) dot16_2x2<S3>(sT3 + e0 * S3, sT3 + e1 * S3, sh.qr[0], sh.qr[1], h3);
-                        if (use4) dot16_2x2<S4>(sT4 + e0 * S4, sT4 + e1 * S4, sh.qq[0], sh.qq[1], h4);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int i = q >> 1, tt = q & 1, e = ln + 32 * i;
-                            if (e < P) {
-                                const int a = bA[i], b = bB[i];
-                                const float h = h3[q] + h4[q];
-                                sh.H[tt][a][b] = h;
-                                sh.H[tt][b][a] = h;
-                                const float gce = fmaf(0.5f, h3[q], h4[q] * (1.0f / 3.0f));
-                                sh.Gc[tt][a][b] = gce;
-                                sh.Gc[tt][b][a] = gce;
-                                const float vc = fmaf(1.0f / 6.0f, h3[q], h4[q] * (1.0f / 12.0f));
-                                v[tt] = fmaf(a == b ? vc : 2.0f * vc, sh.qq[tt][e], v[tt]);
-                            }
-                        }
-                    }
-                    // this lane keeps its own trajectory's part and passes the other to the
-                    // matching lane of the other group, so that each group's lanes sum to its total
-                    const float mine = t == 0 ? v[0] : v[1], other = t == 0 ? v[1] : v[0];
-                    vpart = mine + __shfl_xor_sync(FULL, other, 16);
                 } else
 #pragma unroll
                 for (int i = 0; i < EPL; ++i) {
