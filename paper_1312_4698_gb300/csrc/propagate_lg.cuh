@@ -381,7 +381,10 @@ struct WarpShared {
     // half-split Hessian of two-trajectory warps (see TensorLayout and lg_body)
     static constexpr int F3E = TensorLayout<F, Real>::F3E;
     static constexpr int KH = TensorLayout<F, Real>::KH;
-    alignas(16) Real xs[T][2 * KH];
+    // only two-trajectory mixed warps use it: elsewhere a stub, so that the shared memory
+    // left to L1 (the wide groups read their tensors through it) does not shrink
+    static constexpr bool kHalves = (T == 2) && (sizeof(Real) == 4) && F >= 6 && F <= 9;
+    alignas(16) Real xs[T][kHalves ? 2 * KH : 4];
     alignas(16) Real Gc[T][F][S3];          // gradient coefficients, full symmetric matrix (row a read by mode lane a)
     alignas(16) Real H[T][F][SH];
     typename AEntry<Real>::T A[F * F][JOBS]; // prefactor matrix per job, entry-major (job column swizzled)
@@ -526,6 +529,9 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
     // or the same cut with the tensor rows read from shared memory (TL::split)
     constexpr bool kSplit = kPair && !kTreg && TL::split;
     static_assert(kPair == (kTreg || kSplit), "two-trajectory warps take one of the two half-split schedules");
+    static_assert(!kPair || Sh::kHalves, "the half-split schedules need the halves of x");
+    // packed FP32 pairs in the monodromy drift and kick
+    constexpr bool kPacked = sizeof(Real) == 4;
     constexpr int F3E = Sh::F3E, KH = Sh::KH, KHS = TL::KHS;
     constexpr int EPH = (kTreg || kSplit) ? (P + 15) / 16 : 1;
     const int hx = ln >> 4, jx = ln & 15;
@@ -662,7 +668,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         q = coord_axpy(q, A.tdrift[sub], A.tdrift_f[sub], A.tdrift_lo[sub], p);
                         dS = fma(rt * Real(0.5) * pr, pr, dS);
                     }
-                    if constexpr (sizeof(Real) == 4) {
+                    if constexpr (kPacked) {
                         const float2 rt2 = make_float2(rt, rt);
 #pragma unroll
                         for (int s = 0; s < NCOL; ++s) {
@@ -713,15 +719,14 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     for (int i = 0; i < NQ; ++i) {
                         const int q4 = g + i * G;
                         if (4 * q4 < P) {
-                            float2 h3a = make_float2(0.f, 0.f), h3b = h3a, h4a = h3a, h4b = h3a;
+                            float4 h3 = make_float4(0.f, 0.f, 0.f, 0.f), h4 = h3;
                             if (use3) {
 #pragma unroll 8
                                 for (int k = 0; k < F; ++k) {
                                     const float4 tv = __ldg(T3v + k * (P4 / 4) + q4);
                                     const float x = sh.qr[t][k];
-                                    const float2 x2 = make_float2(x, x);
-                                    h3a = ffma2(lo2(tv), x2, h3a);
-                                    h3b = ffma2(hi2(tv), x2, h3b);
+                                    h3.x = fmaf(tv.x, x, h3.x); h3.y = fmaf(tv.y, x, h3.y);
+                                    h3.z = fmaf(tv.z, x, h3.z); h3.w = fmaf(tv.w, x, h3.w);
                                 }
                             }
                             if (use4) {
@@ -729,12 +734,10 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                                 for (int kl = 0; kl < P; ++kl) {
                                     const float4 tv = __ldg(T4v + kl * (P4 / 4) + q4);
                                     const float x = sh.qq[t][kl];
-                                    const float2 x2 = make_float2(x, x);
-                                    h4a = ffma2(lo2(tv), x2, h4a);
-                                    h4b = ffma2(hi2(tv), x2, h4b);
+                                    h4.x = fmaf(tv.x, x, h4.x); h4.y = fmaf(tv.y, x, h4.y);
+                                    h4.z = fmaf(tv.z, x, h4.z); h4.w = fmaf(tv.w, x, h4.w);
                                 }
                             }
-                            const float4 h3 = make_float4(h3a.x, h3a.y, h3b.x, h3b.y), h4 = make_float4(h4a.x, h4a.y, h4b.x, h4b.y);
                             const float h3j[4] = {h3.x, h3.y, h3.z, h3.w}, h4j[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
@@ -876,7 +879,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 __syncwarp();   // H complete before the monodromy kick reads it
                 dS = fma(-rtk, vlane, dS);
                 // monodromy kick: M_p -= tau H M_q (column lanes; rows of H by 16-byte broadcast loads)
-                if constexpr (sizeof(Real) == 4) {
+                if constexpr (kPacked) {
                     // packed pairs of H's row entries against pairs of the column's entries
                     constexpr int SH = Sh::SH;
 #pragma unroll
