@@ -88,8 +88,9 @@ template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<double> { using T = double2; };
 
 // Storage of one entry of the Herman-Kluk matrix A during its elimination: FP64
-// path a double2 (re, im); mixed path a double-FP32 complex (re.hi, re.lo, im.hi,
-// im.lo) -- the entries are formed in FP32 and eliminated to FP64-class accuracy.
+// path a double2 (re, im); mixed path a double-FP32 complex (re.hi, im.hi, re.lo,
+// im.lo) -- the entries are formed in FP32 and eliminated to FP64-class accuracy, the
+// real and imaginary words side by side for packed FP32 arithmetic.
 template <typename Real> struct AEntry;
 template <> struct AEntry<float> { using T = float4; };
 template <> struct AEntry<double> { using T = double2; };
@@ -205,6 +206,45 @@ __device__ __forceinline__ ff coord_add(ff c, float d)
     float s, e;
     ff_two_sum(c.hi, d, s, e);
     return ff_norm(s, e + c.lo);
+}
+
+// Complex double-FP32 numbers as packed pairs: hi = (re.hi, im.hi), lo = (re.lo, im.lo).
+// ff2_sub_mul_add_mul(a, x, u, y, v) = a - x u + y v for real double-FP32 x, y: per part
+// the same operations in the same order as ff_sub_mul_add_mul, each instruction doing the
+// real and the imaginary part at once.
+struct ff2 { float2 hi, lo; };
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+
+__device__ __forceinline__ void ff2_two_sum(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+__device__ __forceinline__ ff2 ff2_sub_mul_add_mul(ff2 a, ff x, ff2 u, ff y, ff2 v)
+{
+    const float2 xh = make_float2(x.hi, x.hi), xl = make_float2(x.lo, x.lo);
+    const float2 yh = make_float2(y.hi, y.hi), yl = make_float2(y.lo, y.lo);
+    const float2 p1 = __fmul2_rn(xh, u.hi);
+    float2 e1 = __ffma2_rn(xh, u.hi, neg2(p1));
+    e1 = __ffma2_rn(xh, u.lo, e1);
+    e1 = __ffma2_rn(xl, u.hi, e1);
+    const float2 p2 = __fmul2_rn(yh, v.hi);
+    float2 e2 = __ffma2_rn(yh, v.hi, neg2(p2));
+    e2 = __ffma2_rn(yh, v.lo, e2);
+    e2 = __ffma2_rn(yl, v.hi, e2);
+    float2 s1, t1, s2, t2;
+    ff2_two_sum(a.hi, neg2(p1), s1, t1);
+    ff2_two_sum(s1, p2, s2, t2);
+    const float2 lo = add2(add2(sub2(a.lo, e1), e2), add2(t1, t2));
+    ff2 r;
+    r.hi = add2(s2, lo);
+    r.lo = sub2(lo, sub2(r.hi, s2));
+    return r;
 }
 
 // Per-mode and per-reference-state constants, staged in shared memory so that
@@ -762,7 +802,10 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 #pragma unroll
                     for (int i = 0; i < EPH; ++i)
 #pragma unroll
-                        for (int tt = 0; tt < 2; ++tt) aF[i][tt] = a4[i][tt] = make_float2(0.0f, 0.0f);
+                        for (int tt = 0; tt < 2; ++tt) {
+                            aF[i][tt] = a4[i][tt] = make_float2(0.0f, 0.0f);
+                            sF[i][tt] = 0.0f;
+                        }
                     const float *x0 = &sh.xs[0][hx * KH], *x1 = &sh.xs[1][hx * KH];
                     const float *trow[EPH];          // kSplit: this lane's rows (entries past P read row 0)
 #pragma unroll
@@ -770,6 +813,8 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         const int e = jx + 16 * i;
                         trow[i] = sTh + (hx * P + (e < P ? e : 0)) * KHS;
                     }
+                    // a surface without couplings (uniform over the CTA) leaves every sum zero
+                    if (use3 || use4)
 #pragma unroll
                     for (int c = 0; c < KH; c += 4) {
                         const float4 u = *reinterpret_cast<const float4 *>(x0 + c);
@@ -1032,7 +1077,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         v.x = fma(k4[0], mqq, k4[1] * Mp[0][a]);
                         v.y = fma(k4[2], Mq[0][a], k4[3] * mpq);
                         if constexpr (sizeof(Real) == 4)
-                            sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = make_float4(v.x, 0.0f, v.y, 0.0f);
+                            sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = make_float4(v.x, v.y, 0.0f, 0.0f);
                         else
                             sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = v;
                     }
@@ -1104,7 +1149,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     const int pos = s0 + r;
                     if (pos < F) {
                         const float4 v = at(prow(pos) * F + k);
-                        const float m = fmaf(v.x, v.x, v.z * v.z);
+                        const float m = fmaf(v.x, v.x, v.y * v.y);
                         if (m > best) { best = m; bpos = pos; }
                     }
                 }
@@ -1123,7 +1168,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 }
                 const int pr = prow(k);
                 const float4 pk4 = at(pr * F + k);
-                const ff pre = {pk4.x, pk4.y}, pim = {pk4.z, pk4.w};
+                const ff pre = {pk4.x, pk4.z}, pim = {pk4.y, pk4.w};
                 {
                     const ff a1 = ff_mul(dr, pre), a2 = ff_mul(di, pim), b1 = ff_mul(dr, pim), b2 = ff_mul(di, pre);
                     dr = ff_add(a1, {-a2.hi, -a2.lo});
@@ -1147,7 +1192,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                     if (pos < F) {
                         const int row = prow(pos);
                         const float4 aik = at(row * F + k);
-                        const ff ar = {aik.x, aik.y}, ai = {aik.z, aik.w};
+                        const ff ar = {aik.x, aik.z}, ai = {aik.y, aik.w};
                         // l = a_ik / pivot
                         const ff zero = {0.0f, 0.0f};
                         const ff lr = ff_sub_mul_add_mul(zero, ai, ii, ar, ir);                       // ar ir - ai ii
@@ -1155,13 +1200,14 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
 #pragma unroll 2
                         for (int cc = k + 1; cc < F; ++cc) {
                             const float4 pv = at(pr * F + cc);
-                            const ff pre_c = {pv.x, pv.y}, pim_c = {pv.z, pv.w};
                             float4 &dst = at(row * F + cc);
                             const float4 av = dst;
-                            // a -= l p: re = a.re - lr pr + li pi, im = a.im - lr pi - li pr
-                            const ff nre = ff_sub_mul_add_mul({av.x, av.y}, lr, pre_c, li, pim_c);
-                            const ff nim = ff_sub_mul_add_mul({av.z, av.w}, lr, pim_c, {-li.hi, -li.lo}, pre_c);
-                            dst = make_float4(nre.hi, nre.lo, nim.hi, nim.lo);
+                            // a -= l p: re = a.re - lr pr + li pi, im = a.im - lr pi - li pr, i.e.
+                            // a - lr u + li v with u = p and v = (pi, -pr), both parts packed
+                            const ff2 u = {lo2(pv), hi2(pv)};
+                            const ff2 v = {make_float2(pv.y, -pv.x), make_float2(pv.w, -pv.z)};
+                            const ff2 n = ff2_sub_mul_add_mul({lo2(av), hi2(av)}, lr, u, li, v);
+                            dst = make_float4(n.hi.x, n.hi.y, n.lo.x, n.lo.y);
                         }
                     }
                 }
