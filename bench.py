@@ -381,11 +381,13 @@ def batch_arm(args):
         "data": "synthetic",
         "config": {"workload": f"batch of {len(mols)} molecules, F cycling over 3/6/9/12/15/24, n_traj log-uniform "
                                f"[512, 32768], steps uniform [2000, 8000], 4000 energies; sampling, "
-                               f"propagation (one persistent launch per F) and spectra in one CUDA graph",
+                               f"propagation (persistent launches, see schedule) and spectra in one CUDA graph",
                    "global_batch": world * sum(w8.n_traj for w8 in mols),
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"replicas x{world}",
-                   "autotuned_warps_per_cta": {f"F{F}": w for F, _, w in groups}},
+                   "autotuned_warps_per_cta": {f"F{F}": w for F, _, w in groups},
+                   "schedule": ("one persistent launch over all F classes" if plan.one_launch()
+                                else "one persistent launch per F class") + " (chosen by a timed probe of the plan)"},
         "spectra_per_s": world * len(mols) / (ms * 1e-3),
         "roofline": {"kernel": "k_propagate_lg_batch<float> (scivr_batch_launch)", "bound": "alu",
                      "achieved": achieved, "peak": eff_peak, "unit": "TFLOP/s", "frac": achieved / eff_peak,
