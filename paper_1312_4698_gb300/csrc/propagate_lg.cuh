@@ -815,14 +815,14 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                             __syncthreads();   // this tile is in shared memory for every warp
                             const float4 *tb = buf + (tile & 1) * (KT * RQ);
                             const int r0 = tile * KT, rows = min(KT, P - r0);
-#pragma unroll 2
-                            for (int kl = 0; kl < rows; ++kl) {
-                                const float x = sh.qq[t][r0 + kl];   // one load feeds every quad of the lane
 #pragma unroll
-                                for (int i = 0; i < NQ; ++i) {
-                                    const int q4 = g + i * G;
-                                    if (4 * q4 < P) {
+                            for (int i = 0; i < NQ; ++i) {
+                                const int q4 = g + i * G;
+                                if (4 * q4 < P) {
+#pragma unroll 4
+                                    for (int kl = 0; kl < rows; ++kl) {
                                         const float4 tv = tb[kl * RQ + q4];
+                                        const float x = sh.qq[t][r0 + kl];
                                         h4[i].x = fmaf(tv.x, x, h4[i].x); h4[i].y = fmaf(tv.y, x, h4[i].y);
                                         h4[i].z = fmaf(tv.z, x, h4[i].z); h4[i].w = fmaf(tv.w, x, h4[i].w);
                                     }
