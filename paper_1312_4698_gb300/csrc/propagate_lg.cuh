@@ -208,16 +208,6 @@ __device__ __forceinline__ ff coord_add(ff c, float d)
     return ff_norm(s, e + c.lo);
 }
 
-// Asynchronous 16-byte global -> shared copies (the CTA's tile stream of the quartic
-// rows) and their completion groups.
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // Complex double-FP32 numbers as packed pairs: hi = (re.hi, im.hi), lo = (re.lo, im.lo).
 // ff2_sub_mul_add_mul(a, x, u, y, v) = a - x u + y v for real double-FP32 x, y: per part
 // the same operations in the same order as ff_sub_mul_add_mul, each instruction doing the
@@ -411,13 +401,7 @@ struct TensorLayout {
     static constexpr int KH = (((F3E + P + 1) / 2) + 3) & ~3;
     static constexpr int KHS = (KH / 4) % 2 ? KH : KH + 4;
     static constexpr bool split = sizeof(Real) == 4 && STAGED && F >= 6 && F <= 9 && !lg_tensor_regs<F>();
-    // Not staged (F > 16): the quartic rows stream through shared memory in tiles of KT rows
-    // of P4 (P rounded up to 4) floats, two buffers, shared by all warps of the CTA.
-    static constexpr int P4 = (P + 3) & ~3;
-    static constexpr int KT = 24;
-    static constexpr size_t tile_elems = (size_t)KT * P4;
-    static constexpr size_t tensor_elems = !staged ? (sizeof(Real) == 4 ? 2 * tile_elems : 0)
-                                                   : (split ? (size_t)2 * P * KHS : (size_t)P * S3 + (size_t)P * S4);
+    static constexpr size_t tensor_elems = !staged ? 0 : (split ? (size_t)2 * P * KHS : (size_t)P * S3 + (size_t)P * S4);
     // after the tensors: the Herman-Kluk matrix coefficients acoef[a][b][4] =
     // (1/2) {rg_a/rg_b, rg_b/rg_a, -rg_a rg_b, 1/(rg_a rg_b)}, rg = sqrt(gamma)
     static constexpr size_t bytes = ((sizeof(Real) * (tensor_elems + (size_t)4 * F * F)) + 15) & ~(size_t)15;
@@ -766,77 +750,35 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                 __syncwarp();
                 Real vpart = Real(0);
                 if constexpr (!TL::staged) {
-                    // entry quads against the tensors ([k][e] and [kl][e] rows padded to P4): one
-                    // 16-byte load feeds four entries.  The cubic rows (F of them) come from L2;
-                    // the quartic rows (P of them) stream through shared memory in tiles of KT
-                    // rows that all warps of the CTA read, so L2 delivers each row once per CTA
-                    // and kick instead of once per warp (every warp is at the same kick: the
-                    // trajectories of a CTA take the same steps).
+                    // entry quads against the tensors in global memory (L2-resident; [k][e] and
+                    // [kl][e] rows padded to P4): one 16-byte load feeds four entries
                     static_assert(sizeof(Real) == 4, "the global-tensor schedule is the mixed path's");
                     const float4 *T3v = reinterpret_cast<const float4 *>(pes.T3p);
                     const float4 *T4v = reinterpret_cast<const float4 *>(pes.T4p);
-                    constexpr int RQ = P4 / 4, KT = TL::KT, NT = (P + KT - 1) / KT;
-                    float4 h3[NQ], h4[NQ];
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) h3[i] = h4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (use3) {
-#pragma unroll
-                        for (int i = 0; i < NQ; ++i) {
-                            const int q4 = g + i * G;
-                            if (4 * q4 < P) {
-#pragma unroll 8
-                                for (int k = 0; k < F; ++k) {
-                                    const float4 tv = __ldg(T3v + k * RQ + q4);
-                                    const float x = sh.qr[t][k];
-                                    h3[i].x = fmaf(tv.x, x, h3[i].x); h3[i].y = fmaf(tv.y, x, h3[i].y);
-                                    h3[i].z = fmaf(tv.z, x, h3[i].z); h3[i].w = fmaf(tv.w, x, h3[i].w);
-                                }
-                            }
-                        }
-                    }
-                    if (use4) {   // uniform over the CTA
-                        float4 *buf = reinterpret_cast<float4 *>(sT3);   // [2][KT][RQ]
-                        auto issue = [&](int tile) {
-                            const int r0 = tile * KT, rows = min(KT, P - r0);
-                            const float4 *src = T4v + (int64_t)r0 * RQ;
-                            float4 *dst = buf + (tile & 1) * (KT * RQ);
-                            for (int idx = threadIdx.x; idx < rows * RQ; idx += blockDim.x) cp_async16(dst + idx, src + idx);
-                            cp_async_commit();
-                        };
-                        __syncthreads();   // every warp is at this kick: both buffers are free
-                        issue(0);
-                        for (int tile = 0; tile < NT; ++tile) {
-                            if (tile + 1 < NT) {
-                                issue(tile + 1);
-                                cp_async_wait<1>();
-                            } else {
-                                cp_async_wait<0>();
-                            }
-                            __syncthreads();   // this tile is in shared memory for every warp
-                            const float4 *tb = buf + (tile & 1) * (KT * RQ);
-                            const int r0 = tile * KT, rows = min(KT, P - r0);
-#pragma unroll
-                            for (int i = 0; i < NQ; ++i) {
-                                const int q4 = g + i * G;
-                                if (4 * q4 < P) {
-#pragma unroll 4
-                                    for (int kl = 0; kl < rows; ++kl) {
-                                        const float4 tv = tb[kl * RQ + q4];
-                                        const float x = sh.qq[t][r0 + kl];
-                                        h4[i].x = fmaf(tv.x, x, h4[i].x); h4[i].y = fmaf(tv.y, x, h4[i].y);
-                                        h4[i].z = fmaf(tv.z, x, h4[i].z); h4[i].w = fmaf(tv.w, x, h4[i].w);
-                                    }
-                                }
-                            }
-                            __syncthreads();   // every warp is done with this buffer before tile + 2 refills it
-                        }
-                    }
 #pragma unroll
                     for (int i = 0; i < NQ; ++i) {
                         const int q4 = g + i * G;
                         if (4 * q4 < P) {
-                            const float h3j[4] = {h3[i].x, h3[i].y, h3[i].z, h3[i].w};
-                            const float h4j[4] = {h4[i].x, h4[i].y, h4[i].z, h4[i].w};
+                            float4 h3 = make_float4(0.f, 0.f, 0.f, 0.f), h4 = h3;
+                            if (use3) {
+#pragma unroll 8
+                                for (int k = 0; k < F; ++k) {
+                                    const float4 tv = __ldg(T3v + k * (P4 / 4) + q4);
+                                    const float x = sh.qr[t][k];
+                                    h3.x = fmaf(tv.x, x, h3.x); h3.y = fmaf(tv.y, x, h3.y);
+                                    h3.z = fmaf(tv.z, x, h3.z); h3.w = fmaf(tv.w, x, h3.w);
+                                }
+                            }
+                            if (use4) {
+#pragma unroll 4
+                                for (int kl = 0; kl < P; ++kl) {
+                                    const float4 tv = __ldg(T4v + kl * (P4 / 4) + q4);
+                                    const float x = sh.qq[t][kl];
+                                    h4.x = fmaf(tv.x, x, h4.x); h4.y = fmaf(tv.y, x, h4.y);
+                                    h4.z = fmaf(tv.z, x, h4.z); h4.w = fmaf(tv.w, x, h4.w);
+                                }
+                            }
+                            const float h3j[4] = {h3.x, h3.y, h3.z, h3.w}, h4j[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 const int e = 4 * q4 + j;
