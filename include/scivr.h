@@ -317,7 +317,7 @@ typedef struct {
     int64_t n_traj;
     const double *p0, *q0;        /* device [F][n_traj] */
     const double *w;              /* device [n_traj] */
-    void *amp;                    /* device complex double [n_chi][n_traj][amp_ld] */
+    void *amp;                    /* device complex double [n_chi][n_traj][amp_ld] (complex float if prm.amp_prec = SCIVR_MIXED) */
     int64_t amp_ld;
     uint8_t *good;                /* device [n_traj] */
     double E_min, E_max;
