@@ -462,7 +462,8 @@ def scivr_batch_create(entries, ft_mode=SCIVR_FT_FP64) -> Batch:
         keep += [g, pe, qe, e["pes"]]
         prm = scivr_prop_params(float(wl.dt), int(wl.n_steps), int(e.get("precision", SCIVR_MIXED)),
                                 float(e.get("stab_tol", wl.stab_tol)), g.ctypes.data, pe.ctypes.data,
-                                qe.ctypes.data, pe.shape[0], int(e.get("kernel", SCIVR_KERNEL_AUTO)))
+                                qe.ctypes.data, pe.shape[0], int(e.get("kernel", SCIVR_KERNEL_AUTO)),
+                                SCIVR_AMP_TA, int(_amp_prec_of(bufs.amp, None)))
         arr[i] = scivr_batch_item(e["pes"].handle, prm, int(bufs.w.shape[0]), _ptr(bufs.p0), _ptr(bufs.q0),
                                   _ptr(bufs.w), _ptr(bufs.amp), int(wl.n_steps) + 1, _ptr(bufs.good),
                                   float(wl.E_min), float(wl.E_max), int(wl.n_E), _ptr(bufs.I),

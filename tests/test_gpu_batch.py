@@ -34,12 +34,12 @@ def _molecules():
     return out
 
 
-def _setup(G, mols, precisions):
+def _setup(G, mols, precisions, amp_f32=False):
     import torch
     entries = []
     for w8, prec in zip(mols, precisions):
         pes = G.scivr_create_pes(w8.pes)
-        bufs = G.alloc_buffers(w8)
+        bufs = G.alloc_buffers(w8, amp_f32=amp_f32 and prec == 1)   # FP32 rows only on the mixed path
         G.scivr_sample_initial(pes, w8.gamma, w8.p_eq[0], w8.q_eq[0], w8.n_traj, w8.seed, bufs.p0,
                                bufs.q0, bufs.w)
         entries.append(dict(pes=pes, wl=w8, bufs=bufs, precision=prec,
@@ -73,6 +73,27 @@ def test_batch_matches_per_molecule_runs(G, ft_mode):
     plan = G.scivr_batch_create(entries, ft_mode=ft_mode)
     groups = plan.groups()
     assert sorted(F for F, _, _ in groups) == [3, 6, 9]
+    G.scivr_batch_launch(plan)
+    torch.cuda.synchronize()
+    for e in entries:
+        amp, good, I, ng = _reference(G, e, ft_mode)
+        b = e["bufs"]
+        assert torch.equal(b.good, good)
+        assert torch.equal(b.amp, amp)
+        assert torch.equal(b.I, I)
+        assert int(b.n_good.item()) == int(ng.item())
+    assert G.scivr_check_status() == G.SCIVR_OK
+
+
+@pytest.mark.parametrize("ft_mode", [0, 2])
+def test_batch_with_float_amplitude_rows_matches_per_molecule_runs(G, ft_mode):
+    """Mixed molecules with complex-float amplitude rows (amp_prec = SCIVR_MIXED) beside an
+    FP64 molecule with complex-double rows: the batch equals the per-molecule calls on the
+    same row types bit for bit."""
+    import torch
+    entries = _setup(G, _molecules(), [1, 1, 1, 1, 1, 0], amp_f32=True)
+    assert entries[0]["bufs"].amp.dtype == torch.float32 and entries[5]["bufs"].amp.dtype == torch.float64
+    plan = G.scivr_batch_create(entries, ft_mode=ft_mode)
     G.scivr_batch_launch(plan)
     torch.cuda.synchronize()
     for e in entries:
