@@ -1,6 +1,6 @@
 // C-ABI entry points of the learned residual (declared in include/scivr_mlp.h):
 // weight upload and tiling, batched evaluation, the training objective's
-// gradient, AdamW, and the analytic FP64 evaluation that judges them.
+// gradient, AdamW, and the analytic FP64 evaluation that checks them.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

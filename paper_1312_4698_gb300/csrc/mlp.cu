@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(320, 1)
         auto gwin = [](int qq) { return ((qq * 32) / R * F) / 32 * 32; };
         const int gbase = gwin(qd);
         int cc = 0;
-        // wait for the accumulator of the current product; uniform verdict over the compute threads
+        // wait for the accumulator of the current product; uniform outcome over the compute threads
         auto wait_acc = [&]() -> bool {
             if (!mbar_wait(&c_bar, cc & 1, kWaitLimitCycles)) atomicExch(&abort_flag, 1);
             ++cc;
