@@ -427,7 +427,12 @@ struct WarpShared {
     alignas(16) Real xs[T][kHalves ? 2 * KH : 4];
     alignas(16) Real Gc[T][F][S3];          // gradient coefficients, full symmetric matrix (row a read by mode lane a)
     alignas(16) Real H[T][F][SH];
-    typename AEntry<Real>::T A[F * F][JOBS]; // prefactor matrix per job, entry-major (job column swizzled)
+    // prefactor matrix per job, job-major rows of AS entries (AS odd): a lane that walks one
+    // row of its job's matrix advances its address by one entry, and lanes of different jobs
+    // at the same entry start in different banks
+    static constexpr int AS = ((F * F) % 2) ? F * F : F * F + 1;
+    typename AEntry<Real>::T A[JOBS][AS];
+    __device__ __forceinline__ typename AEntry<Real>::T &a_at(int job, int e) { return A[job][e]; }
     Real pj[F][JOBS], qj[F][JOBS];         // state per job, for the overlap (job column swizzled); FP32
                                            // in the mixed path, where the overlap is evaluated in FP32
     double Sj[JOBS];                        // action per job
@@ -1077,9 +1082,9 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
                         v.x = fma(k4[0], mqq, k4[1] * Mp[0][a]);
                         v.y = fma(k4[2], Mq[0][a], k4[3] * mpq);
                         if constexpr (sizeof(Real) == 4)
-                            sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = make_float4(v.x, v.y, 0.0f, 0.0f);
+                            sh.a_at(job, a * F + g) = make_float4(v.x, v.y, 0.0f, 0.0f);
                         else
-                            sh.A[a * F + g][jswz<JOBS>(a * F + g, job)] = v;
+                            sh.a_at(job, a * F + g) = v;
                     }
                 }
                 if (g < F) {
@@ -1120,7 +1125,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
             constexpr int LPJ = 32 / JOBS;
             static_assert(LPJ * JOBS == 32, "jobs must tile the warp");
             const int job = ln / LPJ, r = ln % LPJ;
-            auto at = [&](int e) -> float4 & { return sh.A[e][jswz<JOBS>(e, job)]; };
+            auto at = [&](int e) -> float4 & { return sh.a_at(job, e); };
             constexpr int PB = F > 16 ? 5 : 4, PPW = 64 / PB;   // bits per field, fields per word
             constexpr unsigned long long PMASK = (1ull << PB) - 1ull;
             unsigned long long perm0 = 0ull, perm1 = 0ull;
@@ -1229,7 +1234,7 @@ __device__ __forceinline__ void lg_body(const PropLaunch &L, int64_t cta, unsign
         } else {
             // FP64 path: in-place elimination in FP64, one lane per job, det A as the product of
             // the pivots (no range concern in FP64)
-            auto at = [&](int e) -> R2 & { return sh.A[e][jswz<JOBS>(e, ln)]; };
+            auto at = [&](int e) -> R2 & { return sh.a_at(ln, e); };
             double dr = 1.0, di = 0.0;
 #pragma unroll
             for (int k = 0; k < F; ++k) {
