@@ -52,8 +52,8 @@ TRAFFIC = {("k_ft_fp64", "f6"): 29.92e9, ("k_ft_tc2", "f6"): 7.98e9,
            # storage: one launch of 65536 trajectories x 400 steps with complex-double rows
            # read 17.06 MB and wrote 364.34 MB
            ("k_propagate_lg_mixed", "f9", "f64"): (17.06e6 + 364.34e6) / (65536 * 400),
-           # complex-float rows (the default mixed line): 13.80 MB read, 152.65 MB written
-           ("k_propagate_lg_mixed", "f9", "f32"): (13.80e6 + 152.65e6) / (65536 * 400)}
+           # complex-float rows (the default mixed line): 14.58 MB read, 153.33 MB written
+           ("k_propagate_lg_mixed", "f9", "f32"): (14.58e6 + 153.33e6) / (65536 * 400)}
 
 
 # trajectories of the oracle's timed sample per workload (10-30 s of host work on 16 cores),
