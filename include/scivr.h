@@ -239,10 +239,11 @@ int scivr_sample_initial(scivr_pes pes, const double *gamma, const double *p_eq,
  * aligned (the mixed path forms each amplitude sample in FP32, so nothing is lost
  * but the sample at c = 0, rounded from FP64).  good:
  * device [n_traj].  fin: host struct of optional device outputs (NULL = none).
- * Precision SCIVR_MIXED keeps the monodromy, the potential and det M in FP32
- * (positions, momenta, action and phase in FP64; the elimination that gives
- * det A in double-FP32 pairs, pivot product and argument in FP64), so its det M
- * deviation is FP32 rounding: give it a stab_tol scaled accordingly.  The mixed
+ * Precision SCIVR_MIXED keeps the monodromy, the potential and det M in FP32;
+ * positions, momenta, the action, the elimination that gives det A and the
+ * product of its pivots in double-FP32 pairs (FP64-class, about 2^-46 relative
+ * per operation, on the FP32 pipe); the argument of det A and the phase in FP64.
+ * Its det M deviation is FP32 rounding: give it a stab_tol scaled accordingly.  The mixed
  * path tests det M every 16 steps and at the last step (FP64: every step).
  * Built: SCIVR_FP64 for F <= 9 (both schedules), SCIVR_MIXED for F <= 24
  * (lane-group schedule; one trajectory per warp above F = 9, two column
